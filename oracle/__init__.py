@@ -1,0 +1,215 @@
+"""FP64 CPU oracle of the MPNL detection path (ctypes front end).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product library (``paper_2409_14355_gb300``) never imports it and
+shares no code with it.
+
+The arithmetic lives in ``mpnl_oracle.c`` (plain C, double precision), which
+cites the paper section or the stated reading for every step.  This module
+only compiles it with gcc and marshals numpy arrays.
+
+Parity pins (checked by ``tests/test_oracle_*.py`` against things other than
+the oracle itself): exhaustive ML on 4x4 QPSK, N_pe = 1 == sorted-QR SIC,
+N_pe = M^Nt == ML, QR and path-table invariants, brute-force top-N selection,
+noise-free recovery, MMSE vs a direct linear solve, closed-form SISO LLRs and
+the closed-form MRC bit-error rate.  Parity unpinned: how well the selection
+heuristic (the per-level error model) matches the paper's own MPNL BER; the
+paper prints no numbers for it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mpnl_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liborc_mpnl.so")
+_lock = threading.Lock()
+_lib = None
+
+LLR_MAX = 20.0
+PE_FLOOR = 1e-12
+BITS = {4: 2, 16: 4, 64: 6}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (FMA contraction off)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm", "-lpthread"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            D = ctypes.c_double
+            lib.orc_constellation.argtypes = [I, P]
+            lib.orc_sqrd.argtypes = [I, I, P, P, P, P, P]
+            lib.orc_qhy.argtypes = [I, I, I, P, P, P]
+            lib.orc_select_paths.argtypes = [I, I, P, D, I, P, P, P]
+            lib.orc_detect.argtypes = [I, I, I, P, P, P, I, P, D, P, P, P, P, P, P]
+            lib.orc_mmse.argtypes = [I, I, I, I, P, P, D, P, P, P, P]
+            lib.orc_detect_slot.argtypes = [I, I, I, I, I, I, D, P, P, P, P, P, P, P, P, P,
+                                            P, P, P, P, P, I]
+            for f in ("orc_constellation", "orc_sqrd", "orc_qhy", "orc_select_paths",
+                      "orc_detect", "orc_mmse", "orc_detect_slot"):
+                getattr(lib, f).restype = I
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c128(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def _check(st, what):
+    if st < 0:
+        raise RuntimeError(f"oracle {what} failed with status {st}")
+    return st
+
+
+def constellation(qam: int) -> np.ndarray:
+    """Label-indexed unit-energy Gray constellation (TS 38.211 §5.1), complex128[M]."""
+    out = np.zeros(qam, np.complex128)
+    _check(_load().orc_constellation(qam, _p(out)), "constellation")
+    return out
+
+
+def sqrd(H):
+    """Sorted QR of one channel H[nr][nt] -> (Q, R, perm, gap)."""
+    H = _c128(H)
+    nr, nt = H.shape
+    Q = np.zeros((nr, nt), np.complex128)
+    R = np.zeros((nt, nt), np.complex128)
+    perm = np.zeros(nt, np.int32)
+    gap = np.zeros(nt, np.float64)
+    _check(_load().orc_sqrd(nr, nt, _p(H), _p(Q), _p(R), _p(perm), _p(gap)), "sqrd")
+    return Q, R, perm, gap
+
+
+def qhy(Q, Y):
+    """z = Q^H y for Y[n_sym][nr] -> Z[n_sym][nt]."""
+    Q = _c128(Q)
+    Y = _c128(Y)
+    nr, nt = Q.shape
+    n_sym = Y.shape[0]
+    Z = np.zeros((n_sym, nt), np.complex128)
+    _check(_load().orc_qhy(nr, nt, n_sym, _p(Q), _p(Y), _p(Z)), "qhy")
+    return Z
+
+
+def select_paths(rdiag, sigma2: float, qam: int, n_pe: int):
+    """Best-first position-vector table -> (paths uint8[n_pe][nt], score[n_pe], pe[nt])."""
+    rdiag = np.ascontiguousarray(np.asarray(rdiag, np.float64))
+    nt = rdiag.shape[0]
+    paths = np.zeros((n_pe, nt), np.uint8)
+    score = np.zeros(n_pe, np.float64)
+    pe = np.zeros(nt, np.float64)
+    _check(_load().orc_select_paths(nt, qam, _p(rdiag), float(sigma2), n_pe, _p(paths),
+                                    _p(score), _p(pe)), "select_paths")
+    return paths, score, pe
+
+
+def detect(R, Z, perm, paths, sigma2: float, qam: int, want_all: bool = False):
+    """Walks + argmin + LLRs for one subcarrier.
+
+    Returns dict(hard, llr, ped2, margin[, ped_all, sym_all]).
+    """
+    R = _c128(R)
+    Z = _c128(Z)
+    perm = np.ascontiguousarray(np.asarray(perm, np.int32))
+    paths = np.ascontiguousarray(np.asarray(paths, np.uint8))
+    nt = R.shape[0]
+    n_sym = Z.shape[0]
+    n_pe = paths.shape[0]
+    B = BITS[qam]
+    hard = np.zeros((n_sym, nt), np.uint8)
+    llr = np.zeros((n_sym, nt, B), np.float64)
+    ped2 = np.zeros((n_sym, 2), np.float64)
+    margin = np.zeros(n_sym, np.float64)
+    ped_all = np.zeros((n_sym, n_pe), np.float64) if want_all else None
+    sym_all = np.zeros((n_sym, n_pe, nt), np.uint8) if want_all else None
+    _check(_load().orc_detect(nt, qam, n_sym, _p(R), _p(Z), _p(perm), n_pe, _p(paths),
+                              float(sigma2), _p(hard), _p(llr), _p(ped2), _p(margin),
+                              _p(ped_all), _p(sym_all)), "detect")
+    out = dict(hard=hard, llr=llr, ped2=ped2, margin=margin)
+    if want_all:
+        out["ped_all"] = ped_all
+        out["sym_all"] = sym_all
+    return out
+
+
+def mmse(H, Y, sigma2: float, qam: int):
+    """Linear MMSE for one subcarrier -> dict(hard, llr, xt, nu)."""
+    H = _c128(H)
+    Y = _c128(Y)
+    nr, nt = H.shape
+    n_sym = Y.shape[0]
+    B = BITS[qam]
+    hard = np.zeros((n_sym, nt), np.uint8)
+    llr = np.zeros((n_sym, nt, B), np.float64)
+    xt = np.zeros((n_sym, nt), np.complex128)
+    nu = np.zeros(nt, np.float64)
+    _check(_load().orc_mmse(nr, nt, qam, n_sym, _p(H), _p(Y), float(sigma2), _p(hard),
+                            _p(llr), _p(xt), _p(nu)), "mmse")
+    return dict(hard=hard, llr=llr, xt=xt, nu=nu)
+
+
+def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, paths=None, n_threads: int = 0,
+                with_mmse: bool = False):
+    """Steps 1-6 (and 7 with ``with_mmse``) over a whole slot.
+
+    H: [n_sc][nr][nt], Y: [n_sc][n_sym][nr] (any complex dtype; promoted to
+    complex128).  Returns a dict of numpy arrays plus ``threads`` (the number
+    of host threads the oracle used).
+    """
+    H = _c128(H)
+    Y = _c128(Y)
+    n_sc, nr, nt = H.shape
+    n_sym = Y.shape[1]
+    B = BITS[qam]
+    hard = np.zeros((n_sc, n_sym, nt), np.uint8)
+    llr = np.zeros((n_sc, n_sym, nt, B), np.float64)
+    ped2 = np.zeros((n_sc, n_sym, 2), np.float64)
+    R = np.zeros((n_sc, nt, nt), np.complex128)
+    perm = np.zeros((n_sc, nt), np.int32)
+    Z = np.zeros((n_sc, n_sym, nt), np.complex128)
+    paths_out = np.zeros((n_sc, n_pe, nt), np.uint8)
+    gap = np.zeros((n_sc, nt), np.float64)
+    margin = np.zeros((n_sc, n_sym), np.float64)
+    mh = np.zeros((n_sc, n_sym, nt), np.uint8) if with_mmse else None
+    ml = np.zeros((n_sc, n_sym, nt, B), np.float64) if with_mmse else None
+    pin = None if paths is None else np.ascontiguousarray(np.asarray(paths, np.uint8))
+    st = _load().orc_detect_slot(n_sc, n_sym, nr, nt, qam, n_pe, float(sigma2), _p(H), _p(Y),
+                                 _p(pin), _p(hard), _p(llr), _p(ped2), _p(R), _p(perm), _p(Z),
+                                 _p(paths_out), _p(gap), _p(margin), _p(mh), _p(ml),
+                                 int(n_threads))
+    _check(st, "detect_slot")
+    out = dict(hard=hard, llr=llr, ped2=ped2, R=R, perm=perm, Z=Z, paths=paths_out,
+               sqrd_gap=gap, margin=margin, threads=st)
+    if with_mmse:
+        out["mmse_hard"] = mh
+        out["mmse_llr"] = ml
+    return out
