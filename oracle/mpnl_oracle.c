@@ -212,7 +212,7 @@ int orc_qhy(int nr, int nt, int n_sym, const double *Q, const double *Y, double 
  * distance to the level's unconstrained estimate) of the symbol taken at that
  * level.  Reading of the error model (the paper gives none):
  *   gamma_l = R_ll^2 / sigma2                    (unit-energy symbols)
- *   Pe_l    = 1 - (1 - 2 (1 - 1/sqrt(M)) Qf(sqrt(3 gamma_l / (M - 1))))^2,
+ *   Pe_l    = 1 - (1 - c Qf(sqrt(3 gamma_l / (M - 1))))^2, c = 2 (1 - 1/sqrt(M)),
  *             the nearest-neighbour symbol-error rate of square M-QAM,
  *             floored at ORC_PE_FLOOR; Qf(x) = erfc(x / sqrt 2) / 2
  *   P_l(k)  = (1 - Pe_l) Pe_l^(k-1)              (geometric rank model)
@@ -234,8 +234,10 @@ static double level_pe(double rll, double sigma2, int M)
     double gamma = rll * rll / sigma2;
     double x = sqrt(3.0 * gamma / (double)(M - 1));
     double qf = 0.5 * erfc(x / sqrt(2.0));
-    double a = 1.0 - 2.0 * (1.0 - 1.0 / sqrt((double)M)) * qf;
-    double pe = 1.0 - a * a;
+    double cq = 2.0 * (1.0 - 1.0 / sqrt((double)M)) * qf;
+    /* 1 - (1 - cq)^2 written as cq (2 - cq): same value, no cancellation when
+     * cq is tiny (high SNR) */
+    double pe = cq * (2.0 - cq);
     if (pe < ORC_PE_FLOOR) pe = ORC_PE_FLOOR;
     return pe;
 }

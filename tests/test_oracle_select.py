@@ -12,8 +12,9 @@ from tests._ref_helpers import qfunc
 
 def _pe_textbook(gamma, M):
     # exact nearest-neighbour SER of square M-QAM at SNR gamma (Proakis eq. 4.3-30)
+    # (1 - (1 - p)^2 expanded as p (2 - p) to keep precision at high SNR)
     p = 2.0 * (1.0 - 1.0 / math.sqrt(M)) * qfunc(math.sqrt(3.0 * gamma / (M - 1)))
-    return max(1.0 - (1.0 - p) ** 2, oracle.PE_FLOOR)
+    return max(p * (2.0 - p), oracle.PE_FLOOR)
 
 
 def _bruteforce_top(rdiag, sigma2, M, n_pe):
@@ -49,10 +50,12 @@ def test_equal_levels_break_ties_lexicographically():
     paths, score, _ = oracle.select_paths(rdiag, 0.5, 4, 30)
     want, _ = _bruteforce_top(rdiag, 0.5, 4, 30)
     np.testing.assert_array_equal(paths, want)
-    # with equal levels, the lexicographic rule (top level compared first,
-    # smaller first) lists the single deviations from the bottom level up
-    assert paths[1].tolist() == [2, 1, 1, 1]
-    assert paths[2].tolist() == [1, 2, 1, 1]
+    # Two equal levels: swapping the two terms of a two-term sum is exact, so
+    # (2,1) and (1,2) tie exactly and the lexicographic rule (top level
+    # compared first, smaller first) puts (2,1) ahead.
+    paths, score, _ = oracle.select_paths(np.ones(2), 0.5, 4, 5)
+    assert paths[1].tolist() == [2, 1] and paths[2].tolist() == [1, 2]
+    assert score[1] == score[2]
 
 
 @pytest.mark.parametrize("nt,M,n_pe", [(16, 64, 256), (8, 16, 64), (16, 64, 1024)])
