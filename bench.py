@@ -1,0 +1,395 @@
+"""Benchmark of the MPNL detection path on GB300 (one JSON line on stdout).
+
+A step is one pass of the whole path over one slot of synthetic input:
+sorted QR + z = Q^H y, position-vector selection, the N_pe walks with argmin
+and max-log LLRs, and the linear MMSE baseline.  Default workload: 16x16
+64-QAM, 3276 subcarriers x 14 OFDM symbols (one 0.5 ms slot of the real-time
+load), N_pe = 256, i.i.d. Rayleigh, SNR 21 dB.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mpnl|reference]
+
+Multi-GPU (torchrun): every rank detects its own slots (subcarriers are
+independent; no collective on the data path), `value` is the total over all
+ranks divided by the slowest rank's time ("scaling": "weak").
+
+`--impl reference` times the FP64 CPU oracle (the only reference the paper
+allows; it has no code) on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2409_14355_gb300 import inputs  # noqa: E402
+
+METRIC = "MIMO detections/s (hard decisions + max-log LLRs, with the MMSE baseline in the same step)"
+UNIT = "detections/s"
+BITS = {4: 2, 16: 4, 64: 6}
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["mpnl", "reference"], default="mpnl")
+    ap.add_argument("--workload", default="16x16-64qam-3276sc")
+    ap.add_argument("--n-pe", type=int, default=256)
+    ap.add_argument("--snr-index", type=int, default=2)
+    ap.add_argument("--ring", type=int, default=16, help="distinct slots cycled through (> L2)")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_config(args, w):
+    return {
+        "workload": args.workload, "nr": w["nr"], "nt": w["nt"], "qam": w["qam"],
+        "n_sc": w["n_sc"], "n_sym": 14, "n_pe": args.n_pe, "channel": w["channel"],
+        "snr_db": w["snrs"][args.snr_index],
+    }
+
+
+# --------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power = [], [], []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle timing (baseline only)
+# --------------------------------------------------------------------------
+def time_oracle(sl, qam, n_pe, seconds: float, max_sc: int | None = None):
+    """Run the oracle on growing prefixes of the slot's subcarriers until one
+    run takes >= `seconds` (or the cap is reached).  Returns (dets/s, threads,
+    subcarriers, elapsed)."""
+    import oracle
+
+    n = 4
+    cap = sl.n_sc if max_sc is None else min(max_sc, sl.n_sc)
+    while True:
+        n = min(n, cap)
+        t0 = time.perf_counter()
+        out = oracle.detect_slot(sl.H[:n], sl.Y[:n], sl.sigma2, qam, n_pe, with_mmse=True)
+        dt = time.perf_counter() - t0
+        if dt >= seconds or n >= cap:
+            return n * sl.n_sym / dt, out["threads"], n, dt
+        grow = max(2.0, min(8.0, 1.2 * seconds / max(dt, 1e-3)))
+        n = int(n * grow) + 1
+
+
+def source_hash(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic(kernel_src: list[str]):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "detect_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != source_hash(kernel_src):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 oracle on host cores
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = inputs.WORKLOADS[args.workload]
+    sl = inputs.workload_slot(args.workload, args.snr_index)
+    import oracle
+
+    oracle.build()
+    qam, nt = w["qam"], w["nt"]
+    # a bounded sample per step: sized from a calibration run so K + W steps
+    # take a few minutes at most
+    _, _, n_cal, dt_cal = time_oracle(sl, qam, args.n_pe, 1.0)
+    per_sc = dt_cal / n_cal
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    n_step = int(max(2, min(sl.n_sc, budget / per_sc)))
+    for i in range(args.warmup):
+        j = (i * n_step) % (sl.n_sc - n_step + 1)
+        oracle.detect_slot(sl.H[j:j + n_step], sl.Y[j:j + n_step], sl.sigma2, qam, args.n_pe,
+                           with_mmse=True)
+    t0 = time.perf_counter()
+    threads = 0
+    for i in range(args.steps):
+        j = ((args.warmup + i) * n_step) % (sl.n_sc - n_step + 1)
+        o = oracle.detect_slot(sl.H[j:j + n_step], sl.Y[j:j + n_step], sl.sigma2, qam,
+                               args.n_pe, with_mmse=True)
+        threads = o["threads"]
+    dt = time.perf_counter() - t0
+    dets = args.steps * n_step * sl.n_sym
+    value = dets / dt
+    sample = (f"{n_step} of {sl.n_sc} subcarriers x 14 symbols per step "
+              f"(full pipeline incl. MMSE), FP64")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args, w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gb_per_s": value * nt * BITS[qam] / 1e9,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+def run_mpnl(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2409_14355_gb300 import build as cuda_build
+    from paper_2409_14355_gb300 import mpnl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or world == 1:
+        cuda_build.build()
+    if world > 1:
+        dist.barrier()
+    mpnl.load_library()
+
+    w = inputs.WORKLOADS[args.workload]
+    nr, nt, qam, n_sc = w["nr"], w["nt"], w["qam"], w["n_sc"]
+    n_sym, n_pe, B = 14, args.n_pe, BITS[qam]
+    ring = []
+    for i in range(args.ring):
+        sl = inputs.workload_slot(args.workload, args.snr_index, extra_seed=1 + i + 1000 * rank)
+        ring.append((torch.from_numpy(sl.H).to(dev), torch.from_numpy(sl.Y).to(dev), sl.sigma2))
+    sigma2 = ring[0][2]
+    ring_bytes = sum(h.numel() * 8 + y.numel() * 8 for h, y, _ in ring)
+    buf = mpnl.SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, dev, mmse=True)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i, ev=None):
+        H, Y, s2 = ring[i % len(ring)]
+        mpnl.preprocess(H, Y, out=(buf.R, buf.inv_diag, buf.perm, buf.Z))
+        mpnl.select_paths(buf.R, s2, qam, n_pe, nt, out=buf.paths)
+        if ev is not None:
+            ev[0].record(stream)
+        mpnl.detect(buf.R, buf.inv_diag, buf.perm, buf.paths, buf.Z, s2, qam,
+                    out=(buf.hard, buf.llr, buf.ped2))
+        if ev is not None:
+            ev[1].record(stream)
+        mpnl.linear_mmse(H, Y, s2, qam, out=(buf.mmse_hard, buf.mmse_llr))
+
+    for i in range(args.warmup):
+        step(i)
+    mpnl.check_status(local)
+    torch.cuda.synchronize()
+
+    K = args.steps
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(K)]
+    det_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)  # let the sampler attach
+    t_start.record(stream)
+    for i in range(K):
+        step_ev[i][0].record(stream)
+        step(args.warmup + i, det_ev[i])
+        step_ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    mpnl.check_status(local)
+    if world > 1:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    lat = sorted(a.elapsed_time(b) for a, b in step_ev)
+    det_ms = [a.elapsed_time(b) for a, b in det_ev]
+    det_avg = sum(det_ms) / len(det_ms)
+
+    # ---- end to end through the public host API (pinned host buffers)
+    e2e_value = None
+    h2d = d2h = 0
+    hs = []
+    for i in range(min(args.ring, 4)):
+        H, Y, _ = ring[i]
+        hs.append((H.cpu().pin_memory(), Y.cpu().pin_memory()))
+    for i in range(2):
+        mpnl.detect_slot(hs[i % len(hs)][0], hs[i % len(hs)][1], sigma2, qam, n_pe, mmse=True,
+                         buffers=buf)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.e2e_steps):
+        Hh, Yh = hs[i % len(hs)]
+        out = mpnl.detect_slot(Hh, Yh, sigma2, qam, n_pe, mmse=True, buffers=buf)
+    e2e_dt = time.perf_counter() - t0
+    h2d = hs[0][0].numel() * 8 + hs[0][1].numel() * 8
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    e2e_dets = args.e2e_steps * n_sc * n_sym
+    if world > 1:
+        t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    e2e_value = world * e2e_dets / e2e_dt
+
+    dets_per_step = n_sc * n_sym
+    value = world * K * dets_per_step / elapsed
+
+    # ---- roofline of the dominant kernel (walk kernel, FP32 ALU bound)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flop_per_det = n_pe * (4 * nt * nt + 4 * nt)
+    achieved_tflops = flop_per_det * dets_per_step / (det_avg / 1e3) / 1e12
+    det_src = [os.path.join(ROOT, "paper_2409_14355_gb300", "csrc", f)
+               for f in ("detect.cu", "mpnl_common.cuh")]
+    traffic = load_traffic(det_src)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            sl0 = inputs.workload_slot(args.workload, args.snr_index, extra_seed=1)
+            v, thr, n_used, dt = time_oracle(sl0, qam, n_pe, args.cpu_seconds)
+            cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
+                   "sample": f"{n_used} of {n_sc} subcarriers x 14 symbols of one slot "
+                             f"(whole path incl. MMSE), FP64, {dt:.1f} s"}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(args, w), parallelism=f"replicas{world}",
+                           l2=f"ring of {len(ring)} distinct slots, {ring_bytes / 1e6:.0f} MB of "
+                              f"H+Y > 129 MB L2"),
+            "gb_per_s": value * nt * B / 1e9,
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "max": lat[-1], "deadline": 0.5},
+            "roofline": {"bound": "alu", "kernel": "detect_walk_kernel",
+                         "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                         "frac": achieved_tflops / peak_tflops, "traffic": traffic,
+                         "flop_per_launch": flop_per_det * dets_per_step,
+                         "launch_ms": det_avg,
+                         "peak_note": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
+                                      f"{sm_max:.0f} MHz (max SM clock)"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": 4 * K,
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mpnl(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,162 @@
+/*
+ * mpnl.h -- C ABI of the GB300 MPNL uplink MIMO detection path.
+ *
+ * Katsaros & Nikitopoulos, "Enabling Ultra-Dense, Open-RAN, Vehicular
+ * Networks with Non-Linear MIMO Processing" (arXiv 2409.14355).  §II
+ * (Background) describes the Massively Parallelizable Non-Linear (MPNL)
+ * detector: the position of the most promising candidate transmit vectors is
+ * found from the channel alone, before data arrives; during transmission
+ * those N_p candidates are evaluated in parallel.  §III-B uses N_p <= 32,
+ * 14-symbol slots with the channel constant over the slot, and the linear
+ * MMSE detector as the baseline.
+ *
+ * The path, per subcarrier (sc) and OFDM symbol, with y = H s + n:
+ *   mpnl_preprocess    sorted QR  H P = Q R  and  z = Q^H y
+ *   mpnl_select_paths  the N_pe most probable position vectors per sc
+ *   mpnl_detect        N_pe SIC / partial-Euclidean-distance walks, argmin
+ *                      -> hard decisions, max-log LLRs over the list
+ *   mpnl_linear_mmse   linear MMSE baseline (hard decisions + LLRs)
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every data pointer is DEVICE memory (or host memory registered with /
+ *   allocated by CUDA) owned by the caller; the library never allocates on
+ *   these calls and keeps no pointer after returning.
+ * - Complex values are interleaved (re, im) float32 pairs ("c64"), 8-byte
+ *   aligned.  Real arrays are float32, 4-byte aligned.
+ * - Symbol labels are the TS 38.211 §5.1 Gray bit labels as integers, bit b0
+ *   (the most significant) first; constellations have unit average energy.
+ * - Level index l = 0..nt-1 is the row of R; detection runs from level nt-1
+ *   (the column the sorted QR picked last) down to level 0.
+ * - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call
+ *   only enqueues work on it and returns; nothing synchronises.
+ * - Return value: MPNL_OK (0) or a negative MPNL_ERR_*.  On error nothing was
+ *   enqueued, except MPNL_ERR_CUDA from a failed launch; mpnl_last_error()
+ *   returns the message.  No call prints, aborts or traps.
+ * - Limits: 1 <= nt <= nr <= 32, nt <= 16, qam in {4, 16, 64},
+ *   1 <= n_sym <= 32, 1 <= n_pe <= min(1024, qam^nt), n_sc >= 0 (0 is a
+ *   no-op), sigma2 > 0 and finite.
+ */
+#ifndef MPNL_H
+#define MPNL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPNL_OK 0
+#define MPNL_ERR_INVALID_ARG (-1) /* bad size, null or misaligned pointer, bad value */
+#define MPNL_ERR_UNSUPPORTED (-2) /* valid request outside what this build implements */
+#define MPNL_ERR_CUDA (-3)        /* a CUDA runtime call or kernel launch failed */
+#define MPNL_ERR_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+
+#define MPNL_MAX_NT 16
+#define MPNL_MAX_NR 32
+#define MPNL_MAX_NSYM 32
+#define MPNL_MAX_NPE 1024
+/* |LLR| written when the list holds no candidate with the opposite bit. */
+#define MPNL_LLR_MAX 20.0f
+
+typedef struct mpnl_ctx mpnl_ctx;
+
+/* Problem sizes of one slot: n_sc subcarriers x n_sym OFDM symbols, nr
+ * receive antennas, nt single-antenna users (streams), QAM order, and the
+ * number N_pe of position vectors evaluated per detection. */
+typedef struct {
+    int n_sc;
+    int n_sym;
+    int nr;
+    int nt;
+    int qam;
+    int n_pe;
+} mpnl_dims;
+
+/* Create a context bound to CUDA device `device` (made current on the calling
+ * thread).  *ctx receives the handle; release it with mpnl_destroy.
+ * Errors: MPNL_ERR_INVALID_ARG (ctx NULL), MPNL_ERR_CUDA (no such device). */
+int mpnl_create(mpnl_ctx **ctx, int device);
+
+/* Release a context (NULL is ignored).  Does not synchronise any stream. */
+void mpnl_destroy(mpnl_ctx *ctx);
+
+/* Message of the last error on this context ("" if none).  The string is
+ * owned by the context and valid until the next call on it. */
+const char *mpnl_last_error(const mpnl_ctx *ctx);
+
+/* Device scratch bytes the calls below need for `dims` (0: the kernels keep
+ * all intermediates on chip).  `ws` arguments below may then be NULL. */
+size_t mpnl_workspace_bytes(const mpnl_dims *dims);
+
+/* Channel pre-processing (§II: "observing the MIMO channel"): sorted QR
+ * H P = Q R with the smallest-residual-norm column first (SQRD) and
+ * z = Q^H y for every symbol, per subcarrier.
+ *   H        in  c64 [n_sc][nr][nt]          channel, row-major
+ *   Y        in  c64 [n_sc][n_sym][nr]       received symbols
+ *   R        out c64 [n_sc][nt(nt+1)/2]      upper triangle, packed row by
+ *                row: entry (i, j >= i) at i*nt - i(i-1)/2 + (j - i); the
+ *                diagonal is real and positive (imaginary part 0)
+ *   inv_diag out f32 [n_sc][nt]              1 / R_ll
+ *   perm     out u8  [n_sc][nt]              perm[l] = user in column l of HP
+ *   Z        out c64 [n_sc][n_sym][nt]       z = Q^H y  (Q is not stored) */
+int mpnl_preprocess(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const void *Y, void *R,
+                    float *inv_diag, uint8_t *perm, void *Z, void *ws, void *stream);
+
+/* Position-vector pre-selection (§II: found "before any transmission
+ * begins" from the channel; §III-B: N_p).  Per level, gamma_l = R_ll^2 /
+ * sigma2 gives the square-QAM symbol-error probability Pe_l (floored at
+ * 1e-12), and P_l(k) = (1 - Pe_l) Pe_l^(k-1) the chance that the transmitted
+ * symbol is the k-th closest.  The N_pe vectors of largest prod_l P_l(p_l)
+ * are written best first (ties: lexicographically smaller from level nt-1
+ * down); row 0 is the all-ones vector (plain SIC).
+ *   R      in  c64 [n_sc][nt(nt+1)/2]  as written by mpnl_preprocess (only
+ *              the diagonal is read)
+ *   paths  out u8  [n_sc][n_pe][nt]     ranks 1..qam, level index last */
+int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, float sigma2,
+                      uint8_t *paths, void *ws, void *stream);
+
+/* Evaluation of the position vectors (§II: the most promising solutions
+ * "processed in parallel").  For every (sc, symbol) and every row p of the
+ * table, independently: for l = nt-1..0, e_l = z_l - sum_{j>l} R_lj s_j,
+ * b_l = e_l / R_ll, s_l = the p_l-th closest constellation point to b_l
+ * (ordered by distance, then label), d += R_ll^2 |b_l - s_l|^2.  The row
+ * with the smallest d (tie: lower row) gives the hard decisions; user
+ * perm[l] receives s_l.  Max-log LLR of bit b of user k:
+ * (min_{rows, bit=1} d - min_{rows, bit=0} d) / sigma2 (positive: bit 0),
+ * +-MPNL_LLR_MAX when one side is empty.
+ *   R, inv_diag, perm, Z   in   as written by mpnl_preprocess
+ *   paths                  in   u8 [n_sc][n_pe][nt], entries 1..qam
+ *                               (checked on the device: a bad entry is
+ *                               clamped and reported as MPNL_ERR_INVALID_ARG
+ *                               by mpnl_check_status)
+ *   hard                   out  u8  [n_sc][n_sym][nt]      labels, user order
+ *   llr                    out  f32 [n_sc][n_sym][nt][log2 qam] (NULL: skip)
+ *   ped2                   out  f32 [n_sc][n_sym][2] best and runner-up d
+ *                               (+inf runner-up when n_pe == 1; NULL: skip) */
+int mpnl_detect(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const float *inv_diag,
+                const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
+                uint8_t *hard, float *llr, float *ped2, void *ws, void *stream);
+
+/* Linear MMSE baseline (§I, §III-B: "de facto standard linear MMSE"):
+ * W = (H^H H + sigma2 I)^{-1} H^H; x = W y; mu_k = (W H)_kk;
+ * x~_k = x_k / mu_k, nu_k = (1 - mu_k) / mu_k; hard = nearest point to x~_k;
+ * LLR_b = (min_{q: bit b = 1} |x~ - q|^2 - min_{q: bit b = 0} |x~ - q|^2) / nu_k.
+ *   H, Y  in   as for mpnl_preprocess
+ *   hard  out  u8  [n_sc][n_sym][nt]
+ *   llr   out  f32 [n_sc][n_sym][nt][log2 qam]   (NULL: skip) */
+int mpnl_linear_mmse(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const void *Y,
+                     float sigma2, uint8_t *hard, float *llr, void *ws, void *stream);
+
+/* Synchronise `stream` and report device-side argument errors recorded by
+ * the calls enqueued on this context since the previous check (currently: a
+ * position-vector entry outside 1..qam seen by mpnl_detect).  Returns MPNL_OK,
+ * MPNL_ERR_INVALID_ARG (with a message) or MPNL_ERR_CUDA. */
+int mpnl_check_status(mpnl_ctx *ctx, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPNL_H */

@@ -65,10 +65,10 @@ def _load():
             lib.orc_sqrd.argtypes = [I, I, P, P, P, P, P]
             lib.orc_qhy.argtypes = [I, I, I, P, P, P]
             lib.orc_select_paths.argtypes = [I, I, P, D, I, P, P, P]
-            lib.orc_detect.argtypes = [I, I, I, P, P, P, I, P, D, P, P, P, P, P, P]
+            lib.orc_detect.argtypes = [I, I, I, P, P, P, I, P, D, P, P, P, P, P, P, D, P]
             lib.orc_mmse.argtypes = [I, I, I, I, P, P, D, P, P, P, P]
             lib.orc_detect_slot.argtypes = [I, I, I, I, I, I, D, P, P, P, P, P, P, P, P, P,
-                                            P, P, P, P, P, I]
+                                            P, P, P, P, P, I, D, P]
             for f in ("orc_constellation", "orc_sqrd", "orc_qhy", "orc_select_paths",
                       "orc_detect", "orc_mmse", "orc_detect_slot"):
                 getattr(lib, f).restype = I
@@ -132,10 +132,13 @@ def select_paths(rdiag, sigma2: float, qam: int, n_pe: int):
     return paths, score, pe
 
 
-def detect(R, Z, perm, paths, sigma2: float, qam: int, want_all: bool = False):
+def detect(R, Z, perm, paths, sigma2: float, qam: int, want_all: bool = False,
+           tie_eps: float = 0.0):
     """Walks + argmin + LLRs for one subcarrier.
 
-    Returns dict(hard, llr, ped2, margin[, ped_all, sym_all]).
+    Returns dict(hard, llr, ped2, margin, flip_floor[, ped_all, sym_all]);
+    flip_floor is the smallest partial PED at a ranking whose neighbour gap
+    is below tie_eps (+inf if none).
     """
     R = _c128(R)
     Z = _c128(Z)
@@ -151,10 +154,11 @@ def detect(R, Z, perm, paths, sigma2: float, qam: int, want_all: bool = False):
     margin = np.zeros(n_sym, np.float64)
     ped_all = np.zeros((n_sym, n_pe), np.float64) if want_all else None
     sym_all = np.zeros((n_sym, n_pe, nt), np.uint8) if want_all else None
+    flip = np.zeros(n_sym, np.float64)
     _check(_load().orc_detect(nt, qam, n_sym, _p(R), _p(Z), _p(perm), n_pe, _p(paths),
                               float(sigma2), _p(hard), _p(llr), _p(ped2), _p(margin),
-                              _p(ped_all), _p(sym_all)), "detect")
-    out = dict(hard=hard, llr=llr, ped2=ped2, margin=margin)
+                              _p(ped_all), _p(sym_all), float(tie_eps), _p(flip)), "detect")
+    out = dict(hard=hard, llr=llr, ped2=ped2, margin=margin, flip_floor=flip)
     if want_all:
         out["ped_all"] = ped_all
         out["sym_all"] = sym_all
@@ -178,7 +182,7 @@ def mmse(H, Y, sigma2: float, qam: int):
 
 
 def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, paths=None, n_threads: int = 0,
-                with_mmse: bool = False):
+                with_mmse: bool = False, tie_eps: float = 0.0):
     """Steps 1-6 (and 7 with ``with_mmse``) over a whole slot.
 
     H: [n_sc][nr][nt], Y: [n_sc][n_sym][nr] (any complex dtype; promoted to
@@ -202,13 +206,14 @@ def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, paths=None, n_threads:
     mh = np.zeros((n_sc, n_sym, nt), np.uint8) if with_mmse else None
     ml = np.zeros((n_sc, n_sym, nt, B), np.float64) if with_mmse else None
     pin = None if paths is None else np.ascontiguousarray(np.asarray(paths, np.uint8))
+    flip = np.zeros((n_sc, n_sym), np.float64)
     st = _load().orc_detect_slot(n_sc, n_sym, nr, nt, qam, n_pe, float(sigma2), _p(H), _p(Y),
                                  _p(pin), _p(hard), _p(llr), _p(ped2), _p(R), _p(perm), _p(Z),
                                  _p(paths_out), _p(gap), _p(margin), _p(mh), _p(ml),
-                                 int(n_threads))
+                                 int(n_threads), float(tie_eps), _p(flip))
     _check(st, "detect_slot")
     out = dict(hard=hard, llr=llr, ped2=ped2, R=R, perm=perm, Z=Z, paths=paths_out,
-               sqrd_gap=gap, margin=margin, threads=st)
+               sqrd_gap=gap, margin=margin, flip_floor=flip, threads=st)
     if with_mmse:
         out["mmse_hard"] = mh
         out["mmse_llr"] = ml

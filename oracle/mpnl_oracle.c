@@ -353,14 +353,17 @@ int orc_select_paths(int nt, int qam, const double *rdiag, double sigma2, int n_
  * llr [n_sym][nt][B] (user order, bit b0 first), ped2 [n_sym][2] (best and
  * runner-up d; runner-up +inf when n_pe == 1), margin [n_sym] (optional:
  * smallest gap, in constellation distance units, between the chosen point
- * and its neighbours in any ranking of that symbol -- a near-tie detector for
- * the tests), ped_all [n_sym][n_pe] (optional), sym_all [n_sym][n_pe][nt]
- * (optional: labels of every walk, detection order).
+ * and its neighbours in any ranking of that symbol), ped_all [n_sym][n_pe]
+ * (optional), sym_all [n_sym][n_pe][nt] (optional: labels of every walk,
+ * detection order), flip_floor [n_sym] (optional: over all rankings whose
+ * neighbour gap is below tie_eps, the smallest partial PED through that
+ * level; +inf if none).  margin and flip_floor are diagnostics for the tests:
+ * they do not change any result.
  * ------------------------------------------------------------------------- */
 static int detect_sc(int nt, int qam, int n_sym, const cplx *R, const cplx *Z, const int *perm,
                      int n_pe, const unsigned char *paths, double sigma2, unsigned char *hard,
                      double *llr, double *ped2, double *margin, double *ped_all,
-                     unsigned char *sym_all)
+                     unsigned char *sym_all, double tie_eps, double *flip_floor)
 {
     int M = qam, B = bits_of(qam);
     cplx pts[ORC_MAX_M];
@@ -375,7 +378,7 @@ static int detect_sc(int nt, int qam, int n_sym, const cplx *R, const cplx *Z, c
     }
     for (int s = 0; s < n_sym; s++) {
         const cplx *z = Z + (size_t)s * nt;
-        double mg = INFINITY;
+        double mg = INFINITY, ff = INFINITY;
         for (int row = 0; row < n_pe; row++) {
             const unsigned char *p = paths + (size_t)row * nt;
             cplx sv[ORC_MAX_NT];
@@ -406,13 +409,24 @@ static int detect_sc(int nt, int qam, int n_sym, const cplx *R, const cplx *Z, c
                 }
                 int k = p[l] - 1;
                 int q = order[k];
+                double gk = INFINITY;
                 if (k > 0) {
                     double g = sqrt(dist[q]) - sqrt(dist[order[k - 1]]);
-                    if (g < mg) mg = g;
+                    if (g < gk) gk = g;
                 }
                 if (k + 1 < M) {
                     double g = sqrt(dist[order[k + 1]]) - sqrt(dist[q]);
-                    if (g < mg) mg = g;
+                    if (g < gk) gk = g;
+                }
+                if (gk < mg) mg = gk;
+                /* a ranking this close to a tie may resolve the other way in
+                 * lower precision; such a walk keeps at least its PED up to
+                 * and including this level (the nearer candidate's term) */
+                if (gk < tie_eps) {
+                    double dn = dist[q];
+                    if (k > 0 && dist[order[k - 1]] < dn) dn = dist[order[k - 1]];
+                    double part = dd + rll * rll * dn;
+                    if (part < ff) ff = part;
                 }
                 sv[l] = pts[q];
                 lab[(size_t)row * nt + l] = (unsigned char)q;
@@ -421,6 +435,7 @@ static int detect_sc(int nt, int qam, int n_sym, const cplx *R, const cplx *Z, c
             d[row] = dd;
         }
         if (margin) margin[s] = mg;
+        if (flip_floor) flip_floor[s] = ff;
         if (ped_all) memcpy(ped_all + (size_t)s * n_pe, d, (size_t)n_pe * sizeof(double));
         if (sym_all) memcpy(sym_all + (size_t)s * n_pe * nt, lab, (size_t)n_pe * nt);
 
@@ -461,7 +476,8 @@ static int detect_sc(int nt, int qam, int n_sym, const cplx *R, const cplx *Z, c
 
 int orc_detect(int nt, int qam, int n_sym, const double *R, const double *Z, const int *perm,
                int n_pe, const unsigned char *paths, double sigma2, unsigned char *hard, double *llr,
-               double *ped2, double *margin, double *ped_all, unsigned char *sym_all)
+               double *ped2, double *margin, double *ped_all, unsigned char *sym_all,
+               double tie_eps, double *flip_floor)
 {
     if (nt < 1 || nt > ORC_MAX_NT || !bits_of(qam) || n_pe < 1 || n_pe > ORC_MAX_NPE) return -1;
     for (int row = 0; row < n_pe; row++)
@@ -470,7 +486,7 @@ int orc_detect(int nt, int qam, int n_sym, const double *R, const double *Z, con
             if (v < 1 || v > qam) return -1;
         }
     return detect_sc(nt, qam, n_sym, (const cplx *)R, (const cplx *)Z, perm, n_pe, paths, sigma2,
-                     hard, llr, ped2, margin, ped_all, sym_all);
+                     hard, llr, ped2, margin, ped_all, sym_all, tie_eps, flip_floor);
 }
 
 /* ---------------------------------------------------------------------------
@@ -588,7 +604,8 @@ int orc_mmse(int nr, int nt, int qam, int n_sym, const double *H, const double *
  * it replaces step 3 ([n_sc][n_pe][nt]).  Outputs (all optional except hard,
  * llr, ped2): R [n_sc][nt][nt], perm [n_sc][nt], Z [n_sc][n_sym][nt],
  * paths_out [n_sc][n_pe][nt], sqrd_gap [n_sc][nt], margin [n_sc][n_sym],
- * mmse_hard [n_sc][n_sym][nt], mmse_llr [n_sc][n_sym][nt][B].
+ * mmse_hard [n_sc][n_sym][nt], mmse_llr [n_sc][n_sym][nt][B],
+ * flip_floor [n_sc][n_sym] (with tie_eps, as for orc_detect).
  * Returns the number of threads used (>0) or a negative error.
  * ------------------------------------------------------------------------- */
 typedef struct {
@@ -596,7 +613,8 @@ typedef struct {
     double sigma2;
     const double *H, *Y;
     const unsigned char *paths_in;
-    double *R, *Z, *ped2, *llr, *sqrd_gap, *margin, *mmse_llr;
+    double *R, *Z, *ped2, *llr, *sqrd_gap, *margin, *mmse_llr, *flip_floor;
+    double tie_eps;
     int *perm;
     unsigned char *paths_out, *hard, *mmse_hard;
     int sc_begin, sc_end;
@@ -639,7 +657,8 @@ static void *slot_worker(void *arg)
         int st = detect_sc(nt, j->qam, ns, R, Z, perm, npe, pt, j->sigma2,
                            j->hard + (size_t)sc * ns * nt, j->llr + (size_t)sc * ns * nt * B,
                            j->ped2 + (size_t)sc * ns * 2,
-                           j->margin ? j->margin + (size_t)sc * ns : NULL, NULL, NULL);
+                           j->margin ? j->margin + (size_t)sc * ns : NULL, NULL, NULL,
+                           j->tie_eps, j->flip_floor ? j->flip_floor + (size_t)sc * ns : NULL);
         if (st) {
             j->status = st;
             goto out;
@@ -670,7 +689,8 @@ int orc_detect_slot(int n_sc, int n_sym, int nr, int nt, int qam, int n_pe, doub
                     const double *H, const double *Y, const unsigned char *paths_in,
                     unsigned char *hard, double *llr, double *ped2, double *R, int *perm, double *Z,
                     unsigned char *paths_out, double *sqrd_gap, double *margin,
-                    unsigned char *mmse_hard, double *mmse_llr, int n_threads)
+                    unsigned char *mmse_hard, double *mmse_llr, int n_threads, double tie_eps,
+                    double *flip_floor)
 {
     if (n_sc < 0 || n_sym < 1 || nt < 1 || nt > ORC_MAX_NT || nr < nt || nr > ORC_MAX_NR ||
         !bits_of(qam) || n_pe < 1 || n_pe > ORC_MAX_NPE || !(sigma2 > 0.0))
@@ -711,6 +731,8 @@ int orc_detect_slot(int n_sc, int n_sym, int nr, int nt, int qam, int n_pe, doub
         j->paths_out = paths_out;
         j->hard = hard;
         j->mmse_hard = mmse_hard;
+        j->tie_eps = tie_eps;
+        j->flip_floor = flip_floor;
         j->sc_begin = (int)((long)n_sc * t / n_threads);
         j->sc_end = (int)((long)n_sc * (t + 1) / n_threads);
     }

@@ -1,0 +1,30 @@
+// Internal launcher interface between the C ABI (mpnl_api.cu) and the kernel
+// translation units.  Each launcher validates nothing (the ABI layer did),
+// enqueues its kernel(s) on `stream` and returns cudaGetLastError().
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mpnl {
+
+cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, const float2 *H,
+                              const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,
+                              float2 *Z, cudaStream_t stream);
+
+cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,
+                                const float2 *R, uint8_t *paths, cudaStream_t stream);
+
+cudaError_t launch_detect(int n_sc, int n_sym, int nt, int qam, int n_pe, float sigma2,
+                          const float2 *R, const float *inv_diag, const uint8_t *perm,
+                          const uint8_t *paths, const float2 *Z, uint8_t *hard, float *llr,
+                          float *ped2, unsigned *status, cudaStream_t stream);
+
+cudaError_t launch_mmse(int n_sc, int n_sym, int nr, int nt, int qam, float sigma2,
+                        const float2 *H, const float2 *Y, uint8_t *hard, float *llr,
+                        cudaStream_t stream);
+
+// Device status bits (mpnl_check_status).
+constexpr unsigned kStatusBadPathEntry = 1u;
+
+}  // namespace mpnl

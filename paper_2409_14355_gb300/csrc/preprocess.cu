@@ -1,0 +1,220 @@
+// Channel pre-processing: sorted QR (SQRD) of H and z = Q^H y, one warp per
+// subcarrier.
+//
+// The warp factorises the augmented matrix [H | y_0 ... y_{n_sym-1}] by
+// modified Gram-Schmidt: lane c owns column c (columns nt.. are the received
+// symbol vectors).  At step i the not-yet-placed channel column with the
+// smallest residual norm is picked (tie: lower user index), normalised into
+// q_i, and every remaining column -- channel or symbol -- is projected:
+// r = q_i^H col, col -= r q_i.  For a channel column r is R_i,col; for a
+// symbol column r is z_i = q_i^H y (exact arithmetic gives the same value as
+// Q^H y, and Q never has to be stored).  The 14 symbols sharing one channel
+// ride along as 14 extra lanes, so Q^H Y costs no extra pass.
+//
+// H and Y tiles are staged through shared memory with coalesced 8-byte loads;
+// the pivot column is broadcast through shared memory.
+#include <float.h>
+
+#include "mpnl_common.cuh"
+#include "mpnl_internal.h"
+
+namespace mpnl {
+namespace {
+
+constexpr int kWarpsPerCta = 4;
+
+struct WarpSmem {
+    int off_h, off_y, off_q, off_rt, off_z, off_rd, off_perm, bytes;
+};
+
+__host__ __device__ inline WarpSmem warp_smem_layout(int nr, int nt, int n_sym)
+{
+    WarpSmem s;
+    int o = 0;
+    s.off_h = o;
+    o += nr * nt * 8;
+    s.off_y = o;
+    o += n_sym * nr * 8;
+    s.off_q = o;
+    o += nr * 8;
+    s.off_rt = o;
+    o += nt * nt * 8;
+    s.off_z = o;
+    o += n_sym * nt * 8;
+    s.off_rd = o;
+    o += nt * 4;
+    s.off_perm = o;
+    o += nt * 4;
+    s.bytes = (o + 15) & ~15;
+    return s;
+}
+
+template <int NR, int CS>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ H,
+                const float2 *__restrict__ Y, float2 *__restrict__ Rp,
+                float *__restrict__ inv_diag, uint8_t *__restrict__ perm_out,
+                float2 *__restrict__ Z)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int sc = blockIdx.x * kWarpsPerCta + warp;
+    if (sc >= n_sc) return;  // only __syncwarp below: per-warp early exit is safe
+
+    const WarpSmem L = warp_smem_layout(nr, nt, n_sym);
+    unsigned char *base = smem_raw + warp * L.bytes;
+    float2 *sH = reinterpret_cast<float2 *>(base + L.off_h);
+    float2 *sY = reinterpret_cast<float2 *>(base + L.off_y);
+    float2 *sQ = reinterpret_cast<float2 *>(base + L.off_q);
+    float2 *sRt = reinterpret_cast<float2 *>(base + L.off_rt);
+    float2 *sZ = reinterpret_cast<float2 *>(base + L.off_z);
+    float *sRd = reinterpret_cast<float *>(base + L.off_rd);
+    int *sPerm = reinterpret_cast<int *>(base + L.off_perm);
+
+    // coalesced staging of this subcarrier's H and Y tiles
+    const float2 *gH = H + (size_t)sc * nr * nt;
+    const float2 *gY = Y + (size_t)sc * n_sym * nr;
+    for (int k = lane; k < nr * nt; k += 32) sH[k] = gH[k];
+    for (int k = lane; k < n_sym * nr; k += 32) sY[k] = gY[k];
+    __syncwarp();
+
+    const int ncols = nt + n_sym;
+    float2 col[CS][NR];
+#pragma unroll
+    for (int cs = 0; cs < CS; ++cs) {
+        const int c = lane + 32 * cs;
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            float2 v = make_float2(0.f, 0.f);
+            if (r < nr) {
+                if (c < nt) v = sH[r * nt + c];
+                else if (c < ncols) v = sY[(c - nt) * nr + r];
+            }
+            col[cs][r] = v;
+        }
+    }
+    // channel columns are always slot 0, lanes 0..nt-1 (nt <= 16)
+    bool placed = !(lane < nt);
+
+    for (int i = 0; i < nt; ++i) {
+        // placed (or absent) columns carry +inf, live ones a finite key (a NaN
+        // norm maps to FLT_MAX), so every lane agrees on the pivot
+        float nrm = INFINITY;
+        if (!placed) {
+            float s = 0.f;
+#pragma unroll
+            for (int r = 0; r < NR; ++r) s = fmaf(col[0][r].x, col[0][r].x, fmaf(col[0][r].y, col[0][r].y, s));
+            nrm = (s <= FLT_MAX) ? s : FLT_MAX;
+        }
+        // warp argmin of (norm, user index)
+        float bn = nrm;
+        int bl = lane;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            float on = __shfl_xor_sync(0xffffffffu, bn, o);
+            int ol = __shfl_xor_sync(0xffffffffu, bl, o);
+            if (on < bn || (on == bn && ol < bl)) {
+                bn = on;
+                bl = ol;
+            }
+        }
+        const int piv = bl;
+        const float rii = sqrtf(bn);
+        if (lane == piv) {
+            const float inv = 1.0f / rii;
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+                if (r < nr) sQ[r] = make_float2(col[0][r].x * inv, col[0][r].y * inv);
+            sRd[i] = rii;
+            sPerm[i] = piv;
+            placed = true;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int cs = 0; cs < CS; ++cs) {
+            const int c = lane + 32 * cs;
+            // channel columns not yet placed (the pivot was placed just above),
+            // and every symbol column
+            const bool use = (c < nt) ? !placed : (c < ncols);
+            if (use) {
+                float ax = 0.f, ay = 0.f;  // q^H col
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (r < nr) {
+                        const float2 q = sQ[r];
+                        ax = fmaf(q.x, col[cs][r].x, fmaf(q.y, col[cs][r].y, ax));
+                        ay = fmaf(q.x, col[cs][r].y, fmaf(-q.y, col[cs][r].x, ay));
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < NR; ++r) {
+                    if (r < nr) {
+                        const float2 q = sQ[r];
+                        col[cs][r].x -= ax * q.x - ay * q.y;
+                        col[cs][r].y -= ax * q.y + ay * q.x;
+                    }
+                }
+                if (c < nt) sRt[i * nt + c] = make_float2(ax, ay);
+                else sZ[(c - nt) * nt + i] = make_float2(ax, ay);
+            }
+        }
+        __syncwarp();
+    }
+
+    // packed R (row-major upper triangle), 1/R_ll, perm, Z
+    const int P = nt * (nt + 1) / 2;
+    float2 *gR = Rp + (size_t)sc * P;
+    for (int k = lane; k < P; k += 32) {
+        int i = 0, rem = k;
+        while (rem >= nt - i) {
+            rem -= nt - i;
+            ++i;
+        }
+        const int j = i + rem;
+        gR[k] = (j == i) ? make_float2(sRd[i], 0.f) : sRt[i * nt + sPerm[j]];
+    }
+    if (lane < nt) {
+        inv_diag[(size_t)sc * nt + lane] = 1.0f / sRd[lane];
+        perm_out[(size_t)sc * nt + lane] = (uint8_t)sPerm[lane];
+    }
+    float2 *gZ = Z + (size_t)sc * n_sym * nt;
+    for (int k = lane; k < n_sym * nt; k += 32) gZ[k] = sZ[k];
+}
+
+template <int NR, int CS>
+cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, const float2 *H, const float2 *Y,
+                       float2 *R, float *inv_diag, uint8_t *perm, float2 *Z, cudaStream_t stream)
+{
+    const WarpSmem L = warp_smem_layout(nr, nt, n_sym);
+    const size_t smem = (size_t)L.bytes * kWarpsPerCta;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sqrd_qhy_kernel<NR, CS>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = (n_sc + kWarpsPerCta - 1) / kWarpsPerCta;
+    sqrd_qhy_kernel<NR, CS><<<grid, kWarpsPerCta * 32, smem, stream>>>(n_sc, n_sym, nr, nt, H, Y, R,
+                                                                       inv_diag, perm, Z);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, const float2 *H,
+                              const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,
+                              float2 *Z, cudaStream_t stream)
+{
+    if (n_sc == 0) return cudaSuccess;
+    const bool two = nt + n_sym > 32;
+#define MPNL_PRE(NRV)                                                                         \
+    return two ? launch_tpl<NRV, 2>(n_sc, n_sym, nr, nt, H, Y, R, inv_diag, perm, Z, stream)  \
+               : launch_tpl<NRV, 1>(n_sc, n_sym, nr, nt, H, Y, R, inv_diag, perm, Z, stream)
+    if (nr <= 4) MPNL_PRE(4);
+    if (nr <= 8) MPNL_PRE(8);
+    if (nr <= 16) MPNL_PRE(16);
+    MPNL_PRE(32);
+#undef MPNL_PRE
+}
+
+}  // namespace mpnl

@@ -1,0 +1,219 @@
+// Position-vector pre-selection, one CTA per subcarrier.
+//
+// Each level l gets a cost weight w_l = -log Pe_l from its SNR
+// gamma_l = R_ll^2 / sigma2 (square-QAM symbol-error rate, floored); with the
+// geometric rank model P_l(k) = (1 - Pe_l) Pe_l^(k-1) the log-probability of
+// a vector p is a constant minus cost(p) = sum_l (p_l - 1) w_l.  The N_pe
+// vectors of smallest cost (ties: lexicographically smaller from level nt-1
+// down) are the N_pe most probable ones, in the order a best-first search
+// would pop them.
+//
+// Instead of a sequential priority queue the CTA builds the answer level by
+// level with sorted merges, all in shared memory:
+//   L := [ all-ones ]                                  (cost 0)
+//   for each level m (top first):
+//     B := L
+//     for j = 1, 2, ...:  B := first N_pe of merge(B, L shifted by j at level m)
+//       (the shifted list adds j w_m to every cost and sets p_m = 1 + j; it
+//        stays sorted, and once its first entry sorts after B's last entry no
+//        later shift can contribute, so the loop stops there)
+//     L := B
+// Truncating to N_pe after every level is exact: a vector in the final top
+// N_pe has its restriction to the levels seen so far (ones elsewhere) ahead of
+// it in the order, so that restriction is in the partial top N_pe.
+// Each merge places every element by a binary search in the other list
+// (merge path), so all threads work at once.
+//
+// A vector is keyed by 16 bytes (two u64, level nt-1 in the most significant
+// byte): comparing keys as unsigned integers is the lexicographic order from
+// the top level down, and the key bytes are the ranks written out.
+#include "mpnl_common.cuh"
+#include "mpnl_internal.h"
+
+namespace mpnl {
+namespace {
+
+__device__ __forceinline__ bool before(float ca, unsigned long long ha, unsigned long long la,
+                                       float cb, unsigned long long hb, unsigned long long lb)
+{
+    return ca < cb || (ca == cb && (ha < hb || (ha == hb && la < lb)));
+}
+
+// byte position of level l in the (hi, lo) key: top level first
+__device__ __forceinline__ void level_shift(int nt, int l, bool &in_hi, int &shift)
+{
+    const int t = nt - 1 - l;
+    in_hi = t < 8;
+    shift = in_hi ? 56 - 8 * t : 56 - 8 * (t - 8);
+}
+
+template <int QAM>
+__global__ void __launch_bounds__(256)
+select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
+                    uint8_t *__restrict__ paths)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int sc = blockIdx.x;
+    const int tid = threadIdx.x;
+    const int T = blockDim.x;
+
+    // three lists (struct of arrays): keys first for 8-byte alignment
+    unsigned long long *hi[3], *lo[3];
+    float *cost[3];
+    {
+        unsigned char *p = smem_raw;
+        for (int b = 0; b < 3; ++b) {
+            hi[b] = reinterpret_cast<unsigned long long *>(p);
+            p += (size_t)n_pe * 8;
+            lo[b] = reinterpret_cast<unsigned long long *>(p);
+            p += (size_t)n_pe * 8;
+        }
+        for (int b = 0; b < 3; ++b) {
+            cost[b] = reinterpret_cast<float *>(p);
+            p += (size_t)n_pe * 4;
+        }
+    }
+    __shared__ float w[kMaxNt];
+
+    const int P = nt * (nt + 1) / 2;
+    if (tid < nt) {
+        const int l = tid;
+        const float rll = Rp[(size_t)sc * P + l * nt - l * (l - 1) / 2].x;
+        const float gamma = rll * rll / sigma2;
+        const float x = sqrtf(3.0f * gamma / (float)(QAM - 1));
+        const float qf = 0.5f * erfcf(x * 0.70710678118654752f);
+        constexpr float c = 2.0f * (1.0f - 1.0f / (float)Qam<QAM>::L);  // 2 (1 - 1/sqrt(M))
+        const float cq = c * qf;
+        float pe = cq * (2.0f - cq);  // = 1 - (1 - cq)^2 without cancellation
+        pe = fmaxf(pe, kPeFloor);
+        w[l] = -logf(pe);
+    }
+    // L = [all ones]
+    int li = 0;
+    if (tid == 0) {
+        unsigned long long h = 0, o = 0;
+        for (int l = 0; l < nt; ++l) {
+            bool in_hi;
+            int sh;
+            level_shift(nt, l, in_hi, sh);
+            if (in_hi) h |= 1ull << sh;
+            else o |= 1ull << sh;
+        }
+        hi[0][0] = h;
+        lo[0][0] = o;
+        cost[0][0] = 0.f;
+    }
+    int nL = 1;
+    __syncthreads();
+
+    for (int m = nt - 1; m >= 0; --m) {
+        const float wm = w[m];
+        bool in_hi;
+        int sh;
+        level_shift(nt, m, in_hi, sh);
+        int bi = li, nB = nL;          // B starts as L itself (read only)
+        int oi = (li + 1) % 3;         // first output buffer
+        for (int j = 1; j < QAM; ++j) {
+            const unsigned long long add = (unsigned long long)j << sh;
+            const float cj = (float)j * wm;
+            // first entry of the shifted list vs the last entry of B
+            {
+                const float c0 = cost[li][0] + cj;
+                const unsigned long long h0 = hi[li][0] + (in_hi ? add : 0ull);
+                const unsigned long long l0 = lo[li][0] + (in_hi ? 0ull : add);
+                if (nB == n_pe &&
+                    !before(c0, h0, l0, cost[bi][nB - 1], hi[bi][nB - 1], lo[bi][nB - 1]))
+                    break;
+            }
+            const int nOut = min(n_pe, nB + nL);
+            // elements of B: position = own index + #shifted entries before it
+            for (int a = tid; a < nB; a += T) {
+                const float ca = cost[bi][a];
+                const unsigned long long ha = hi[bi][a], la = lo[bi][a];
+                int lo_i = 0, hi_i = nL;  // count shifted entries strictly before a
+                while (lo_i < hi_i) {
+                    const int mid = (lo_i + hi_i) >> 1;
+                    const float cm = cost[li][mid] + cj;
+                    const unsigned long long hm = hi[li][mid] + (in_hi ? add : 0ull);
+                    const unsigned long long lm = lo[li][mid] + (in_hi ? 0ull : add);
+                    if (before(cm, hm, lm, ca, ha, la)) lo_i = mid + 1;
+                    else hi_i = mid;
+                }
+                const int pos = a + lo_i;
+                if (pos < nOut) {
+                    cost[oi][pos] = ca;
+                    hi[oi][pos] = ha;
+                    lo[oi][pos] = la;
+                }
+            }
+            // elements of the shifted list
+            for (int a = tid; a < nL; a += T) {
+                const float ca = cost[li][a] + cj;
+                const unsigned long long ha = hi[li][a] + (in_hi ? add : 0ull);
+                const unsigned long long la = lo[li][a] + (in_hi ? 0ull : add);
+                if (a >= nOut) continue;
+                int lo_i = 0, hi_i = nB;  // count B entries strictly before it
+                while (lo_i < hi_i) {
+                    const int mid = (lo_i + hi_i) >> 1;
+                    if (before(cost[bi][mid], hi[bi][mid], lo[bi][mid], ca, ha, la)) lo_i = mid + 1;
+                    else hi_i = mid;
+                }
+                const int pos = a + lo_i;
+                if (pos < nOut) {
+                    cost[oi][pos] = ca;
+                    hi[oi][pos] = ha;
+                    lo[oi][pos] = la;
+                }
+            }
+            __syncthreads();
+            nB = nOut;
+            // next output goes to the buffer that is neither L nor the new B
+            bi = oi;
+            oi = 3 - li - bi;
+        }
+        li = bi;
+        nL = nB;
+        __syncthreads();
+    }
+
+    // write the table: row r, level l -> byte of the key
+    uint8_t *out = paths + (size_t)sc * n_pe * nt;
+    for (int k = tid; k < n_pe * nt; k += T) {
+        const int r = k / nt, l = k - r * nt;
+        bool in_hi;
+        int sh;
+        level_shift(nt, l, in_hi, sh);
+        const unsigned long long v = in_hi ? hi[li][r] : lo[li][r];
+        out[k] = (uint8_t)((v >> sh) & 0xffull);
+    }
+}
+
+template <int QAM>
+cudaError_t launch_tpl(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
+                       uint8_t *paths, cudaStream_t stream)
+{
+    const size_t smem = (size_t)n_pe * 60;  // 3 lists x (8 + 8 + 4) bytes
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(select_paths_kernel<QAM>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int threads = n_pe >= 256 ? 256 : (n_pe >= 128 ? 128 : (n_pe >= 64 ? 64 : 32));
+    select_paths_kernel<QAM><<<n_sc, threads, smem, stream>>>(nt, n_pe, sigma2, R, paths);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,
+                                const float2 *R, uint8_t *paths, cudaStream_t stream)
+{
+    if (n_sc == 0) return cudaSuccess;
+    switch (qam) {
+    case 4: return launch_tpl<4>(n_sc, nt, n_pe, sigma2, R, paths, stream);
+    case 16: return launch_tpl<16>(n_sc, nt, n_pe, sigma2, R, paths, stream);
+    default: return launch_tpl<64>(n_sc, nt, n_pe, sigma2, R, paths, stream);
+    }
+}
+
+}  // namespace mpnl

@@ -1,0 +1,290 @@
+"""Python binding of libmpnl.so (include/mpnl.h): argument marshalling only.
+
+Every step of the detection path runs in the CUDA kernels behind the C ABI;
+this module allocates output tensors with PyTorch, passes raw device
+pointers and the current CUDA stream, and turns error codes into
+exceptions.  There is no CPU fallback: if the library is missing or no GPU is
+present, every call raises.
+
+Layouts (complex = torch.complex64, interleaved re/im float32):
+  H [n_sc][nr][nt], Y [n_sc][n_sym][nr]          inputs
+  R [n_sc][nt(nt+1)/2] packed upper triangle     preprocess output
+  inv_diag f32 [n_sc][nt], perm u8 [n_sc][nt], Z [n_sc][n_sym][nt]
+  paths u8 [n_sc][n_pe][nt] (ranks 1..qam)
+  hard u8 [n_sc][n_sym][nt], llr f32 [n_sc][n_sym][nt][log2 qam],
+  ped2 f32 [n_sc][n_sym][2]
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libmpnl.so")
+BITS = {4: 2, 16: 4, 64: 6}
+LLR_MAX = 20.0
+MAX_NT, MAX_NR, MAX_NSYM, MAX_NPE = 16, 32, 32, 1024
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_UNSUPPORTED = -2
+ERR_CUDA = -3
+ERR_TIMEOUT = -4
+
+EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_bytes",
+            "mpnl_preprocess", "mpnl_select_paths", "mpnl_detect", "mpnl_linear_mmse",
+            "mpnl_check_status")
+
+
+class MpnlError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mpnl error {code}: {msg}")
+        self.code = code
+
+
+class Dims(ctypes.Structure):
+    _fields_ = [("n_sc", ctypes.c_int), ("n_sym", ctypes.c_int), ("nr", ctypes.c_int),
+                ("nt", ctypes.c_int), ("qam", ctypes.c_int), ("n_pe", ctypes.c_int)]
+
+
+_lib = None
+_lib_lock = threading.Lock()
+_ctxs: dict[int, ctypes.c_void_p] = {}
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libmpnl.so and declare its signatures (no GPU needed)."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise MpnlError(ERR_CUDA, f"{path} not built: run paper_2409_14355_gb300.build.build()")
+        lib = ctypes.CDLL(path)
+        P, I, F, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_size_t
+        D = ctypes.POINTER(Dims)
+        lib.mpnl_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), I]
+        lib.mpnl_create.restype = I
+        lib.mpnl_destroy.argtypes = [P]
+        lib.mpnl_destroy.restype = None
+        lib.mpnl_last_error.argtypes = [P]
+        lib.mpnl_last_error.restype = ctypes.c_char_p
+        lib.mpnl_workspace_bytes.argtypes = [D]
+        lib.mpnl_workspace_bytes.restype = S
+        lib.mpnl_preprocess.argtypes = [P, D, P, P, P, P, P, P, P, P]
+        lib.mpnl_preprocess.restype = I
+        lib.mpnl_select_paths.argtypes = [P, D, P, F, P, P, P]
+        lib.mpnl_select_paths.restype = I
+        lib.mpnl_detect.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
+        lib.mpnl_detect.restype = I
+        lib.mpnl_linear_mmse.argtypes = [P, D, P, P, F, P, P, P, P]
+        lib.mpnl_linear_mmse.restype = I
+        lib.mpnl_check_status.argtypes = [P, P]
+        lib.mpnl_check_status.restype = I
+        _lib = lib
+        return lib
+
+
+def context(device: int | None = None) -> ctypes.c_void_p:
+    """The per-device mpnl_ctx (created on first use, kept for the process)."""
+    lib = load_library()
+    if not torch.cuda.is_available():
+        raise MpnlError(ERR_CUDA, "no CUDA device: the MPNL path has no CPU fallback")
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _ctxs:
+        h = ctypes.c_void_p()
+        st = lib.mpnl_create(ctypes.byref(h), dev)
+        if st != OK:
+            raise MpnlError(st, f"mpnl_create(device={dev}) failed")
+        _ctxs[dev] = h
+    return _ctxs[dev]
+
+
+def _raise(st: int, ctx) -> None:
+    if st != OK:
+        msg = load_library().mpnl_last_error(ctx).decode(errors="replace")
+        raise MpnlError(st, msg)
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t) -> ctypes.c_void_p | None:
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dev_of(t: torch.Tensor) -> torch.device:
+    if t.device.type != "cuda":
+        raise MpnlError(ERR_INVALID_ARG, "tensor must live on a CUDA device")
+    return t.device
+
+
+def _need(t: torch.Tensor, dtype, shape, name):
+    if t.dtype != dtype:
+        raise MpnlError(ERR_INVALID_ARG, f"{name}: dtype {t.dtype}, expected {dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise MpnlError(ERR_INVALID_ARG, f"{name}: shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if not t.is_contiguous():
+        raise MpnlError(ERR_INVALID_ARG, f"{name}: must be contiguous")
+
+
+def workspace_bytes(n_sc, n_sym, nr, nt, qam, n_pe) -> int:
+    d = Dims(n_sc, n_sym, nr, nt, qam, n_pe)
+    return int(load_library().mpnl_workspace_bytes(ctypes.byref(d)))
+
+
+def preprocess(H: torch.Tensor, Y: torch.Tensor, out=None):
+    """Sorted QR + z = Q^H y.  Returns (R, inv_diag, perm, Z)."""
+    dev = _dev_of(H)
+    n_sc, nr, nt = H.shape
+    n_sym = Y.shape[1]
+    _need(H, torch.complex64, (n_sc, nr, nt), "H")
+    _need(Y, torch.complex64, (n_sc, n_sym, nr), "Y")
+    if out is None:
+        R = torch.empty((n_sc, nt * (nt + 1) // 2), dtype=torch.complex64, device=dev)
+        inv_diag = torch.empty((n_sc, nt), dtype=torch.float32, device=dev)
+        perm = torch.empty((n_sc, nt), dtype=torch.uint8, device=dev)
+        Z = torch.empty((n_sc, n_sym, nt), dtype=torch.complex64, device=dev)
+    else:
+        R, inv_diag, perm, Z = out
+    ctx = context(dev.index)
+    d = Dims(n_sc, n_sym, nr, nt, 4, 1)
+    st = load_library().mpnl_preprocess(ctx, ctypes.byref(d), _ptr(H), _ptr(Y), _ptr(R),
+                                        _ptr(inv_diag), _ptr(perm), _ptr(Z), None, _stream(dev))
+    _raise(st, ctx)
+    return R, inv_diag, perm, Z
+
+
+def select_paths(R: torch.Tensor, sigma2: float, qam: int, n_pe: int, nt: int, out=None):
+    """Position-vector table u8 [n_sc][n_pe][nt] from the R diagonal."""
+    dev = _dev_of(R)
+    n_sc = R.shape[0]
+    _need(R, torch.complex64, (n_sc, nt * (nt + 1) // 2), "R")
+    paths = out if out is not None else torch.empty((n_sc, n_pe, nt), dtype=torch.uint8, device=dev)
+    ctx = context(dev.index)
+    d = Dims(n_sc, 1, nt, nt, qam, n_pe)
+    st = load_library().mpnl_select_paths(ctx, ctypes.byref(d), _ptr(R), float(sigma2),
+                                          _ptr(paths), None, _stream(dev))
+    _raise(st, ctx)
+    return paths
+
+
+def detect(R, inv_diag, perm, paths, Z, sigma2: float, qam: int, want_llr: bool = True,
+           want_ped2: bool = True, out=None):
+    """Walks + argmin + max-log LLRs.  Returns (hard, llr or None, ped2 or None)."""
+    dev = _dev_of(R)
+    n_sc, n_sym, nt = Z.shape
+    n_pe = paths.shape[1]
+    B = BITS[qam]
+    _need(R, torch.complex64, (n_sc, nt * (nt + 1) // 2), "R")
+    _need(inv_diag, torch.float32, (n_sc, nt), "inv_diag")
+    _need(perm, torch.uint8, (n_sc, nt), "perm")
+    _need(paths, torch.uint8, (n_sc, n_pe, nt), "paths")
+    _need(Z, torch.complex64, (n_sc, n_sym, nt), "Z")
+    if out is None:
+        hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, device=dev)
+        llr = torch.empty((n_sc, n_sym, nt, B), dtype=torch.float32, device=dev) if want_llr else None
+        ped2 = torch.empty((n_sc, n_sym, 2), dtype=torch.float32, device=dev) if want_ped2 else None
+    else:
+        hard, llr, ped2 = out
+    ctx = context(dev.index)
+    d = Dims(n_sc, n_sym, nt, nt, qam, n_pe)
+    st = load_library().mpnl_detect(ctx, ctypes.byref(d), _ptr(R), _ptr(inv_diag), _ptr(perm),
+                                    _ptr(paths), _ptr(Z), float(sigma2), _ptr(hard), _ptr(llr),
+                                    _ptr(ped2), None, _stream(dev))
+    _raise(st, ctx)
+    return hard, llr, ped2
+
+
+def linear_mmse(H, Y, sigma2: float, qam: int, want_llr: bool = True, out=None):
+    """Linear MMSE baseline.  Returns (hard, llr or None)."""
+    dev = _dev_of(H)
+    n_sc, nr, nt = H.shape
+    n_sym = Y.shape[1]
+    B = BITS[qam]
+    _need(H, torch.complex64, (n_sc, nr, nt), "H")
+    _need(Y, torch.complex64, (n_sc, n_sym, nr), "Y")
+    if out is None:
+        hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, device=dev)
+        llr = torch.empty((n_sc, n_sym, nt, B), dtype=torch.float32, device=dev) if want_llr else None
+    else:
+        hard, llr = out
+    ctx = context(dev.index)
+    d = Dims(n_sc, n_sym, nr, nt, qam, 1)
+    st = load_library().mpnl_linear_mmse(ctx, ctypes.byref(d), _ptr(H), _ptr(Y), float(sigma2),
+                                         _ptr(hard), _ptr(llr), None, _stream(dev))
+    _raise(st, ctx)
+    return hard, llr
+
+
+def check_status(device: int | None = None) -> None:
+    """Synchronise the current stream and raise on device-side argument errors."""
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    ctx = context(dev.index)
+    _raise(load_library().mpnl_check_status(ctx, _stream(dev)), ctx)
+
+
+class SlotBuffers:
+    """Device buffers for one slot of a given size, reused across calls."""
+
+    def __init__(self, n_sc, n_sym, nr, nt, qam, n_pe, device, mmse: bool = True):
+        B = BITS[qam]
+        kw = dict(device=device)
+        self.dims = (n_sc, n_sym, nr, nt, qam, n_pe)
+        self.H = torch.empty((n_sc, nr, nt), dtype=torch.complex64, **kw)
+        self.Y = torch.empty((n_sc, n_sym, nr), dtype=torch.complex64, **kw)
+        self.R = torch.empty((n_sc, nt * (nt + 1) // 2), dtype=torch.complex64, **kw)
+        self.inv_diag = torch.empty((n_sc, nt), dtype=torch.float32, **kw)
+        self.perm = torch.empty((n_sc, nt), dtype=torch.uint8, **kw)
+        self.Z = torch.empty((n_sc, n_sym, nt), dtype=torch.complex64, **kw)
+        self.paths = torch.empty((n_sc, n_pe, nt), dtype=torch.uint8, **kw)
+        self.hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, **kw)
+        self.llr = torch.empty((n_sc, n_sym, nt, B), dtype=torch.float32, **kw)
+        self.ped2 = torch.empty((n_sc, n_sym, 2), dtype=torch.float32, **kw)
+        self.mmse_hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, **kw) if mmse else None
+        self.mmse_llr = torch.empty((n_sc, n_sym, nt, B), dtype=torch.float32, **kw) if mmse else None
+
+
+def run_slot(buf: SlotBuffers, H, Y, sigma2: float, mmse: bool = True) -> None:
+    """The whole path on device tensors H, Y (enqueued on the current stream):
+    preprocess -> select_paths -> detect (hard, LLR, PED pair) [-> MMSE]."""
+    n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
+    preprocess(H, Y, out=(buf.R, buf.inv_diag, buf.perm, buf.Z))
+    select_paths(buf.R, sigma2, qam, n_pe, nt, out=buf.paths)
+    detect(buf.R, buf.inv_diag, buf.perm, buf.paths, buf.Z, sigma2, qam,
+           out=(buf.hard, buf.llr, buf.ped2))
+    if mmse:
+        linear_mmse(H, Y, sigma2, qam, out=(buf.mmse_hard, buf.mmse_llr))
+
+
+def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
+                buffers: SlotBuffers | None = None, device=None):
+    """End-to-end call a user makes: accepts host (ideally pinned) or device
+    tensors.  Host inputs are copied to the device, the path runs, and the
+    hard decisions and LLRs (and MMSE outputs with ``mmse``) come back as host
+    tensors.  Returns a dict."""
+    host = H.device.type == "cpu"
+    if device is None:
+        device = torch.device("cuda", torch.cuda.current_device()) if host else H.device
+    n_sc, nr, nt = H.shape
+    n_sym = Y.shape[1]
+    buf = buffers or SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, device, mmse)
+    if host:
+        buf.H.copy_(H, non_blocking=True)
+        buf.Y.copy_(Y, non_blocking=True)
+        Hd, Yd = buf.H, buf.Y
+    else:
+        Hd, Yd = H, Y
+    run_slot(buf, Hd, Yd, sigma2, mmse)
+    out = dict(hard=buf.hard, llr=buf.llr, ped2=buf.ped2)
+    if mmse:
+        out["mmse_hard"] = buf.mmse_hard
+        out["mmse_llr"] = buf.mmse_llr
+    if host:
+        out = {k: v.to("cpu", non_blocking=True) for k, v in out.items()}
+        torch.cuda.current_stream(device).synchronize()
+    return out
