@@ -169,7 +169,9 @@ def _stage_isolated(dev, nr, nt, qam, n_sc, snr_db, n_pe, channel="iid", seed=0,
 def test_detect_stage_isolated(dev, nr, nt, qam, n_sc, snr_db, n_pe, channel):
     sl, gpu, ref, R = _stage_isolated(dev, nr, nt, qam, n_sc, snr_db, n_pe, channel,
                                       seed=nr * 31 + n_pe)
-    P.compare_detect(gpu, ref, R, sl.sigma2, what=f"{nr}x{nt} q{qam} npe{n_pe}")
+    # the larger the list, the more rankings per detection come near a tie
+    P.compare_detect(gpu, ref, R, sl.sigma2, what=f"{nr}x{nt} q{qam} npe{n_pe}",
+                     min_frac=0.5 if n_pe < 1024 else 0.2)
 
 
 def test_detect_full_list_is_exhaustive_ml(dev):
@@ -216,8 +218,7 @@ def _end_to_end(dev, sl, n_pe, with_mmse=True):
     if with_mmse:
         g["mmse_hard"] = buf.mmse_hard.cpu().numpy()
         g["mmse_llr"] = buf.mmse_llr.cpu().numpy()
-    ref = oracle.detect_slot(sl.H, sl.Y, sl.sigma2, sl.qam, n_pe, with_mmse=with_mmse,
-                             tie_eps=P.TIE_EPS_E2E)
+    ref = P.e2e_reference(sl.H, sl.Y, sl.sigma2, sl.qam, n_pe, with_mmse=with_mmse)
     return g, ref
 
 
@@ -249,8 +250,7 @@ def test_end_to_end_slot(dev, name, snr_index, n_pe, n_sc):
     same_tab = np.all(g["paths"] == ref["paths"], axis=(1, 2))
     sc_ok = same_front & same_tab
     assert sc_ok.mean() > 0.8, sc_ok.mean()
-    # float32 QR error enters R and z: PED / LLR tolerance 1e-3 relative here
-    P.compare_detect(g, ref, ref["R"], sl.sigma2, rtol=1e-3, what=name, sc_mask=sc_ok,
+    P.compare_detect(g, ref, ref["R"], sl.sigma2, rtol=ref["rtol"], what=name, sc_mask=sc_ok,
                      min_frac=0.4)
 
 
@@ -266,8 +266,7 @@ def test_full_size_slot_sampled(dev):
     rng = np.random.default_rng(1)
     idx = np.sort(rng.choice(sl.n_sc, 12, replace=False))
     idx[-1] = sl.n_sc - 1  # include the last (ragged-tail) subcarrier
-    ref = oracle.detect_slot(sl.H[idx], sl.Y[idx], sl.sigma2, sl.qam, n_pe, with_mmse=True,
-                             tie_eps=P.TIE_EPS_E2E)
+    ref = P.e2e_reference(sl.H[idx], sl.Y[idx], sl.sigma2, sl.qam, n_pe)
     g = dict(hard=buf.hard.cpu().numpy()[idx], llr=buf.llr.cpu().numpy()[idx],
              ped2=buf.ped2.cpu().numpy()[idx])
     paths = buf.paths.cpu().numpy()[idx]
@@ -275,8 +274,8 @@ def test_full_size_slot_sampled(dev):
     sc_ok = np.all(perm == ref["perm"], axis=1) & np.all(paths == ref["paths"], axis=(1, 2)) \
         & np.all(ref["sqrd_gap"] > 1e-4, axis=1)
     assert sc_ok.sum() >= 6
-    P.compare_detect(g, ref, ref["R"], sl.sigma2, rtol=1e-3, what="full slot", sc_mask=sc_ok,
-                     min_frac=0.3)
+    P.compare_detect(g, ref, ref["R"], sl.sigma2, rtol=ref["rtol"], what="full slot",
+                     sc_mask=sc_ok, min_frac=0.3)
     assert np.mean(buf.mmse_hard.cpu().numpy()[idx] == ref["mmse_hard"]) > 0.999
 
 
