@@ -1,10 +1,10 @@
 // Evaluation of the N_pe position vectors of every (subcarrier, symbol):
 // SIC / partial-Euclidean-distance walks, argmin, max-log LLRs.
 //
-// One CTA per subcarrier; R, 1/R_ll, perm, the table and the subcarrier's 14
-// z vectors are staged in shared memory once.  A warp takes 32 rows of the
-// table for one symbol; each lane runs one walk with its whole state in
-// registers:
+// One CTA per subcarrier; R, 1/R_ll, perm, the table and the subcarrier's z
+// vectors are staged in shared memory once.  A warp takes 32 rows of the
+// table for two OFDM symbols; each lane runs the walks of one row for both
+// symbols with the whole state in registers:
 //
 //   e := z
 //   for l = nt-1 .. 0:
@@ -13,10 +13,16 @@
 //     d  += R_ll^2 |b - s_l|^2
 //     e_i -= R_il s_l   for every i < l          (4 FFMA per complex term)
 //
-// Column l of R is read with 16-byte shared loads that every lane of the warp
-// issues for the same address (one broadcast wavefront per two complex
-// entries).  Rank 1 (the SIC choice, most entries of the table) is plain
-// per-axis slicing; higher ranks enumerate the nearest points in order.
+// Column l of R is read with 16-byte shared loads that all lanes issue for the
+// same address (broadcast) and that serve both symbols.
+//
+// Ranking.  Rank 1 (the SIC choice; ~90% of the entries below the first
+// level) is per-axis rounding to the grid; rank 2 compares the two next
+// neighbours; higher ranks enumerate the nearest points in order (out of
+// line).  The first detected level sees the same b for every row, so its
+// ordered neighbour list is built once per symbol and looked up.  Rows are
+// sorted in the CTA by how far they deviate from rank 1 below the first
+// level, so that lanes needing the slower paths share warps.
 //
 // Reductions, without contended atomics:
 //   warp:  argmin key (d, row) by shuffles; runner-up d and, for every
@@ -25,7 +31,7 @@
 //   CTA:   per (symbol, level, bit, value) a u32 atomicMin on shared memory
 //          (one per warp, distinct addresses across lanes); per symbol a
 //          64-bit atomicMin on the argmin key (one per warp);
-//   final: one thread per (symbol, level, bit) forms the LLR.
+//   final: one lane per (symbol, level, bit) forms the LLR.
 #include "mpnl_common.cuh"
 #include "mpnl_internal.h"
 
@@ -34,10 +40,41 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+constexpr int kTopList = 64;  // entries of the first-level neighbour list
 
 // --------------------------------------------------------------------------
-// ranking: p-th closest constellation point
+// ranking
 // --------------------------------------------------------------------------
+
+// Nearest grid index along one axis by rounding (an exact midpoint goes to
+// the smaller axis label); returns the index, writes the squared distance.
+template <int QAM>
+__device__ __forceinline__ int axis_round(float x, float &d)
+{
+    constexpr int L = Qam<QAM>::L;
+    const float u = fmaf(x, 0.5f * Qam<QAM>::kScale, 0.5f * (float)(L - 1));
+    float fr = fminf(fmaxf(rintf(u), 0.f), (float)(L - 1));
+    const float fl = floorf(u);
+    if (u - fl == 0.5f && fl >= 0.f && fl < (float)(L - 1)) {
+        const int a = (int)fl;
+        fr = Qam<QAM>::axis_label(a) < Qam<QAM>::axis_label(a + 1) ? fl : fl + 1.f;
+    }
+    const float pos = fmaf(fr, 2.f * Qam<QAM>::kInvScale, -(float)(L - 1) * Qam<QAM>::kInvScale);
+    const float df = x - pos;
+    d = df * df;
+    return (int)fr;
+}
+
+// The next grid index after i0 in distance order along an axis (one step
+// towards x, or away when the constellation ends there).
+template <int QAM>
+__device__ __forceinline__ int axis_next(float x, int i0)
+{
+    constexpr int L = Qam<QAM>::L;
+    const int s = x >= axis_pos<QAM>(i0) ? 1 : -1;
+    const int n = i0 + s;
+    return (n >= 0 && n < L) ? n : i0 - s;
+}
 
 // Grid indices of one axis in order of distance to x: the nearest index i0,
 // then alternately one step towards x and one step away, until one side runs
@@ -73,27 +110,17 @@ __device__ __forceinline__ int grid_label(int ire, int iim)
     return join_label<QAM>(Qam<QAM>::axis_label(ire), Qam<QAM>::axis_label(iim));
 }
 
-// p-th closest point (p >= 1) to b = (bx, by) by (squared distance, label);
-// returns the squared distance, writes the label and the coordinates.
-// p == 1 is per-axis slicing.  Otherwise the 2-D order is enumerated over the
-// "staircase" of (row a, column c) pairs of the two axis orders: popping
-// (a, c) exposes (a, c + 1), popping (a, 0) also exposes (a + 1, 0); every
-// pair's predecessor sorts no later, so p pops reach the p-th point.  The
-// per-row column pointers are packed 4 bits each in one register.
+// p-th closest point (p >= 3) by (squared distance, label): the 2-D order is
+// enumerated over the "staircase" of (row a, column c) pairs of the two axis
+// orders: popping (a, c) exposes (a, c + 1), popping (a, 0) also exposes
+// (a + 1, 0); every pair's predecessor sorts no later, so p pops reach the
+// p-th point.  The per-row column pointers are packed 4 bits each.
+// Writes the grid indices, returns the squared distance.
 template <int QAM>
-__device__ __forceinline__ float kth_point(float bx, float by, int p, int &label, float &sx,
-                                           float &sy)
+__device__ __noinline__ float kth_point_slow(float bx, float by, int p, int ire, int iim,
+                                             int &oi, int &oj)
 {
     constexpr int L = Qam<QAM>::L;
-    float dre, dim;
-    const int ire = axis_nearest<QAM>(bx, dre);
-    const int iim = axis_nearest<QAM>(by, dim);
-    if (p <= 1) {
-        label = grid_label<QAM>(ire, iim);
-        sx = axis_pos<QAM>(ire);
-        sy = axis_pos<QAM>(iim);
-        return dre + dim;
-    }
     const AxisOrder<QAM> ore(bx, ire), oim(by, iim);
     unsigned cols = 0;
     int na = 1;
@@ -127,10 +154,52 @@ __device__ __forceinline__ float kth_point(float bx, float by, int p, int &label
         if (bc == 0 && ba == na - 1 && na < L) ++na;
         cols += 1u << (4 * ba);
     }
-    label = grid_label<QAM>(bi, bj);
-    sx = axis_pos<QAM>(bi);
-    sy = axis_pos<QAM>(bj);
+    oi = bi;
+    oj = bj;
     return bd;
+}
+
+// The first detected level sees the same b = z_{nt-1} / R for every row, so
+// its ordered neighbour list is built once per symbol by one warp: lane j
+// holds points j and j + 32; a point's rank is the number of points before it
+// in (distance, label) order.  Entry r: (x, y, distance, label).
+template <int QAM>
+__device__ __forceinline__ void top_list(float bx, float by, int kmax, float4 *list)
+{
+    constexpr int M = QAM;
+    constexpr int PER = (M + 31) / 32;
+    const int lane = threadIdx.x & 31;
+    float dq[PER], xq[PER], yq[PER];
+    int lq[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = lane + 32 * k;  // q = grid index: iy * L + ix
+        const int ix = q % Qam<QAM>::L, iy = q / Qam<QAM>::L;
+        xq[k] = axis_pos<QAM>(ix);
+        yq[k] = axis_pos<QAM>(iy);
+        const float dx = bx - xq[k], dy = by - yq[k];
+        dq[k] = q < M ? dx * dx + dy * dy : INFINITY;
+        lq[k] = q < M ? grid_label<QAM>(ix, iy) : 0x7fffffff;
+    }
+    int rank[PER];
+#pragma unroll
+    for (int k = 0; k < PER; ++k) rank[k] = 0;
+    for (int j = 0; j < 32; ++j) {
+#pragma unroll
+        for (int kk = 0; kk < PER; ++kk) {
+            const float dj = __shfl_sync(0xffffffffu, dq[kk], j);
+            const int lj = __shfl_sync(0xffffffffu, lq[kk], j);
+#pragma unroll
+            for (int k = 0; k < PER; ++k)
+                rank[k] += (dj < dq[k] || (dj == dq[k] && lj < lq[k])) ? 1 : 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+        const int q = lane + 32 * k;
+        if (q < M && rank[k] < kmax)
+            list[rank[k]] = make_float4(xq[k], yq[k], dq[k], __int_as_float(lq[k]));
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -176,15 +245,22 @@ struct Labels {
 };
 
 __host__ __device__ inline int a16(int o) { return (o + 15) & ~15; }
+__host__ __device__ inline int pow2_at_least(int n)
+{
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
 
 struct DetSmem {
-    int off_rc, off_r2, off_invd, off_perm, off_z, off_tab, off_m, off_best, off_wmin,
-        off_second, off_blab, bytes;
+    int off_rc, off_r2, off_invd, off_perm, off_z, off_tab, off_order, off_m, off_best, off_wmin,
+        off_second, off_blab, off_top, off_lut, bytes;
 };
 
 __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym, int WORDS)
 {
     const int chunks = (n_pe + 31) / 32;
+    const int np2 = pow2_at_least(chunks * 32);
     DetSmem s;
     int o = 0;
     s.off_rc = o;
@@ -196,9 +272,11 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     s.off_perm = o;
     o = a16(o + NT * 4);
     s.off_z = o;
-    o = a16(o + n_sym * NT * 8);
+    o = a16(o + (n_sym + 1) * NT * 8);
     s.off_tab = o;
     o = a16(o + chunks * 32 * NT);
+    s.off_order = o;
+    o = a16(o + np2 * 4);
     s.off_m = o;
     o = a16(o + n_sym * NT * B * 2 * 4);
     s.off_best = o;
@@ -209,8 +287,82 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     o = a16(o + n_sym * chunks * 4);
     s.off_blab = o;
     o = a16(o + n_sym * chunks * WORDS * 4);
+    s.off_top = o;
+    o = a16(o + (n_sym + 1) * kTopList * 16);
+    s.off_lut = o;  // 2-D label of grid point (ire, iim) at ire * 8 + iim
+    o = a16(o + 64);
     s.bytes = o;
     return s;
+}
+
+// Warp-level results of one symbol for the 32 walks a warp just finished.
+template <int NT, int B>
+__device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int row, int chunk,
+                                                   int chunks, int nt, float d,
+                                                   const Labels<NT, B> &lab, int s,
+                                                   unsigned long long *sBest, unsigned *sWmin,
+                                                   unsigned *sSecond, uint32_t *sBlab,
+                                                   unsigned *sM, bool want_llr)
+{
+    using Lab = Labels<NT, B>;
+    constexpr int WORDS = Lab::WORDS;
+    const int lane = threadIdx.x & 31;
+    const unsigned db = active ? fbits(d) : kInfBits;
+    // key: PED bits, table row (the tie-break), then the sorted position
+    unsigned long long key =
+        active ? (((unsigned long long)db << 32) | ((unsigned)row << 16) | (unsigned)(chunk * 32 + lane))
+               : ~0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
+        key = k2 < key ? k2 : key;
+    }
+    const int blane = (int)(key & 31u);  // lane of the warp's best row
+    const unsigned wmin = (unsigned)(key >> 32);
+    const unsigned second = __reduce_min_sync(0xffffffffu, lane == blane ? kInfBits : db);
+    Lab bl;
+#pragma unroll
+    for (int k = 0; k < WORDS; ++k) bl.w[k] = __shfl_sync(0xffffffffu, lab.w[k], blane);
+    if (!valid) return;  // (warp-uniform) second symbol slot beyond n_sym
+    if (lane == 0) {
+        atomicMin(&sBest[s], key);
+        sWmin[s * chunks + chunk] = wmin;
+        sSecond[s * chunks + chunk] = second;
+#pragma unroll
+        for (int k = 0; k < WORDS; ++k) sBlab[(s * chunks + chunk) * WORDS + k] = bl.w[k];
+    }
+    if (!want_llr) return;
+    // per (level, bit): the warp-best row's bit value bb has minimum wmin; the
+    // other value's minimum comes from one redux
+    unsigned mine_other[3] = {kInfBits, kInfBits, kInfBits};
+    int mine_bb[3] = {0, 0, 0};
+#pragma unroll
+    for (int l = 0; l < NT; ++l) {
+        if (l < nt) {
+            const int x = lab.get(l) ^ bl.get(l);  // bits that differ from the best row
+            const int bbl = bl.get(l);
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int sh = B - 1 - b;
+                const unsigned v = ((x >> sh) & 1) ? db : kInfBits;
+                const unsigned mo = __reduce_min_sync(0xffffffffu, v);
+                const int slot = l * B + b;
+                if (lane == (slot & 31)) {
+                    mine_other[slot >> 5] = mo;
+                    mine_bb[slot >> 5] = (bbl >> sh) & 1;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const int slot = lane + 32 * q;
+        if (slot < nt * B) {
+            unsigned *mm = sM + (s * NT * B + slot) * 2;
+            atomicMin(mm + mine_bb[q], wmin);
+            atomicMin(mm + (1 - mine_bb[q]), mine_other[q]);
+        }
+    }
 }
 
 template <int NT, int QAM>
@@ -222,10 +374,13 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                    unsigned *__restrict__ status)
 {
     constexpr int B = Qam<QAM>::B;
+    constexpr int L = Qam<QAM>::L;
     using Lab = Labels<NT, B>;
     constexpr int WORDS = Lab::WORDS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int chunks = (n_pe + 31) / 32;
+    const int nrows = chunks * 32;
+    const int np2 = pow2_at_least(nrows);
     const DetSmem S = det_layout(NT, B, n_pe, n_sym, WORDS);
     float2 *sRc = reinterpret_cast<float2 *>(smem + S.off_rc);  // sRc[l*NT + i] = R_il, i < l
     float *sR2 = reinterpret_cast<float *>(smem + S.off_r2);
@@ -233,11 +388,15 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
     int *sPerm = reinterpret_cast<int *>(smem + S.off_perm);
     float2 *sZ = reinterpret_cast<float2 *>(smem + S.off_z);
     uint8_t *sTab = smem + S.off_tab;
+    unsigned *sOrder = reinterpret_cast<unsigned *>(smem + S.off_order);
     unsigned *sM = reinterpret_cast<unsigned *>(smem + S.off_m);
     unsigned long long *sBest = reinterpret_cast<unsigned long long *>(smem + S.off_best);
     unsigned *sWmin = reinterpret_cast<unsigned *>(smem + S.off_wmin);
     unsigned *sSecond = reinterpret_cast<unsigned *>(smem + S.off_second);
     uint32_t *sBlab = reinterpret_cast<uint32_t *>(smem + S.off_blab);
+    float4 *sTop = reinterpret_cast<float4 *>(smem + S.off_top);
+    uint8_t *sLut = smem + S.off_lut;
+    __shared__ int s_kmax;
 
     const int sc = blockIdx.x;
     const int tid = threadIdx.x;
@@ -262,120 +421,185 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
             sPerm[k] = perm[(size_t)sc * nt + k];
         }
     }
-    for (int k = tid; k < n_sym * nt; k += kThreads)
-        sZ[(k / nt) * NT + (k % nt)] = Z[(size_t)sc * n_sym * nt + k];
-    for (int k = tid; k < chunks * 32 * NT; k += kThreads) {
-        const int r = k / NT, l = k - r * NT;
-        int v = 1;  // padding rows and levels: rank 1
-        if (r < n_pe && l < nt) {
-            v = paths[((size_t)sc * n_pe + r) * nt + l];
-            if (v < 1 || v > QAM) {
-                atomicOr(status, kStatusBadPathEntry);
-                v = v < 1 ? 1 : QAM;
-            }
-        }
-        sTab[k] = (uint8_t)v;
+    for (int k = tid; k < (n_sym + 1) * NT; k += kThreads) {
+        const int s = k / NT, l = k - s * NT;
+        sZ[k] = (s < n_sym && l < nt) ? Z[((size_t)sc * n_sym + s) * nt + l] : make_float2(0.f, 0.f);
     }
+    if (tid < L * 8) {
+        const int ire = tid >> 3, iim = tid & 7;
+        sLut[tid] = (uint8_t)(iim < L ? grid_label<QAM>(ire, iim) : 0);
+    }
+    if (tid == 0) s_kmax = 1;
+    __syncthreads();
+    // table, clamped; the sort key of a row: how far it deviates from rank 1
+    // below the first level (largest rank, then rank sum), then the row
+    int kmax = 1;
+    for (int r = tid; r < np2; r += kThreads) {
+        unsigned key = 0xffffffffu;
+        if (r < nrows) {
+            int mx = 1, sum = 0;
+            for (int l = 0; l < NT; ++l) {
+                int v = 1;  // padding rows and levels: rank 1
+                if (r < n_pe && l < nt) {
+                    v = paths[((size_t)sc * n_pe + r) * nt + l];
+                    if (v < 1 || v > QAM) {
+                        atomicOr(status, kStatusBadPathEntry);
+                        v = v < 1 ? 1 : QAM;
+                    }
+                    if (l == nt - 1) kmax = max(kmax, v);
+                    else {
+                        mx = max(mx, v);
+                        sum += v - 1;
+                    }
+                }
+                sTab[r * NT + l] = (uint8_t)v;
+            }
+            key = r < n_pe ? ((unsigned)min(mx, 255) << 24) | ((unsigned)min(sum, 4095) << 12) |
+                                 (unsigned)r
+                           : (0xfffu << 20) | (unsigned)r;
+        }
+        sOrder[r] = key;
+    }
+    atomicMax(&s_kmax, kmax);
     for (int k = tid; k < n_sym * NT * B * 2; k += kThreads) sM[k] = kInfBits;
     for (int k = tid; k < n_sym; k += kThreads) sBest[k] = ~0ull;
     __syncthreads();
+    // bitonic sort of the row keys
+    for (int k = 2; k <= np2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < np2; i += kThreads) {
+                const int ixj = i ^ j;
+                if (ixj > i) {
+                    const unsigned a = sOrder[i], b = sOrder[ixj];
+                    if ((a > b) == ((i & k) == 0)) {
+                        sOrder[i] = b;
+                        sOrder[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // ordered neighbours of b = z_{nt-1} / R_{nt-1,nt-1}, one warp per symbol
+    {
+        const int kmx = s_kmax;
+        const float iv = sInvd[nt - 1];
+        for (int s = warp; s <= n_sym; s += kWarps) {
+            const float2 z = sZ[s * NT + nt - 1];
+            top_list<QAM>(z.x * iv, z.y * iv, kmx, sTop + s * kTopList);
+        }
+    }
+    __syncthreads();
 
-    // ---- walks: warp item = (chunk of 32 rows, symbol)
-    for (int item = warp; item < chunks * n_sym; item += kWarps) {
-        const int chunk = item / n_sym, s = item - chunk * n_sym;
-        const int row = chunk * 32 + lane;
+    // ---- walks: warp item = (chunk of 32 rows, pair of symbols)
+    const int pairs = (n_sym + 1) >> 1;
+    for (int item = warp; item < chunks * pairs; item += kWarps) {
+        const int chunk = item / pairs, s0 = 2 * (item - chunk * pairs);
+        const bool has1 = s0 + 1 < n_sym;
+        const int row = (int)(sOrder[chunk * 32 + lane] & 0xfffu);
         const bool active = row < n_pe;
         RowRanks<NT> pr;
         pr.load(sTab + row * NT);
-        float ex[NT], ey[NT];
+        float ex[2][NT], ey[2][NT];
 #pragma unroll
         for (int l = 0; l < NT; ++l) {
-            const float2 z = sZ[s * NT + l];
-            ex[l] = z.x;
-            ey[l] = z.y;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const float2 z = sZ[(s0 + k) * NT + l];
+                ex[k][l] = z.x;
+                ey[k][l] = z.y;
+            }
         }
-        Lab lab;
-        lab.clear();
-        float d = 0.f;
+        Lab lab[2];
+        lab[0].clear();
+        lab[1].clear();
+        float d[2] = {0.f, 0.f};
 #pragma unroll
         for (int l = NT - 1; l >= 0; --l) {
             if (l < nt) {
-                const float iv = sInvd[l];
-                int lb;
-                float sx, sy;
-                const float dist = kth_point<QAM>(ex[l] * iv, ey[l] * iv, pr.get(l), lb, sx, sy);
-                d = fmaf(sR2[l], dist, d);
-                lab.set(l, lb);
+                const int p = pr.get(l);
+                float sx[2], sy[2], dist[2];
+                int lb[2];
+                if (l == nt - 1) {  // shared first level: look the rank up
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const float4 q = sTop[(s0 + k) * kTopList + p - 1];
+                        sx[k] = q.x;
+                        sy[k] = q.y;
+                        dist[k] = q.z;
+                        lb[k] = __float_as_int(q.w);
+                    }
+                } else {
+                    const float iv = sInvd[l];
+                    int ire[2], iim[2];
+                    float dre[2], dim[2];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const float bx = ex[k][l] * iv, by = ey[k][l] * iv;
+                        ire[k] = axis_round<QAM>(bx, dre[k]);
+                        iim[k] = axis_round<QAM>(by, dim[k]);
+                        if (p == 2) {
+                            // second nearest: the next point along one axis
+                            const int nre = axis_next<QAM>(bx, ire[k]);
+                            const int nim = axis_next<QAM>(by, iim[k]);
+                            float a = bx - axis_pos<QAM>(nre), c = by - axis_pos<QAM>(nim);
+                            const float d_re = a * a + dim[k];  // (nre, iim)
+                            const float d_im = dre[k] + c * c;  // (ire, nim)
+                            bool take_re = d_re < d_im;
+                            if (d_re == d_im)
+                                take_re = sLut[nre * 8 + iim[k]] < sLut[ire[k] * 8 + nim];
+                            if (take_re) {
+                                ire[k] = nre;
+                                dre[k] = d_re;
+                                dim[k] = 0.f;
+                            } else {
+                                iim[k] = nim;
+                                dre[k] = d_im;
+                                dim[k] = 0.f;
+                            }
+                        } else if (p > 2) {
+                            int oi, oj;
+                            dre[k] = kth_point_slow<QAM>(bx, by, p, ire[k], iim[k], oi, oj);
+                            dim[k] = 0.f;
+                            ire[k] = oi;
+                            iim[k] = oj;
+                        }
+                        dist[k] = dre[k] + dim[k];
+                        sx[k] = axis_pos<QAM>(ire[k]);
+                        sy[k] = axis_pos<QAM>(iim[k]);
+                        lb[k] = sLut[ire[k] * 8 + iim[k]];
+                    }
+                }
+                const float r2 = sR2[l];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    d[k] = fmaf(r2, dist[k], d[k]);
+                    lab[k].set(l, lb[k]);
+                }
                 const float4 *col = reinterpret_cast<const float4 *>(sRc + l * NT);
 #pragma unroll
                 for (int i2 = 0; i2 < NT / 2; ++i2) {
                     if (2 * i2 < l) {
                         const float4 r = col[i2];  // R_{2i2,l}, R_{2i2+1,l}
-                        ex[2 * i2] = fmaf(-r.x, sx, fmaf(r.y, sy, ex[2 * i2]));
-                        ey[2 * i2] = fmaf(-r.x, sy, fmaf(-r.y, sx, ey[2 * i2]));
-                        if (2 * i2 + 1 < l) {
-                            ex[2 * i2 + 1] = fmaf(-r.z, sx, fmaf(r.w, sy, ex[2 * i2 + 1]));
-                            ey[2 * i2 + 1] = fmaf(-r.z, sy, fmaf(-r.w, sx, ey[2 * i2 + 1]));
+#pragma unroll
+                        for (int k = 0; k < 2; ++k) {
+                            ex[k][2 * i2] = fmaf(-r.x, sx[k], fmaf(r.y, sy[k], ex[k][2 * i2]));
+                            ey[k][2 * i2] = fmaf(-r.x, sy[k], fmaf(-r.y, sx[k], ey[k][2 * i2]));
+                            if (2 * i2 + 1 < l) {
+                                ex[k][2 * i2 + 1] =
+                                    fmaf(-r.z, sx[k], fmaf(r.w, sy[k], ex[k][2 * i2 + 1]));
+                                ey[k][2 * i2 + 1] =
+                                    fmaf(-r.z, sy[k], fmaf(-r.w, sx[k], ey[k][2 * i2 + 1]));
+                            }
                         }
                     }
                 }
             }
         }
-
-        // warp argmin of (d, row)
-        const unsigned db = active ? fbits(d) : kInfBits;
-        unsigned long long key = active ? (((unsigned long long)db << 32) | (unsigned)row) : ~0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-            key = k2 < key ? k2 : key;
-        }
-        const int blane = (int)(key & 0xffffffffull) - chunk * 32;
-        const unsigned wmin = (unsigned)(key >> 32);
-        const unsigned second = __reduce_min_sync(0xffffffffu, lane == blane ? kInfBits : db);
-        Lab bl;
-#pragma unroll
-        for (int k = 0; k < WORDS; ++k) bl.w[k] = __shfl_sync(0xffffffffu, lab.w[k], blane & 31);
-        if (lane == 0) {
-            atomicMin(&sBest[s], key);
-            sWmin[s * chunks + chunk] = wmin;
-            sSecond[s * chunks + chunk] = second;
-#pragma unroll
-            for (int k = 0; k < WORDS; ++k) sBlab[(s * chunks + chunk) * WORDS + k] = bl.w[k];
-        }
-        if (llr != nullptr) {
-            // per (level, bit): the warp-best row's bit value bb has minimum
-            // wmin; the other value's minimum comes from one redux
-            unsigned mine_other[3] = {kInfBits, kInfBits, kInfBits};
-            int mine_bb[3] = {0, 0, 0};
-#pragma unroll
-            for (int l = 0; l < NT; ++l) {
-                if (l < nt) {
-                    const int x = lab.get(l) ^ bl.get(l);  // bits that differ from the best row
-                    const int bbl = bl.get(l);
-#pragma unroll
-                    for (int b = 0; b < B; ++b) {
-                        const int sh = B - 1 - b;
-                        const unsigned v = ((x >> sh) & 1) ? db : kInfBits;
-                        const unsigned mo = __reduce_min_sync(0xffffffffu, v);
-                        const int slot = l * B + b;
-                        if (lane == (slot & 31)) {
-                            mine_other[slot >> 5] = mo;
-                            mine_bb[slot >> 5] = (bbl >> sh) & 1;
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                const int slot = lane + 32 * q;
-                if (slot < nt * B) {
-                    unsigned *mm = sM + (s * NT * B + slot) * 2;
-                    atomicMin(mm + mine_bb[q], wmin);
-                    atomicMin(mm + (1 - mine_bb[q]), mine_other[q]);
-                }
-            }
-        }
+        warp_reduce_symbol<NT, B>(true, active, row, chunk, chunks, nt, d[0], lab[0], s0, sBest,
+                                  sWmin, sSecond, sBlab, sM, llr != nullptr);
+        warp_reduce_symbol<NT, B>(has1, active, row, chunk, chunks, nt, d[1], lab[1], s0 + 1,
+                                  sBest, sWmin, sSecond, sBlab, sM, llr != nullptr);
     }
     __syncthreads();
 
@@ -383,19 +607,20 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
     for (int s = warp; s < n_sym; s += kWarps) {
         const size_t det = (size_t)sc * n_sym + s;
         const unsigned long long key = sBest[s];
-        const int brow = (int)(key & 0xffffffffull);
-        const int bchunk = brow >> 5;
+        const unsigned bd = (unsigned)(key >> 32);
+        int bc = (int)((key & 0xffffu) >> 5);  // chunk of the best row's sorted position
+        if (bc >= chunks) bc = 0;
         if (lane < nt) {
-            const uint32_t w = sBlab[(s * chunks + bchunk) * WORDS + lane / Lab::PER];
+            const uint32_t w = sBlab[(s * chunks + bc) * WORDS + lane / Lab::PER];
             hard[det * nt + sPerm[lane]] = (uint8_t)((w >> (B * (lane % Lab::PER))) & ((1 << B) - 1));
         }
         if (ped2 != nullptr) {
             unsigned sec = kInfBits;
             for (int c = lane; c < chunks; c += 32)
-                sec = min(sec, c == bchunk ? sSecond[s * chunks + c] : sWmin[s * chunks + c]);
+                sec = min(sec, c == bc ? sSecond[s * chunks + c] : sWmin[s * chunks + c]);
             sec = __reduce_min_sync(0xffffffffu, sec);
             if (lane == 0) {
-                ped2[det * 2] = __uint_as_float((unsigned)(key >> 32));
+                ped2[det * 2] = __uint_as_float(bd);
                 ped2[det * 2 + 1] = __uint_as_float(sec);
             }
         }

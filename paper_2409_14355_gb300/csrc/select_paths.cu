@@ -88,6 +88,25 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
         pe = fmaxf(pe, kPeFloor);
         w[l] = -logf(pe);
     }
+    __syncthreads();
+    // Upper bound on the final N_pe-th cost: the vectors that deviate from
+    // all-ones at a single level (cost j w_l) plus all-ones itself are valid
+    // vectors, so if N_pe of them cost <= v, the answer's N_pe-th cost is
+    // <= v.  Shifts whose first entry j w_m exceeds the bound cannot
+    // contribute and are skipped (the bound is padded against rounding).
+    __shared__ unsigned s_bound;
+    if (tid == 0) s_bound = 0x7f800000u;  // +inf
+    __syncthreads();
+    for (int k = tid; k < nt * (QAM - 1); k += T) {
+        const int l = k / (QAM - 1), j = 1 + k % (QAM - 1);
+        const float v = (float)j * w[l];
+        int cnt = 1;
+        for (int m = 0; m < nt; ++m) {
+            const int c = (int)floorf(v * (1.0f - 1e-6f) / w[m]);
+            cnt += c < 0 ? 0 : (c > QAM - 1 ? QAM - 1 : c);
+        }
+        if (cnt >= n_pe) atomicMin(&s_bound, __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f));
+    }
     // L = [all ones]
     int li = 0;
     if (tid == 0) {
@@ -106,6 +125,7 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
     int nL = 1;
     __syncthreads();
 
+    const float bound = __uint_as_float(s_bound);
     for (int m = nt - 1; m >= 0; --m) {
         const float wm = w[m];
         bool in_hi;
@@ -116,6 +136,7 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
         for (int j = 1; j < QAM; ++j) {
             const unsigned long long add = (unsigned long long)j << sh;
             const float cj = (float)j * wm;
+            if (cj > bound) break;
             // first entry of the shifted list vs the last entry of B
             {
                 const float c0 = cost[li][0] + cj;
