@@ -10,7 +10,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-#include "../../include/mpnl.h"
+#include "mpnl.h"
 #include "mpnl_internal.h"
 
 struct mpnl_ctx {

@@ -57,22 +57,14 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
     const int tid = threadIdx.x;
     const int T = blockDim.x;
 
-    // three lists (struct of arrays): keys first for 8-byte alignment
-    unsigned long long *hi[3], *lo[3];
-    float *cost[3];
-    {
-        unsigned char *p = smem_raw;
-        for (int b = 0; b < 3; ++b) {
-            hi[b] = reinterpret_cast<unsigned long long *>(p);
-            p += (size_t)n_pe * 8;
-            lo[b] = reinterpret_cast<unsigned long long *>(p);
-            p += (size_t)n_pe * 8;
-        }
-        for (int b = 0; b < 3; ++b) {
-            cost[b] = reinterpret_cast<float *>(p);
-            p += (size_t)n_pe * 4;
-        }
-    }
+    // three lists (struct of arrays) addressed as base + list * n_pe, so that
+    // the list index stays arithmetic (no pointer arrays in local memory)
+    unsigned long long *HI = reinterpret_cast<unsigned long long *>(smem_raw);
+    unsigned long long *LO = HI + 3 * n_pe;
+    float *CO = reinterpret_cast<float *>(LO + 3 * n_pe);
+#define hi(b) (HI + (size_t)(b) * n_pe)
+#define lo(b) (LO + (size_t)(b) * n_pe)
+#define cost(b) (CO + (size_t)(b) * n_pe)
     __shared__ float w[kMaxNt];
 
     const int P = nt * (nt + 1) / 2;
@@ -118,9 +110,9 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
             if (in_hi) h |= 1ull << sh;
             else o |= 1ull << sh;
         }
-        hi[0][0] = h;
-        lo[0][0] = o;
-        cost[0][0] = 0.f;
+        hi(0)[0] = h;
+        lo(0)[0] = o;
+        cost(0)[0] = 0.f;
     }
     int nL = 1;
     __syncthreads();
@@ -139,51 +131,51 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
             if (cj > bound) break;
             // first entry of the shifted list vs the last entry of B
             {
-                const float c0 = cost[li][0] + cj;
-                const unsigned long long h0 = hi[li][0] + (in_hi ? add : 0ull);
-                const unsigned long long l0 = lo[li][0] + (in_hi ? 0ull : add);
+                const float c0 = cost(li)[0] + cj;
+                const unsigned long long h0 = hi(li)[0] + (in_hi ? add : 0ull);
+                const unsigned long long l0 = lo(li)[0] + (in_hi ? 0ull : add);
                 if (nB == n_pe &&
-                    !before(c0, h0, l0, cost[bi][nB - 1], hi[bi][nB - 1], lo[bi][nB - 1]))
+                    !before(c0, h0, l0, cost(bi)[nB - 1], hi(bi)[nB - 1], lo(bi)[nB - 1]))
                     break;
             }
             const int nOut = min(n_pe, nB + nL);
             // elements of B: position = own index + #shifted entries before it
             for (int a = tid; a < nB; a += T) {
-                const float ca = cost[bi][a];
-                const unsigned long long ha = hi[bi][a], la = lo[bi][a];
+                const float ca = cost(bi)[a];
+                const unsigned long long ha = hi(bi)[a], la = lo(bi)[a];
                 int lo_i = 0, hi_i = nL;  // count shifted entries strictly before a
                 while (lo_i < hi_i) {
                     const int mid = (lo_i + hi_i) >> 1;
-                    const float cm = cost[li][mid] + cj;
-                    const unsigned long long hm = hi[li][mid] + (in_hi ? add : 0ull);
-                    const unsigned long long lm = lo[li][mid] + (in_hi ? 0ull : add);
+                    const float cm = cost(li)[mid] + cj;
+                    const unsigned long long hm = hi(li)[mid] + (in_hi ? add : 0ull);
+                    const unsigned long long lm = lo(li)[mid] + (in_hi ? 0ull : add);
                     if (before(cm, hm, lm, ca, ha, la)) lo_i = mid + 1;
                     else hi_i = mid;
                 }
                 const int pos = a + lo_i;
                 if (pos < nOut) {
-                    cost[oi][pos] = ca;
-                    hi[oi][pos] = ha;
-                    lo[oi][pos] = la;
+                    cost(oi)[pos] = ca;
+                    hi(oi)[pos] = ha;
+                    lo(oi)[pos] = la;
                 }
             }
             // elements of the shifted list
             for (int a = tid; a < nL; a += T) {
-                const float ca = cost[li][a] + cj;
-                const unsigned long long ha = hi[li][a] + (in_hi ? add : 0ull);
-                const unsigned long long la = lo[li][a] + (in_hi ? 0ull : add);
+                const float ca = cost(li)[a] + cj;
+                const unsigned long long ha = hi(li)[a] + (in_hi ? add : 0ull);
+                const unsigned long long la = lo(li)[a] + (in_hi ? 0ull : add);
                 if (a >= nOut) continue;
                 int lo_i = 0, hi_i = nB;  // count B entries strictly before it
                 while (lo_i < hi_i) {
                     const int mid = (lo_i + hi_i) >> 1;
-                    if (before(cost[bi][mid], hi[bi][mid], lo[bi][mid], ca, ha, la)) lo_i = mid + 1;
+                    if (before(cost(bi)[mid], hi(bi)[mid], lo(bi)[mid], ca, ha, la)) lo_i = mid + 1;
                     else hi_i = mid;
                 }
                 const int pos = a + lo_i;
                 if (pos < nOut) {
-                    cost[oi][pos] = ca;
-                    hi[oi][pos] = ha;
-                    lo[oi][pos] = la;
+                    cost(oi)[pos] = ca;
+                    hi(oi)[pos] = ha;
+                    lo(oi)[pos] = la;
                 }
             }
             __syncthreads();
@@ -204,10 +196,14 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
         bool in_hi;
         int sh;
         level_shift(nt, l, in_hi, sh);
-        const unsigned long long v = in_hi ? hi[li][r] : lo[li][r];
+        const unsigned long long v = in_hi ? hi(li)[r] : lo(li)[r];
         out[k] = (uint8_t)((v >> sh) & 0xffull);
     }
 }
+
+#undef hi
+#undef lo
+#undef cost
 
 template <int QAM>
 cudaError_t launch_tpl(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
