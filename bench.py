@@ -152,6 +152,29 @@ def time_oracle(sl, qam, n_pe, seconds: float, max_sc: int | None = None):
         n = int(n * grow) + 1
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """Maximum of a per-rank scalar over the process group (identity when no
+    group is initialised).  Works with nccl (device tensor) and gloo (CPU)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, seconds: float, device=None) -> tuple[float, float]:
+    """Weak-scaling aggregate: every rank processed `units_per_rank`; the job
+    took as long as its slowest rank.  Returns (units/s over all ranks, max s)."""
+    import torch.distributed as dist
+
+    world = dist.get_world_size() if (dist.is_available() and dist.is_initialized()) else 1
+    slowest = max_over_ranks(seconds, device)
+    return world * units_per_rank / slowest, slowest
+
+
 def source_hash(paths) -> str:
     h = hashlib.sha256()
     for p in paths:
@@ -304,10 +327,6 @@ def run_mpnl(args):
     clk = clocks.stop()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     mpnl.check_status(local)
-    if world > 1:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
     lat = sorted(a.elapsed_time(b) for a, b in step_ev)
     det_ms = [a.elapsed_time(b) for a, b in det_ev]
     det_avg = sum(det_ms) / len(det_ms)
@@ -331,15 +350,10 @@ def run_mpnl(args):
         e2e_dt = time.perf_counter() - t0
         h2d = hs[0][0].numel() * 8 + hs[0][1].numel() * 8
         d2h = sum(v.numel() * v.element_size() for v in out.values())
-        e2e_dets = args.e2e_steps * n_sc * n_sym
-        if world > 1:
-            t = torch.tensor([e2e_dt], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_dt = float(t.item())
-        e2e_value = world * e2e_dets / e2e_dt
+        e2e_value, _ = whole_job_rate(args.e2e_steps * n_sc * n_sym, e2e_dt, dev)
 
     dets_per_step = n_sc * n_sym
-    value = world * K * dets_per_step / elapsed
+    value, elapsed = whole_job_rate(K * dets_per_step, elapsed, dev)
 
     # ---- roofline of the dominant kernel (walk kernel, FP32 ALU bound)
     props = torch.cuda.get_device_properties(dev)
