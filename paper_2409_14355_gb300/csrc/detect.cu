@@ -41,6 +41,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTopList = 64;  // entries of the first-level neighbour list
+constexpr int kList2 = 64;    // per symbol: entries of all second-level lists together
 
 // --------------------------------------------------------------------------
 // ranking
@@ -202,6 +203,44 @@ __device__ __forceinline__ void top_list(float bx, float by, int kmax, float4 *l
     }
 }
 
+// The len nearest points to b in order, by one thread: the staircase
+// enumeration of kth_point_slow, emitting every pop.  Entry r: (x, y,
+// distance, label).
+template <int QAM>
+__device__ __forceinline__ void nearest_list(float bx, float by, int len, float4 *out)
+{
+    constexpr int L = Qam<QAM>::L;
+    float d0;
+    const int ire = axis_round<QAM>(bx, d0);
+    const int iim = axis_round<QAM>(by, d0);
+    const AxisOrder<QAM> ore(bx, ire), oim(by, iim);
+    unsigned cols = 0;
+    int na = 1;
+    for (int pop = 0; pop < len; ++pop) {
+        int ba = -1, bi = 0, bj = 0, blab = 0;
+        float bd = INFINITY;
+        for (int a = 0; a < na; ++a) {
+            const int c = (cols >> (4 * a)) & 0xF;
+            if (c >= L) continue;
+            const int ia = ore.idx(a), ic = oim.idx(c);
+            const float dx = bx - axis_pos<QAM>(ia), dy = by - axis_pos<QAM>(ic);
+            const float v = dx * dx + dy * dy;
+            const int lv = grid_label<QAM>(ia, ic);
+            if (ba < 0 || v < bd || (v == bd && lv < blab)) {
+                ba = a;
+                bi = ia;
+                bj = ic;
+                bd = v;
+                blab = lv;
+            }
+        }
+        out[pop] = make_float4(axis_pos<QAM>(bi), axis_pos<QAM>(bj), bd, __int_as_float(blab));
+        const int bc = (cols >> (4 * ba)) & 0xF;
+        if (bc == 0 && ba == na - 1 && na < L) ++na;
+        cols += 1u << (4 * ba);
+    }
+}
+
 // --------------------------------------------------------------------------
 // per-walk state helpers
 // --------------------------------------------------------------------------
@@ -254,7 +293,7 @@ __host__ __device__ inline int pow2_at_least(int n)
 
 struct DetSmem {
     int off_rc, off_r2, off_invd, off_perm, off_z, off_tab, off_order, off_m, off_best, off_wmin,
-        off_second, off_blab, off_top, off_lut, bytes;
+        off_second, off_blab, off_top, off_l2, off_lut, bytes;
 };
 
 __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym, int WORDS)
@@ -289,6 +328,8 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     o = a16(o + n_sym * chunks * WORDS * 4);
     s.off_top = o;
     o = a16(o + (n_sym + 1) * kTopList * 16);
+    s.off_l2 = o;
+    o = a16(o + (n_sym + 1) * kList2 * 16);
     s.off_lut = o;  // 2-D label of grid point (ire, iim) at ire * 8 + iim
     o = a16(o + 64);
     s.bytes = o;
@@ -395,6 +436,9 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
     unsigned *sSecond = reinterpret_cast<unsigned *>(smem + S.off_second);
     uint32_t *sBlab = reinterpret_cast<uint32_t *>(smem + S.off_blab);
     float4 *sTop = reinterpret_cast<float4 *>(smem + S.off_top);
+    float4 *sL2 = reinterpret_cast<float4 *>(smem + S.off_l2);
+    __shared__ int s_k1[QAM + 1], s_off1[QAM + 1];
+    __shared__ int s_use2;
     uint8_t *sLut = smem + S.off_lut;
     __shared__ int s_kmax;
 
@@ -430,14 +474,17 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
         sLut[tid] = (uint8_t)(iim < L ? grid_label<QAM>(ire, iim) : 0);
     }
     if (tid == 0) s_kmax = 1;
+    for (int k = tid; k <= QAM; k += kThreads) s_k1[k] = 0;
     __syncthreads();
     // table, clamped; the sort key of a row: how far it deviates from rank 1
-    // below the first level (largest rank, then rank sum), then the row
+    // below the two list-served levels (largest rank, then rank sum), then
+    // the row.  Also: the largest first-level rank, and per first-level rank
+    // the largest second-level rank (the lengths of the second-level lists).
     int kmax = 1;
     for (int r = tid; r < np2; r += kThreads) {
         unsigned key = 0xffffffffu;
         if (r < nrows) {
-            int mx = 1, sum = 0;
+            int mx = 1, sum = 0, top = 1, second = 1;
             for (int l = 0; l < NT; ++l) {
                 int v = 1;  // padding rows and levels: rank 1
                 if (r < n_pe && l < nt) {
@@ -446,14 +493,19 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                         atomicOr(status, kStatusBadPathEntry);
                         v = v < 1 ? 1 : QAM;
                     }
-                    if (l == nt - 1) kmax = max(kmax, v);
-                    else {
+                    if (l == nt - 1) {
+                        kmax = max(kmax, v);
+                        top = v;
+                    } else if (l == nt - 2) {
+                        second = v;
+                    } else {
                         mx = max(mx, v);
                         sum += v - 1;
                     }
                 }
                 sTab[r * NT + l] = (uint8_t)v;
             }
+            if (r < n_pe && nt >= 2) atomicMax(&s_k1[top], second);
             key = r < n_pe ? ((unsigned)min(mx, 255) << 24) | ((unsigned)min(sum, 4095) << 12) |
                                  (unsigned)r
                            : (0xfffu << 20) | (unsigned)r;
@@ -488,8 +540,37 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
             const float2 z = sZ[s * NT + nt - 1];
             top_list<QAM>(z.x * iv, z.y * iv, kmx, sTop + s * kTopList);
         }
+        if (tid == 0) {  // offsets of the second-level lists (one per first-level rank)
+            int o = 0;
+            for (int a = 1; a <= kmx; ++a) {
+                s_off1[a] = o;
+                o += s_k1[a];
+            }
+            s_use2 = nt >= 2 && o <= kList2;
+        }
     }
     __syncthreads();
+    // Second level: rows that took the same first-level rank a see the same
+    // b = (z_{nt-2} - R_{nt-2,nt-1} s(a)) / R_{nt-2,nt-2}, so one ordered list
+    // per (symbol, a) serves them all -- as long as the lists fit.
+    if (s_use2) {
+        const int kmx = s_kmax;
+        const int l = nt - 2;
+        const float iv = sInvd[l];
+        const float2 r = sRc[(nt - 1) * NT + l];  // R_{nt-2, nt-1}
+        for (int it = tid; it < (n_sym + 1) * kmx; it += kThreads) {  // one thread per list
+            const int s = it / kmx, a = 1 + it - s * kmx;
+            const int len = s_k1[a];
+            if (len == 0) continue;
+            const float4 q = sTop[s * kTopList + a - 1];
+            const float2 z = sZ[s * NT + l];
+            const float ex = z.x - (r.x * q.x - r.y * q.y);
+            const float ey = z.y - (r.x * q.y + r.y * q.x);
+            nearest_list<QAM>(ex * iv, ey * iv, len, sL2 + s * kList2 + s_off1[a]);
+        }
+        __syncthreads();
+    }
+    const bool use2 = s_use2 != 0;
 
     // ---- walks: warp item = (chunk of 32 rows, pair of symbols)
     const int pairs = (n_sym + 1) >> 1;
@@ -520,10 +601,13 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                 const int p = pr.get(l);
                 float sx[2], sy[2], dist[2];
                 int lb[2];
-                if (l == nt - 1) {  // shared first level: look the rank up
+                if (l == nt - 1 || (use2 && l == nt - 2)) {  // list-served levels
+                    const float4 *lst = l == nt - 1 ? sTop + s0 * kTopList + p - 1
+                                                    : sL2 + s0 * kList2 + s_off1[pr.get(nt - 1)] + p - 1;
+                    const int stride = l == nt - 1 ? kTopList : kList2;
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const float4 q = sTop[(s0 + k) * kTopList + p - 1];
+                        const float4 q = lst[k * stride];
                         sx[k] = q.x;
                         sy[k] = q.y;
                         dist[k] = q.z;

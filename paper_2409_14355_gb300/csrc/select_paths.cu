@@ -99,9 +99,17 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
         }
         if (cnt >= n_pe) atomicMin(&s_bound, __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f));
     }
-    // L = [all ones]
-    int li = 0;
-    if (tid == 0) {
+    __syncthreads();
+    const float bound = __uint_as_float(s_bound);
+    // The first level processed (nt-1) in closed form: starting from the
+    // all-ones vector, its list is the arithmetic sequence j * w (rank j + 1
+    // at that level), already sorted, cut at N_pe, at M and at the bound --
+    // exactly what the shift-and-merge steps would produce one by one.
+    int li = 0, nL = 1;
+    {
+        const int mt = nt - 1;
+        const float wt = w[mt];
+        while (nL < QAM && nL < n_pe && (float)nL * wt <= bound) ++nL;
         unsigned long long h = 0, o = 0;
         for (int l = 0; l < nt; ++l) {
             bool in_hi;
@@ -110,15 +118,18 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
             if (in_hi) h |= 1ull << sh;
             else o |= 1ull << sh;
         }
-        hi(0)[0] = h;
-        lo(0)[0] = o;
-        cost(0)[0] = 0.f;
+        bool in_hi;
+        int sh;
+        level_shift(nt, mt, in_hi, sh);
+        for (int j = tid; j < nL; j += T) {
+            const unsigned long long add = (unsigned long long)j << sh;
+            hi(0)[j] = h + (in_hi ? add : 0ull);
+            lo(0)[j] = o + (in_hi ? 0ull : add);
+            cost(0)[j] = (float)j * wt;
+        }
     }
-    int nL = 1;
     __syncthreads();
-
-    const float bound = __uint_as_float(s_bound);
-    for (int m = nt - 1; m >= 0; --m) {
+    for (int m = nt - 2; m >= 0; --m) {
         const float wm = w[m];
         bool in_hi;
         int sh;
