@@ -21,8 +21,9 @@
 // Truncating to N_pe after every level is exact: a vector in the final top
 // N_pe has its restriction to the levels seen so far (ones elsewhere) ahead of
 // it in the order, so that restriction is in the partial top N_pe.
-// Each merge places every element by a binary search in the other list
-// (merge path), so all threads work at once.
+// Each merge is a merge path: every thread finds where its slice of the
+// output starts by one co-rank binary search and merges from there, so all
+// threads work at once.
 //
 // A vector is keyed by 16 bytes (two u64, level nt-1 in the most significant
 // byte): comparing keys as unsigned integers is the lexicographic order from
@@ -150,43 +151,41 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
                     break;
             }
             const int nOut = min(n_pe, nB + nL);
-            // elements of B: position = own index + #shifted entries before it
-            for (int a = tid; a < nB; a += T) {
-                const float ca = cost(bi)[a];
-                const unsigned long long ha = hi(bi)[a], la = lo(bi)[a];
-                int lo_i = 0, hi_i = nL;  // count shifted entries strictly before a
+            // Merge path: thread t writes outputs [k0, k1).  A co-rank binary
+            // search finds how many of the first k0 outputs come from B (the
+            // rest from the shifted list C), then the thread merges onward.
+            const int per = (nOut + T - 1) / T;
+            const int k0 = min(nOut, tid * per), k1 = min(nOut, k0 + per);
+            if (k0 < k1) {
+                int lo_i = max(0, k0 - nL), hi_i = min(k0, nB);
                 while (lo_i < hi_i) {
-                    const int mid = (lo_i + hi_i) >> 1;
-                    const float cm = cost(li)[mid] + cj;
-                    const unsigned long long hm = hi(li)[mid] + (in_hi ? add : 0ull);
-                    const unsigned long long lm = lo(li)[mid] + (in_hi ? 0ull : add);
-                    if (before(cm, hm, lm, ca, ha, la)) lo_i = mid + 1;
-                    else hi_i = mid;
+                    const int i = (lo_i + hi_i) >> 1, jj = k0 - i;  // jj >= 1, i < nB
+                    const float cc = cost(li)[jj - 1] + cj;
+                    const unsigned long long hc = hi(li)[jj - 1] + (in_hi ? add : 0ull);
+                    const unsigned long long lc = lo(li)[jj - 1] + (in_hi ? 0ull : add);
+                    if (before(cost(bi)[i], hi(bi)[i], lo(bi)[i], cc, hc, lc)) lo_i = i + 1;
+                    else hi_i = i;
                 }
-                const int pos = a + lo_i;
-                if (pos < nOut) {
-                    cost(oi)[pos] = ca;
-                    hi(oi)[pos] = ha;
-                    lo(oi)[pos] = la;
-                }
-            }
-            // elements of the shifted list
-            for (int a = tid; a < nL; a += T) {
-                const float ca = cost(li)[a] + cj;
-                const unsigned long long ha = hi(li)[a] + (in_hi ? add : 0ull);
-                const unsigned long long la = lo(li)[a] + (in_hi ? 0ull : add);
-                if (a >= nOut) continue;
-                int lo_i = 0, hi_i = nB;  // count B entries strictly before it
-                while (lo_i < hi_i) {
-                    const int mid = (lo_i + hi_i) >> 1;
-                    if (before(cost(bi)[mid], hi(bi)[mid], lo(bi)[mid], ca, ha, la)) lo_i = mid + 1;
-                    else hi_i = mid;
-                }
-                const int pos = a + lo_i;
-                if (pos < nOut) {
-                    cost(oi)[pos] = ca;
-                    hi(oi)[pos] = ha;
-                    lo(oi)[pos] = la;
+                int i = lo_i, jj = k0 - lo_i;
+                for (int k = k0; k < k1; ++k) {
+                    float ca = 0.f, cc = 0.f;
+                    unsigned long long ha = 0, la = 0, hc = 0, lc = 0;
+                    if (i < nB) {
+                        ca = cost(bi)[i];
+                        ha = hi(bi)[i];
+                        la = lo(bi)[i];
+                    }
+                    if (jj < nL) {
+                        cc = cost(li)[jj] + cj;
+                        hc = hi(li)[jj] + (in_hi ? add : 0ull);
+                        lc = lo(li)[jj] + (in_hi ? 0ull : add);
+                    }
+                    const bool take_b = jj >= nL || (i < nB && before(ca, ha, la, cc, hc, lc));
+                    cost(oi)[k] = take_b ? ca : cc;
+                    hi(oi)[k] = take_b ? ha : hc;
+                    lo(oi)[k] = take_b ? la : lc;
+                    if (take_b) ++i;
+                    else ++jj;
                 }
             }
             __syncthreads();
