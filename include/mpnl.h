@@ -139,6 +139,20 @@ int mpnl_detect(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const float
                 const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
                 uint8_t *hard, float *llr, float *ped2, void *ws, void *stream);
 
+/* Mixed-precision variant of mpnl_detect (same arguments, same layouts).
+ * The walks keep the interference-cancelled residuals e in FP16 (half2) and
+ * update them with packed half-precision FMAs; b = e_l / R_ll, the ranking
+ * and the PED accumulation stay in FP32.  The final best and runner-up paths
+ * are re-checked in FP32 (d = ||z - R s||^2 from their symbols) and the
+ * better of the two gives the hard decisions; ped2 holds those two FP32
+ * metrics (smaller first).  LLRs come from the FP16-walk PEDs.  Decisions can
+ * differ from mpnl_detect's where FP16 rounding changes a ranking; the
+ * decision-mismatch rate and BER delta against the FP64 oracle are reported
+ * by the tests and the benchmark. */
+int mpnl_detect_mixed(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const float *inv_diag,
+                      const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
+                      uint8_t *hard, float *llr, float *ped2, void *ws, void *stream);
+
 /* Linear MMSE baseline (§I, §III-B: "de facto standard linear MMSE"):
  * W = (H^H H + sigma2 I)^{-1} H^H; x = W y; mu_k = (W H)_kk;
  * x~_k = x_k / mu_k, nu_k = (1 - mu_k) / mu_k; hard = nearest point to x~_k;

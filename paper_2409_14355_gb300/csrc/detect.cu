@@ -32,6 +32,8 @@
 //          (one per warp, distinct addresses across lanes); per symbol a
 //          64-bit atomicMin on the argmin key (one per warp);
 //   final: one lane per (symbol, level, bit) forms the LLR.
+#include <cuda_fp16.h>
+
 #include "mpnl_common.cuh"
 #include "mpnl_internal.h"
 
@@ -109,6 +111,27 @@ template <int QAM>
 __device__ __forceinline__ int grid_label(int ire, int iim)
 {
     return join_label<QAM>(Qam<QAM>::axis_label(ire), Qam<QAM>::axis_label(iim));
+}
+
+// Coordinates of a label (inverse of grid_label).
+template <int QAM>
+__device__ __forceinline__ float2 label_point(int lab)
+{
+    constexpr int H = Qam<QAM>::B / 2;
+    constexpr int L = Qam<QAM>::L;
+    int lre = 0, lim = 0;
+#pragma unroll
+    for (int t = 0; t < H; ++t) {
+        lre = (lre << 1) | ((lab >> (2 * (H - 1 - t) + 1)) & 1);
+        lim = (lim << 1) | ((lab >> (2 * (H - 1 - t))) & 1);
+    }
+    int ire = 0, iim = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        if (Qam<QAM>::axis_label(i) == lre) ire = i;
+        if (Qam<QAM>::axis_label(i) == lim) iim = i;
+    }
+    return make_float2(axis_pos<QAM>(ire), axis_pos<QAM>(iim));
 }
 
 // p-th closest point (p >= 3) by (squared distance, label): the 2-D order is
@@ -293,7 +316,7 @@ __host__ __device__ inline int pow2_at_least(int n)
 
 struct DetSmem {
     int off_rc, off_r2, off_invd, off_perm, off_z, off_tab, off_order, off_m, off_best, off_wmin,
-        off_second, off_blab, off_top, off_l2, off_lut, bytes;
+        off_second, off_blab, off_top, off_l2, off_lut, off_rh, off_key2, off_blab2, bytes;
 };
 
 __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym, int WORDS)
@@ -332,6 +355,13 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     o = a16(o + (n_sym + 1) * kList2 * 16);
     s.off_lut = o;  // 2-D label of grid point (ire, iim) at ire * 8 + iim
     o = a16(o + 64);
+    // mixed precision only: R columns as half2 pairs, runner-up key and labels
+    s.off_rh = o;
+    o = a16(o + NT * NT * 8);
+    s.off_key2 = o;
+    o = a16(o + n_sym * chunks * 8);
+    s.off_blab2 = o;
+    o = a16(o + n_sym * chunks * WORDS * 4);
     s.bytes = o;
     return s;
 }
@@ -343,7 +373,9 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
                                                    const Labels<NT, B> &lab, int s,
                                                    unsigned long long *sBest, unsigned *sWmin,
                                                    unsigned *sSecond, uint32_t *sBlab,
-                                                   unsigned *sM, bool want_llr)
+                                                   unsigned *sM, bool want_llr,
+                                                   unsigned long long *sKey2 = nullptr,
+                                                   uint32_t *sBlab2 = nullptr)
 {
     using Lab = Labels<NT, B>;
     constexpr int WORDS = Lab::WORDS;
@@ -364,6 +396,27 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
     Lab bl;
 #pragma unroll
     for (int k = 0; k < WORDS; ++k) bl.w[k] = __shfl_sync(0xffffffffu, lab.w[k], blane);
+    if (sKey2 != nullptr) {
+        // the warp's runner-up row (key and labels), for the FP32 re-check
+        unsigned long long k2 = (active && lane != blane)
+                                    ? (((unsigned long long)db << 32) | ((unsigned)row << 16) |
+                                       (unsigned)(chunk * 32 + lane))
+                                    : ~0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long k3 = __shfl_xor_sync(0xffffffffu, k2, o);
+            k2 = k3 < k2 ? k3 : k2;
+        }
+        const int rlane = (int)(k2 & 31u);
+        uint32_t rw[WORDS];
+#pragma unroll
+        for (int k = 0; k < WORDS; ++k) rw[k] = __shfl_sync(0xffffffffu, lab.w[k], rlane);
+        if (valid && lane == 0) {
+            sKey2[s * chunks + chunk] = k2;
+#pragma unroll
+            for (int k = 0; k < WORDS; ++k) sBlab2[(s * chunks + chunk) * WORDS + k] = rw[k];
+        }
+    }
     if (!valid) return;  // (warp-uniform) second symbol slot beyond n_sym
     if (lane == 0) {
         atomicMin(&sBest[s], key);
@@ -406,7 +459,10 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
     }
 }
 
-template <int NT, int QAM>
+// F16: the interference-cancelled residuals e are kept as half2 (re, im) and
+// updated with two HFMA2 per complex term; b, the ranking and the PED stay in
+// FP32, and the final best and runner-up paths are re-checked in FP32.
+template <int NT, int QAM, bool F16>
 __global__ void __launch_bounds__(kThreads, 2)
 detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
                    const float *__restrict__ inv_diag, const uint8_t *__restrict__ perm,
@@ -440,6 +496,9 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
     __shared__ int s_k1[QAM + 1], s_off1[QAM + 1];
     __shared__ int s_use2;
     uint8_t *sLut = smem + S.off_lut;
+    uint2 *sRh = reinterpret_cast<uint2 *>(smem + S.off_rh);  // {(-Re,-Re), (Im,-Im)} as half2
+    unsigned long long *sKey2 = reinterpret_cast<unsigned long long *>(smem + S.off_key2);
+    uint32_t *sBlab2 = reinterpret_cast<uint32_t *>(smem + S.off_blab2);
     __shared__ int s_kmax;
 
     const int sc = blockIdx.x;
@@ -456,8 +515,16 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
         }
         const int j = i + rem;
         const float2 v = Rp[(size_t)sc * P + k];
-        if (i == j) sR2[i] = v.x * v.x;
-        else sRc[j * NT + i] = v;
+        if (i == j) {
+            sR2[i] = v.x * v.x;
+        } else {
+            sRc[j * NT + i] = v;
+            if constexpr (F16) {
+                const __half2 a = __floats2half2_rn(-v.x, -v.x), b = __floats2half2_rn(v.y, -v.y);
+                sRh[j * NT + i] = make_uint2(*reinterpret_cast<const unsigned *>(&a),
+                                             *reinterpret_cast<const unsigned *>(&b));
+            }
+        }
     }
     for (int k = tid; k < NT; k += kThreads) {
         if (k < nt) {
@@ -582,13 +649,18 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
         RowRanks<NT> pr;
         pr.load(sTab + row * NT);
         float ex[2][NT], ey[2][NT];
+        __half2 eh[2][NT];
 #pragma unroll
         for (int l = 0; l < NT; ++l) {
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
                 const float2 z = sZ[(s0 + k) * NT + l];
-                ex[k][l] = z.x;
-                ey[k][l] = z.y;
+                if constexpr (F16) {
+                    eh[k][l] = __floats2half2_rn(z.x, z.y);
+                } else {
+                    ex[k][l] = z.x;
+                    ey[k][l] = z.y;
+                }
             }
         }
         Lab lab[2];
@@ -619,7 +691,15 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                     float dre[2], dim[2];
 #pragma unroll
                     for (int k = 0; k < 2; ++k) {
-                        const float bx = ex[k][l] * iv, by = ey[k][l] * iv;
+                        float bx, by;
+                        if constexpr (F16) {
+                            const float2 f = __half22float2(eh[k][l]);
+                            bx = f.x * iv;
+                            by = f.y * iv;
+                        } else {
+                            bx = ex[k][l] * iv;
+                            by = ey[k][l] * iv;
+                        }
                         ire[k] = axis_round<QAM>(bx, dre[k]);
                         iim[k] = axis_round<QAM>(by, dim[k]);
                         if (p == 2) {
@@ -660,6 +740,33 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                     d[k] = fmaf(r2, dist[k], d[k]);
                     lab[k].set(l, lb[k]);
                 }
+                if constexpr (F16) {
+                    // e_i -= R_il s: e + (-Re,-Re)*(sx,sy) + (Im,-Im)*(sy,sx)
+                    const uint4 *colh = reinterpret_cast<const uint4 *>(sRh + l * NT);
+                    __half2 sh[2], sw[2];
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        sh[k] = __floats2half2_rn(sx[k], sy[k]);
+                        sw[k] = __floats2half2_rn(sy[k], sx[k]);
+                    }
+#pragma unroll
+                    for (int i2 = 0; i2 < NT / 2; ++i2) {
+                        if (2 * i2 < l) {
+                            const uint4 r = colh[i2];  // entries 2 i2 and 2 i2 + 1
+                            const __half2 a0 = *reinterpret_cast<const __half2 *>(&r.x);
+                            const __half2 b0 = *reinterpret_cast<const __half2 *>(&r.y);
+                            const __half2 a1 = *reinterpret_cast<const __half2 *>(&r.z);
+                            const __half2 b1 = *reinterpret_cast<const __half2 *>(&r.w);
+#pragma unroll
+                            for (int k = 0; k < 2; ++k) {
+                                eh[k][2 * i2] = __hfma2(b0, sw[k], __hfma2(a0, sh[k], eh[k][2 * i2]));
+                                if (2 * i2 + 1 < l)
+                                    eh[k][2 * i2 + 1] =
+                                        __hfma2(b1, sw[k], __hfma2(a1, sh[k], eh[k][2 * i2 + 1]));
+                            }
+                        }
+                    }
+                } else {
                 const float4 *col = reinterpret_cast<const float4 *>(sRc + l * NT);
 #pragma unroll
                 for (int i2 = 0; i2 < NT / 2; ++i2) {
@@ -678,12 +785,15 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                         }
                     }
                 }
+                }
             }
         }
         warp_reduce_symbol<NT, B>(true, active, row, chunk, chunks, nt, d[0], lab[0], s0, sBest,
-                                  sWmin, sSecond, sBlab, sM, llr != nullptr);
+                                  sWmin, sSecond, sBlab, sM, llr != nullptr,
+                                  F16 ? sKey2 : nullptr, sBlab2);
         warp_reduce_symbol<NT, B>(has1, active, row, chunk, chunks, nt, d[1], lab[1], s0 + 1,
-                                  sBest, sWmin, sSecond, sBlab, sM, llr != nullptr);
+                                  sBest, sWmin, sSecond, sBlab, sM, llr != nullptr,
+                                  F16 ? sKey2 : nullptr, sBlab2);
     }
     __syncthreads();
 
@@ -694,6 +804,70 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
         const unsigned bd = (unsigned)(key >> 32);
         int bc = (int)((key & 0xffffu) >> 5);  // chunk of the best row's sorted position
         if (bc >= chunks) bc = 0;
+        if constexpr (F16) {
+            // runner-up: the best chunk's second row or another chunk's best
+            unsigned long long rk = ~0ull;
+            int rsrc = -1;  // >= 0: sBlab of chunk rsrc; -1: sBlab2 of chunk bc
+            for (int c = lane; c < chunks; c += 32) {
+                const unsigned long long kc = c == bc ? sKey2[s * chunks + c]
+                                                      : ((unsigned long long)sWmin[s * chunks + c] << 32);
+                if (kc < rk) {
+                    rk = kc;
+                    rsrc = c == bc ? -1 : c;
+                }
+            }
+            // warp min of (rk, rsrc): chunk keys of other chunks only carry the PED
+            // (their rows are unique per chunk), ties -> lower chunk
+            unsigned long long best_rk = rk;
+            int best_src = rsrc;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best_rk, o);
+                const int s2 = __shfl_xor_sync(0xffffffffu, best_src, o);
+                if (k2 < best_rk || (k2 == best_rk && s2 < best_src)) {
+                    best_rk = k2;
+                    best_src = s2;
+                }
+            }
+            // FP32 metrics ||z - R s||^2 of both paths: lane l owns row l of R
+            const uint32_t *w1 = sBlab + (s * chunks + bc) * WORDS;
+            const uint32_t *w2 = best_src < 0 ? sBlab2 + (s * chunks + bc) * WORDS
+                                              : sBlab + (s * chunks + best_src) * WORDS;
+            const bool have2 = best_rk != ~0ull;
+            float m1 = 0.f, m2 = 0.f;
+            if (lane < nt) {
+                const float2 z = sZ[s * NT + lane];
+                float t1x = z.x, t1y = z.y, t2x = z.x, t2y = z.y;
+                for (int j = lane; j < nt; ++j) {
+                    const float2 r = j == lane ? make_float2(sqrtf(sR2[j]), 0.f) : sRc[j * NT + lane];
+                    const int lb1 = (w1[j / Lab::PER] >> (B * (j % Lab::PER))) & ((1 << B) - 1);
+                    const int lb2 = (w2[j / Lab::PER] >> (B * (j % Lab::PER))) & ((1 << B) - 1);
+                    const float2 p1 = label_point<QAM>(lb1), p2 = label_point<QAM>(lb2);
+                    t1x -= r.x * p1.x - r.y * p1.y;
+                    t1y -= r.x * p1.y + r.y * p1.x;
+                    t2x -= r.x * p2.x - r.y * p2.y;
+                    t2y -= r.x * p2.y + r.y * p2.x;
+                }
+                m1 = t1x * t1x + t1y * t1y;
+                m2 = t2x * t2x + t2y * t2y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                m1 += __shfl_xor_sync(0xffffffffu, m1, o);
+                m2 += __shfl_xor_sync(0xffffffffu, m2, o);
+            }
+            if (!have2) m2 = INFINITY;
+            const bool swap = have2 && m2 < m1;
+            const uint32_t *wb = swap ? w2 : w1;
+            if (lane < nt) {
+                const uint32_t w = wb[lane / Lab::PER];
+                hard[det * nt + sPerm[lane]] = (uint8_t)((w >> (B * (lane % Lab::PER))) & ((1 << B) - 1));
+            }
+            if (ped2 != nullptr && lane == 0) {
+                ped2[det * 2] = fminf(m1, m2);
+                ped2[det * 2 + 1] = fmaxf(m1, m2);
+            }
+        } else {
         if (lane < nt) {
             const uint32_t w = sBlab[(s * chunks + bc) * WORDS + lane / Lab::PER];
             hard[det * nt + sPerm[lane]] = (uint8_t)((w >> (B * (lane % Lab::PER))) & ((1 << B) - 1));
@@ -707,6 +881,7 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                 ped2[det * 2] = __uint_as_float(bd);
                 ped2[det * 2 + 1] = __uint_as_float(sec);
             }
+        }
         }
         if (llr != nullptr) {
             for (int slot = lane; slot < nt * B; slot += 32) {
@@ -722,40 +897,52 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
     }
 }
 
-template <int NT, int QAM>
-cudaError_t launch_tpl(int n_sc, int n_sym, int nt, int n_pe, float sigma2, const float2 *R,
-                       const float *inv_diag, const uint8_t *perm, const uint8_t *paths,
-                       const float2 *Z, uint8_t *hard, float *llr, float *ped2, unsigned *status,
-                       cudaStream_t stream)
+template <int NT, int QAM, bool F16>
+cudaError_t launch_prec(int n_sc, int n_sym, int nt, int n_pe, float sigma2, const float2 *R,
+                        const float *inv_diag, const uint8_t *perm, const uint8_t *paths,
+                        const float2 *Z, uint8_t *hard, float *llr, float *ped2,
+                        unsigned *status, cudaStream_t stream)
 {
     const DetSmem S = det_layout(NT, Qam<QAM>::B, n_pe, n_sym, Labels<NT, Qam<QAM>::B>::WORDS);
     const size_t smem = S.bytes;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(detect_walk_kernel<NT, QAM>,
+        cudaError_t e = cudaFuncSetAttribute(detect_walk_kernel<NT, QAM, F16>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    detect_walk_kernel<NT, QAM><<<n_sc, kThreads, smem, stream>>>(
+    detect_walk_kernel<NT, QAM, F16><<<n_sc, kThreads, smem, stream>>>(
         n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard, llr, ped2, status);
     return cudaGetLastError();
+}
+
+template <int NT, int QAM>
+cudaError_t launch_tpl(int n_sc, int n_sym, int nt, int n_pe, float sigma2, const float2 *R,
+                       const float *inv_diag, const uint8_t *perm, const uint8_t *paths,
+                       const float2 *Z, uint8_t *hard, float *llr, float *ped2, unsigned *status,
+                       bool f16, cudaStream_t stream)
+{
+    return f16 ? launch_prec<NT, QAM, true>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm,
+                                            paths, Z, hard, llr, ped2, status, stream)
+               : launch_prec<NT, QAM, false>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm,
+                                             paths, Z, hard, llr, ped2, status, stream);
 }
 
 template <int NT>
 cudaError_t launch_nt(int qam, int n_sc, int n_sym, int nt, int n_pe, float sigma2,
                       const float2 *R, const float *inv_diag, const uint8_t *perm,
                       const uint8_t *paths, const float2 *Z, uint8_t *hard, float *llr,
-                      float *ped2, unsigned *status, cudaStream_t stream)
+                      float *ped2, unsigned *status, bool f16, cudaStream_t stream)
 {
     switch (qam) {
     case 4:
         return launch_tpl<NT, 4>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                                 llr, ped2, status, stream);
+                                 llr, ped2, status, f16, stream);
     case 16:
         return launch_tpl<NT, 16>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                                  llr, ped2, status, stream);
+                                  llr, ped2, status, f16, stream);
     default:
         return launch_tpl<NT, 64>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                                  llr, ped2, status, stream);
+                                  llr, ped2, status, f16, stream);
     }
 }
 
@@ -764,17 +951,17 @@ cudaError_t launch_nt(int qam, int n_sc, int n_sym, int nt, int n_pe, float sigm
 cudaError_t launch_detect(int n_sc, int n_sym, int nt, int qam, int n_pe, float sigma2,
                           const float2 *R, const float *inv_diag, const uint8_t *perm,
                           const uint8_t *paths, const float2 *Z, uint8_t *hard, float *llr,
-                          float *ped2, unsigned *status, cudaStream_t stream)
+                          float *ped2, unsigned *status, bool f16, cudaStream_t stream)
 {
     if (n_sc == 0) return cudaSuccess;
     if (nt <= 4)
         return launch_nt<4>(qam, n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                            llr, ped2, status, stream);
+                            llr, ped2, status, f16, stream);
     if (nt <= 8)
         return launch_nt<8>(qam, n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                            llr, ped2, status, stream);
+                            llr, ped2, status, f16, stream);
     return launch_nt<16>(qam, n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                         llr, ped2, status, stream);
+                         llr, ped2, status, f16, stream);
 }
 
 }  // namespace mpnl

@@ -185,11 +185,10 @@ int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, float si
     return MPNL_OK;
 }
 
-int mpnl_detect(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, const float *inv_diag,
-                const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
-                uint8_t *hard, float *llr, float *ped2, void *ws, void *stream)
+static int detect_impl(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, const float *inv_diag,
+                       const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
+                       uint8_t *hard, float *llr, float *ped2, void *stream, bool f16)
 {
-    (void)ws;
     MPNL_TRY(begin(ctx));
     MPNL_TRY(check_dims(ctx, d, true));
     MPNL_TRY(check_sigma2(ctx, sigma2));
@@ -204,9 +203,25 @@ int mpnl_detect(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, const float *i
     MPNL_TRY(check_ptr(ctx, ped2, 4, "ped2", true));
     cudaError_t e = mpnl::launch_detect(d->n_sc, d->n_sym, d->nt, d->qam, d->n_pe, sigma2,
                                         (const float2 *)R, inv_diag, perm, paths, (const float2 *)Z,
-                                        hard, llr, ped2, ctx->status, (cudaStream_t)stream);
+                                        hard, llr, ped2, ctx->status, f16, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, "detect launch", e);
     return MPNL_OK;
+}
+
+int mpnl_detect(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, const float *inv_diag,
+                const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
+                uint8_t *hard, float *llr, float *ped2, void *ws, void *stream)
+{
+    (void)ws;
+    return detect_impl(ctx, d, R, inv_diag, perm, paths, Z, sigma2, hard, llr, ped2, stream, false);
+}
+
+int mpnl_detect_mixed(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, const float *inv_diag,
+                      const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
+                      uint8_t *hard, float *llr, float *ped2, void *ws, void *stream)
+{
+    (void)ws;
+    return detect_impl(ctx, d, R, inv_diag, perm, paths, Z, sigma2, hard, llr, ped2, stream, true);
 }
 
 int mpnl_linear_mmse(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const void *Y,

@@ -15,10 +15,12 @@ cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, const float2 
 cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,
                                 const float2 *R, uint8_t *paths, cudaStream_t stream);
 
+// f16: residuals in half2 with FP32 ranking / PED and an FP32 re-check of
+// the best and runner-up paths (mpnl_detect_mixed); false: all FP32.
 cudaError_t launch_detect(int n_sc, int n_sym, int nt, int qam, int n_pe, float sigma2,
                           const float2 *R, const float *inv_diag, const uint8_t *perm,
                           const uint8_t *paths, const float2 *Z, uint8_t *hard, float *llr,
-                          float *ped2, unsigned *status, cudaStream_t stream);
+                          float *ped2, unsigned *status, bool f16, cudaStream_t stream);
 
 cudaError_t launch_mmse(int n_sc, int n_sym, int nr, int nt, int qam, float sigma2,
                         const float2 *H, const float2 *Y, uint8_t *hard, float *llr,

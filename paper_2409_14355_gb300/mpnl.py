@@ -35,8 +35,9 @@ ERR_CUDA = -3
 ERR_TIMEOUT = -4
 
 EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_bytes",
-            "mpnl_preprocess", "mpnl_select_paths", "mpnl_detect", "mpnl_linear_mmse",
-            "mpnl_check_status")
+            "mpnl_preprocess", "mpnl_select_paths", "mpnl_detect", "mpnl_detect_mixed",
+            "mpnl_linear_mmse", "mpnl_check_status")
+PRECISIONS = ("fp32", "fp16")
 
 
 class MpnlError(RuntimeError):
@@ -80,6 +81,8 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_select_paths.restype = I
         lib.mpnl_detect.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
         lib.mpnl_detect.restype = I
+        lib.mpnl_detect_mixed.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
+        lib.mpnl_detect_mixed.restype = I
         lib.mpnl_linear_mmse.argtypes = [P, D, P, P, F, P, P, P, P]
         lib.mpnl_linear_mmse.restype = I
         lib.mpnl_check_status.argtypes = [P, P]
@@ -174,8 +177,12 @@ def select_paths(R: torch.Tensor, sigma2: float, qam: int, n_pe: int, nt: int, o
 
 
 def detect(R, inv_diag, perm, paths, Z, sigma2: float, qam: int, want_llr: bool = True,
-           want_ped2: bool = True, out=None):
-    """Walks + argmin + max-log LLRs.  Returns (hard, llr or None, ped2 or None)."""
+           want_ped2: bool = True, out=None, precision: str = "fp32"):
+    """Walks + argmin + max-log LLRs.  Returns (hard, llr or None, ped2 or None).
+    precision "fp16" selects mpnl_detect_mixed (FP16 residuals, FP32 ranking,
+    PED and re-check of the best and runner-up paths)."""
+    if precision not in PRECISIONS:
+        raise MpnlError(ERR_INVALID_ARG, f"precision {precision!r} not in {PRECISIONS}")
     dev = _dev_of(R)
     n_sc, n_sym, nt = Z.shape
     n_pe = paths.shape[1]
@@ -193,9 +200,10 @@ def detect(R, inv_diag, perm, paths, Z, sigma2: float, qam: int, want_llr: bool 
         hard, llr, ped2 = out
     ctx = context(dev.index)
     d = Dims(n_sc, n_sym, nt, nt, qam, n_pe)
-    st = load_library().mpnl_detect(ctx, ctypes.byref(d), _ptr(R), _ptr(inv_diag), _ptr(perm),
-                                    _ptr(paths), _ptr(Z), float(sigma2), _ptr(hard), _ptr(llr),
-                                    _ptr(ped2), None, _stream(dev))
+    lib = load_library()
+    fn = lib.mpnl_detect if precision == "fp32" else lib.mpnl_detect_mixed
+    st = fn(ctx, ctypes.byref(d), _ptr(R), _ptr(inv_diag), _ptr(perm), _ptr(paths), _ptr(Z),
+            float(sigma2), _ptr(hard), _ptr(llr), _ptr(ped2), None, _stream(dev))
     _raise(st, ctx)
     return hard, llr, ped2
 
@@ -249,20 +257,21 @@ class SlotBuffers:
         self.mmse_llr = torch.empty((n_sc, n_sym, nt, B), dtype=torch.float32, **kw) if mmse else None
 
 
-def run_slot(buf: SlotBuffers, H, Y, sigma2: float, mmse: bool = True) -> None:
+def run_slot(buf: SlotBuffers, H, Y, sigma2: float, mmse: bool = True,
+             precision: str = "fp32") -> None:
     """The whole path on device tensors H, Y (enqueued on the current stream):
     preprocess -> select_paths -> detect (hard, LLR, PED pair) [-> MMSE]."""
     n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
     preprocess(H, Y, out=(buf.R, buf.inv_diag, buf.perm, buf.Z))
     select_paths(buf.R, sigma2, qam, n_pe, nt, out=buf.paths)
     detect(buf.R, buf.inv_diag, buf.perm, buf.paths, buf.Z, sigma2, qam,
-           out=(buf.hard, buf.llr, buf.ped2))
+           out=(buf.hard, buf.llr, buf.ped2), precision=precision)
     if mmse:
         linear_mmse(H, Y, sigma2, qam, out=(buf.mmse_hard, buf.mmse_llr))
 
 
 def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
-                buffers: SlotBuffers | None = None, device=None):
+                buffers: SlotBuffers | None = None, device=None, precision: str = "fp32"):
     """End-to-end call a user makes: accepts host (ideally pinned) or device
     tensors.  Host inputs are copied to the device, the path runs, and the
     hard decisions and LLRs (and MMSE outputs with ``mmse``) come back as host
@@ -279,7 +288,7 @@ def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
         Hd, Yd = buf.H, buf.Y
     else:
         Hd, Yd = H, Y
-    run_slot(buf, Hd, Yd, sigma2, mmse)
+    run_slot(buf, Hd, Yd, sigma2, mmse, precision)
     out = dict(hard=buf.hard, llr=buf.llr, ped2=buf.ped2)
     if mmse:
         out["mmse_hard"] = buf.mmse_hard
