@@ -63,13 +63,14 @@ def _load():
             D = ctypes.c_double
             lib.orc_constellation.argtypes = [I, P]
             lib.orc_sqrd.argtypes = [I, I, P, P, P, P, P]
+            lib.orc_sqrd_mmse.argtypes = [I, I, P, D, P, P, P, P]
             lib.orc_qhy.argtypes = [I, I, I, P, P, P]
             lib.orc_select_paths.argtypes = [I, I, P, D, I, P, P, P]
             lib.orc_detect.argtypes = [I, I, I, P, P, P, I, P, D, P, P, P, P, P, P, D, P]
             lib.orc_mmse.argtypes = [I, I, I, I, P, P, D, P, P, P, P]
             lib.orc_detect_slot.argtypes = [I, I, I, I, I, I, D, P, P, P, P, P, P, P, P, P,
-                                            P, P, P, P, P, I, D, P]
-            for f in ("orc_constellation", "orc_sqrd", "orc_qhy", "orc_select_paths",
+                                            P, P, P, P, P, I, D, P, I]
+            for f in ("orc_constellation", "orc_sqrd", "orc_sqrd_mmse", "orc_qhy", "orc_select_paths",
                       "orc_detect", "orc_mmse", "orc_detect_slot"):
                 getattr(lib, f).restype = I
             _lib = lib
@@ -106,6 +107,20 @@ def sqrd(H):
     perm = np.zeros(nt, np.int32)
     gap = np.zeros(nt, np.float64)
     _check(_load().orc_sqrd(nr, nt, _p(H), _p(Q), _p(R), _p(perm), _p(gap)), "sqrd")
+    return Q, R, perm, gap
+
+
+def sqrd_mmse(H, sigma2: float):
+    """MMSE-extended sorted QR of [H; sigma I] -> (Q_a [(nr+nt)][nt], R, perm, gap).
+    z = Q_a^H [y; 0] = qhy(Q_a[:nr], Y)."""
+    H = _c128(H)
+    nr, nt = H.shape
+    Q = np.zeros((nr + nt, nt), np.complex128)
+    R = np.zeros((nt, nt), np.complex128)
+    perm = np.zeros(nt, np.int32)
+    gap = np.zeros(nt, np.float64)
+    _check(_load().orc_sqrd_mmse(nr, nt, _p(H), float(sigma2), _p(Q), _p(R), _p(perm), _p(gap)),
+           "sqrd_mmse")
     return Q, R, perm, gap
 
 
@@ -182,7 +197,7 @@ def mmse(H, Y, sigma2: float, qam: int):
 
 
 def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, paths=None, n_threads: int = 0,
-                with_mmse: bool = False, tie_eps: float = 0.0):
+                with_mmse: bool = False, tie_eps: float = 0.0, mmse_qr: bool = False):
     """Steps 1-6 (and 7 with ``with_mmse``) over a whole slot.
 
     H: [n_sc][nr][nt], Y: [n_sc][n_sym][nr] (any complex dtype; promoted to
@@ -210,7 +225,7 @@ def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, paths=None, n_threads:
     st = _load().orc_detect_slot(n_sc, n_sym, nr, nt, qam, n_pe, float(sigma2), _p(H), _p(Y),
                                  _p(pin), _p(hard), _p(llr), _p(ped2), _p(R), _p(perm), _p(Z),
                                  _p(paths_out), _p(gap), _p(margin), _p(mh), _p(ml),
-                                 int(n_threads), float(tie_eps), _p(flip))
+                                 int(n_threads), float(tie_eps), _p(flip), int(mmse_qr))
     _check(st, "detect_slot")
     out = dict(hard=hard, llr=llr, ped2=ped2, R=R, perm=perm, Z=Z, paths=paths_out,
                sqrd_gap=gap, margin=margin, flip_floor=flip, threads=st)

@@ -185,6 +185,33 @@ int orc_sqrd(int nr, int nt, const double *H, double *Q, double *R, int *perm, d
     return 0;
 }
 
+/* ---------------------------------------------------------------------------
+ * Step 1 for more users than antennas (Nt > Nr, the regime of §III-IV where
+ * MPNL serves e.g. 12 streams on 7 antennas).  Reading: the MMSE-extended
+ * sorted QR (Wuebben et al. 2003): the SQRD above applied to the augmented
+ * channel H_a = [H; sigma I] ((nr + nt) x nt) and y_a = [y; 0].  Then
+ * ||y_a - H_a s||^2 = ||y - H s||^2 + sigma2 ||s||^2, R is nt x nt and
+ * regular for any nr, and z = Q_a^H y_a uses only the top nr rows of Q_a.
+ * Q: [(nr + nt)][nt].
+ * ------------------------------------------------------------------------- */
+static void augment(int nr, int nt, const cplx *H, double sigma2, cplx *Ha)
+{
+    double sg = sqrt(sigma2);
+    for (int r = 0; r < nr + nt; r++)
+        for (int c = 0; c < nt; c++)
+            Ha[r * nt + c] = r < nr ? H[r * nt + c] : (r - nr == c ? sg : 0.0);
+}
+
+int orc_sqrd_mmse(int nr, int nt, const double *H, double sigma2, double *Q, double *R, int *perm,
+                  double *gap)
+{
+    if (nt < 1 || nt > ORC_MAX_NT || nr < 1 || nr + nt > ORC_MAX_NR || !(sigma2 > 0.0)) return -1;
+    cplx Ha[ORC_MAX_NR * ORC_MAX_NT];
+    augment(nr, nt, (const cplx *)H, sigma2, Ha);
+    sqrd(nr + nt, nt, Ha, (cplx *)Q, (cplx *)R, perm, gap);
+    return 0;
+}
+
 /* Step 2: z = Q^H y for each OFDM symbol.  Y: [n_sym][nr], Z: [n_sym][nt]. */
 static void qhy(int nr, int nt, int n_sym, const cplx *Q, const cplx *Y, cplx *Z)
 {
@@ -590,7 +617,8 @@ static int mmse_sc(int nr, int nt, int qam, int n_sym, const cplx *H, const cplx
 int orc_mmse(int nr, int nt, int qam, int n_sym, const double *H, const double *Y, double sigma2,
              unsigned char *hard, double *llr, double *xt, double *nu)
 {
-    if (nt < 1 || nt > ORC_MAX_NT || nr < nt || nr > ORC_MAX_NR || !bits_of(qam)) return -1;
+    /* A = H^H H + sigma2 I is positive definite for any nr, so nt > nr is fine */
+    if (nt < 1 || nt > ORC_MAX_NT || nr < 1 || nr > ORC_MAX_NR || !bits_of(qam)) return -1;
     if (!(sigma2 > 0.0)) return -1;
     return mmse_sc(nr, nt, qam, n_sym, (const cplx *)H, (const cplx *)Y, sigma2, hard, llr,
                    (cplx *)xt, nu);
@@ -605,7 +633,9 @@ int orc_mmse(int nr, int nt, int qam, int n_sym, const double *H, const double *
  * llr, ped2): R [n_sc][nt][nt], perm [n_sc][nt], Z [n_sc][n_sym][nt],
  * paths_out [n_sc][n_pe][nt], sqrd_gap [n_sc][nt], margin [n_sc][n_sym],
  * mmse_hard [n_sc][n_sym][nt], mmse_llr [n_sc][n_sym][nt][B],
- * flip_floor [n_sc][n_sym] (with tie_eps, as for orc_detect).
+ * flip_floor [n_sc][n_sym] (with tie_eps, as for orc_detect).  mmse_qr != 0
+ * replaces step 1 by the MMSE-extended sorted QR (orc_sqrd_mmse), which also
+ * allows nt > nr.
  * Returns the number of threads used (>0) or a negative error.
  * ------------------------------------------------------------------------- */
 typedef struct {
@@ -615,6 +645,7 @@ typedef struct {
     const unsigned char *paths_in;
     double *R, *Z, *ped2, *llr, *sqrd_gap, *margin, *mmse_llr, *flip_floor;
     double tie_eps;
+    int mmse_qr;
     int *perm;
     unsigned char *paths_out, *hard, *mmse_hard;
     int sc_begin, sc_end;
@@ -625,7 +656,7 @@ static void *slot_worker(void *arg)
 {
     orc_job *j = (orc_job *)arg;
     int nr = j->nr, nt = j->nt, ns = j->n_sym, npe = j->n_pe, B = bits_of(j->qam);
-    cplx *Q = (cplx *)malloc(sizeof(cplx) * nr * nt);
+    cplx *Q = (cplx *)malloc(sizeof(cplx) * (nr + nt) * nt);
     cplx *R = (cplx *)malloc(sizeof(cplx) * nt * nt);
     cplx *Z = (cplx *)malloc(sizeof(cplx) * ns * nt);
     unsigned char *paths = (unsigned char *)malloc((size_t)npe * nt);
@@ -639,7 +670,15 @@ static void *slot_worker(void *arg)
         const cplx *Y = (const cplx *)j->Y + (size_t)sc * ns * nr;
         int perm[ORC_MAX_NT];
         double gap[ORC_MAX_NT];
-        sqrd(nr, nt, H, Q, R, perm, gap);
+        if (j->mmse_qr) {
+            /* Q_a is (nr + nt) x nt; z = Q_a^H [y; 0] reads its top nr rows,
+             * which with row stride nt are Q_a's first nr rows */
+            cplx Ha[ORC_MAX_NR * ORC_MAX_NT];
+            augment(nr, nt, H, j->sigma2, Ha);
+            sqrd(nr + nt, nt, Ha, Q, R, perm, gap);
+        } else {
+            sqrd(nr, nt, H, Q, R, perm, gap);
+        }
         qhy(nr, nt, ns, Q, Y, Z);
         const unsigned char *pt;
         if (j->paths_in) {
@@ -690,11 +729,12 @@ int orc_detect_slot(int n_sc, int n_sym, int nr, int nt, int qam, int n_pe, doub
                     unsigned char *hard, double *llr, double *ped2, double *R, int *perm, double *Z,
                     unsigned char *paths_out, double *sqrd_gap, double *margin,
                     unsigned char *mmse_hard, double *mmse_llr, int n_threads, double tie_eps,
-                    double *flip_floor)
+                    double *flip_floor, int mmse_qr)
 {
-    if (n_sc < 0 || n_sym < 1 || nt < 1 || nt > ORC_MAX_NT || nr < nt || nr > ORC_MAX_NR ||
-        !bits_of(qam) || n_pe < 1 || n_pe > ORC_MAX_NPE || !(sigma2 > 0.0))
+    if (n_sc < 0 || n_sym < 1 || nt < 1 || nt > ORC_MAX_NT || nr < 1 || !bits_of(qam) ||
+        n_pe < 1 || n_pe > ORC_MAX_NPE || !(sigma2 > 0.0))
         return -1;
+    if (mmse_qr ? nr + nt > ORC_MAX_NR : (nr < nt || nr > ORC_MAX_NR)) return -1;
     if ((double)n_pe > ipow((double)qam, nt)) return -1;
     if (n_threads <= 0) {
         long c = sysconf(_SC_NPROCESSORS_ONLN);
@@ -733,6 +773,7 @@ int orc_detect_slot(int n_sc, int n_sym, int nr, int nt, int qam, int n_pe, doub
         j->mmse_hard = mmse_hard;
         j->tie_eps = tie_eps;
         j->flip_floor = flip_floor;
+        j->mmse_qr = mmse_qr;
         j->sc_begin = (int)((long)n_sc * t / n_threads);
         j->sc_end = (int)((long)n_sc * (t + 1) / n_threads);
     }

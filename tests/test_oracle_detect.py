@@ -161,3 +161,36 @@ def test_mrc_qpsk_ber_matches_closed_form():
     want = mrc_rayleigh_bpsk_ber(1.0 / (2.0 * sl.sigma2), 2)
     sd = math.sqrt(want * (1 - want) / nbits)
     assert abs(ber - want) < 4 * sd + 1e-4, (ber, want)
+
+
+@pytest.mark.parametrize("nr,nt,qam", [(2, 3, 4), (3, 4, 4), (2, 2, 16)])
+def test_mmse_qr_full_enumeration_is_regularised_ml(nr, nt, qam):
+    # More users than antennas: with the MMSE-extended QR and a complete list
+    # the decision is argmin ||y - H s||^2 + sigma2 ||s||^2 over all of Q^nt.
+    sl = inputs.make_slot(nr, nt, qam, 5, 14, 8.0, "iid", 0.3, 123 + nt)
+    pts = oracle.constellation(qam)
+    cand = all_label_vectors(qam, nt)
+    cand_s = pts[cand]
+    n_all = qam ** nt
+    out = oracle.detect_slot(sl.H, sl.Y, sl.sigma2, qam, n_all, mmse_qr=True)
+    for c in range(sl.n_sc):
+        H = sl.H[c].astype(np.complex128)
+        Y = sl.Y[c].astype(np.complex128)
+        for s in range(sl.n_sym):
+            met = ml_metrics(H, Y[s], cand_s) + sl.sigma2 * np.sum(np.abs(cand_s) ** 2, axis=1)
+            best = np.argmin(met)
+            np.testing.assert_array_equal(out["hard"][c, s], cand[best])
+            z = out["Z"][c, s]
+            dml = out["ped2"][c, s, 0] + np.sum(np.abs(Y[s]) ** 2) - np.sum(np.abs(z) ** 2)
+            assert abs(dml - met[best]) <= 1e-11 * max(met[best], 1.0)
+
+
+def test_mmse_baseline_handles_more_users_than_antennas():
+    sl = inputs.make_slot(4, 6, 16, 3, 14, 20.0, "iid", 0.3, 5)
+    for c in range(sl.n_sc):
+        H = sl.H[c].astype(np.complex128)
+        out = oracle.mmse(H, sl.Y[c], sl.sigma2, 16)
+        W = np.linalg.solve(H.conj().T @ H + sl.sigma2 * np.eye(6), H.conj().T)
+        mu = np.real(np.diag(W @ H))
+        np.testing.assert_allclose(out["xt"] * mu, sl.Y[c].astype(np.complex128) @ W.T,
+                                   rtol=1e-10, atol=1e-12)

@@ -88,3 +88,25 @@ def test_z_preserves_energy_in_column_space():
         np.testing.assert_allclose(np.sum(np.abs(Y) ** 2, 1),
                                    np.sum(np.abs(Z) ** 2, 1) + np.sum(np.abs(orth) ** 2, 0),
                                    rtol=1e-12)
+
+
+@pytest.mark.parametrize("nr,nt", [(7, 12), (2, 3), (8, 8), (4, 16), (16, 16)])
+def test_mmse_extended_qr_factorises_the_augmented_channel(nr, nt):
+    sl = inputs.make_slot(nr, nt, 4, 6, 3, 15.0, "iid", 0.3, 40 + nr + nt)
+    for c in range(sl.n_sc):
+        H = sl.H[c].astype(np.complex128)
+        Q, R, perm, _ = oracle.sqrd_mmse(H, sl.sigma2)
+        Ha = np.vstack([H, np.sqrt(sl.sigma2) * np.eye(nt)])
+        P = np.eye(nt)[:, perm]
+        assert np.linalg.norm(Ha @ P - Q @ R) / np.linalg.norm(Ha) < 1e-13
+        assert np.linalg.norm(Q.conj().T @ Q - np.eye(nt)) < 1e-13
+        assert np.allclose(np.tril(R, -1), 0) and np.all(np.real(np.diag(R)) > 0)
+        # the pivot order is the minimum residual norm of the augmented columns
+        for i in range(nt):
+            if i:
+                Qi, _ = np.linalg.qr(Ha[:, perm[:i]])
+                res = Ha - Qi @ (Qi.conj().T @ Ha)
+            else:
+                res = Ha
+            rest = [k for k in range(nt) if k not in perm[:i]]
+            assert perm[i] == min(rest, key=lambda k: (np.linalg.norm(res[:, k]), k))
