@@ -33,7 +33,8 @@
  * - Return value: MPNL_OK (0) or a negative MPNL_ERR_*.  On error nothing was
  *   enqueued, except MPNL_ERR_CUDA from a failed launch; mpnl_last_error()
  *   returns the message.  No call prints, aborts or traps.
- * - Limits: 1 <= nt <= nr <= 32, nt <= 16, qam in {4, 16, 64},
+ * - Limits: 1 <= nt <= 16, 1 <= nr <= 32 (nt <= nr for mpnl_preprocess,
+ *   nr + nt <= 32 for mpnl_preprocess_mmse), qam in {4, 16, 64},
  *   1 <= n_sym <= 32, 1 <= n_pe <= min(1024, qam^nt), n_sc >= 0 (0 is a
  *   no-op), sigma2 > 0 and finite.
  */
@@ -103,6 +104,17 @@ size_t mpnl_workspace_bytes(const mpnl_dims *dims);
  *   Z        out c64 [n_sc][n_sym][nt]       z = Q^H y  (Q is not stored) */
 int mpnl_preprocess(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const void *Y, void *R,
                     float *inv_diag, uint8_t *perm, void *Z, void *ws, void *stream);
+
+/* MMSE-extended pre-processing, for more users than antennas (the regime of
+ * §III-IV where MPNL serves e.g. 12 streams on 7 antennas) and usable for any
+ * nt: the sorted QR of the augmented channel [H; sqrt(sigma2) I] and
+ * z = Q_a^H [y; 0] (Wuebben et al. 2003's MMSE-SQRD).  The walks of
+ * mpnl_detect then minimise ||y - H s||^2 + sigma2 ||s||^2 instead of
+ * ||y - H s||^2.  Same outputs and layouts as mpnl_preprocess; requires
+ * nr + nt <= MPNL_MAX_NR (nt > nr allowed) and sigma2 > 0. */
+int mpnl_preprocess_mmse(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const void *Y,
+                         float sigma2, void *R, float *inv_diag, uint8_t *perm, void *Z, void *ws,
+                         void *stream);
 
 /* Position-vector pre-selection (§II: found "before any transmission
  * begins" from the channel; §III-B: N_p).  Per level, gamma_l = R_ll^2 /

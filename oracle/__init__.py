@@ -112,7 +112,7 @@ def sqrd(H):
 
 def sqrd_mmse(H, sigma2: float):
     """MMSE-extended sorted QR of [H; sigma I] -> (Q_a [(nr+nt)][nt], R, perm, gap).
-    z = Q_a^H [y; 0] = qhy(Q_a[:nr], Y)."""
+    z = Q_a^H [y; 0] = qhy(Q_a, [Y | 0])."""
     H = _c128(H)
     nr, nt = H.shape
     Q = np.zeros((nr + nt, nt), np.complex128)

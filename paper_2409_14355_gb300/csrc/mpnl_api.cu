@@ -39,14 +39,27 @@ int cuda_fail(mpnl_ctx *ctx, const char *what, cudaError_t e)
 
 int bits_of(int qam) { return qam == 4 ? 2 : qam == 16 ? 4 : qam == 64 ? 6 : 0; }
 
-int check_dims(mpnl_ctx *ctx, const mpnl_dims *d, bool need_pe)
+// Rules for nr: the plain sorted QR needs nt <= nr <= MPNL_MAX_NR (a square
+// or tall channel); the MMSE-extended one factors nr + nt rows and needs
+// nr + nt <= MPNL_MAX_NR; the other calls take nr from the caller's buffers
+// (MMSE baseline) or ignore it (selection, walks) and need 1 <= nr <= MAX.
+enum NrRule { kNrTall, kNrAugmented, kNrAny };
+
+int check_dims(mpnl_ctx *ctx, const mpnl_dims *d, bool need_pe, NrRule nr_rule = kNrAny)
 {
     if (!d) return fail(ctx, MPNL_ERR_INVALID_ARG, "dims is NULL");
     if (d->n_sc < 0) return fail(ctx, MPNL_ERR_INVALID_ARG, "n_sc=%d < 0", d->n_sc);
     if (d->nt < 1 || d->nt > MPNL_MAX_NT)
         return fail(ctx, MPNL_ERR_INVALID_ARG, "nt=%d outside 1..%d", d->nt, MPNL_MAX_NT);
-    if (d->nr < d->nt || d->nr > MPNL_MAX_NR)
-        return fail(ctx, MPNL_ERR_INVALID_ARG, "nr=%d outside nt(=%d)..%d", d->nr, d->nt, MPNL_MAX_NR);
+    if (d->nr < 1 || d->nr > MPNL_MAX_NR)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "nr=%d outside 1..%d", d->nr, MPNL_MAX_NR);
+    if (nr_rule == kNrTall && d->nr < d->nt)
+        return fail(ctx, MPNL_ERR_INVALID_ARG,
+                    "nr=%d < nt=%d: use mpnl_preprocess_mmse for more users than antennas", d->nr,
+                    d->nt);
+    if (nr_rule == kNrAugmented && d->nr + d->nt > MPNL_MAX_NR)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "nr + nt = %d exceeds %d", d->nr + d->nt,
+                    MPNL_MAX_NR);
     if (d->n_sym < 1 || d->n_sym > MPNL_MAX_NSYM)
         return fail(ctx, MPNL_ERR_INVALID_ARG, "n_sym=%d outside 1..%d", d->n_sym, MPNL_MAX_NSYM);
     if (!bits_of(d->qam)) return fail(ctx, MPNL_ERR_INVALID_ARG, "qam=%d not in {4,16,64}", d->qam);
@@ -149,12 +162,10 @@ size_t mpnl_workspace_bytes(const mpnl_dims *dims)
     return 0;
 }
 
-int mpnl_preprocess(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const void *Y, void *R,
-                    float *inv_diag, uint8_t *perm, void *Z, void *ws, void *stream)
+static int preprocess_impl(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const void *Y,
+                           float sigma, void *R, float *inv_diag, uint8_t *perm, void *Z,
+                           void *stream)
 {
-    (void)ws;
-    MPNL_TRY(begin(ctx));
-    MPNL_TRY(check_dims(ctx, d, false));
     if (d->n_sc == 0) return MPNL_OK;
     MPNL_TRY(check_ptr(ctx, H, 8, "H", false));
     MPNL_TRY(check_ptr(ctx, Y, 8, "Y", false));
@@ -162,11 +173,31 @@ int mpnl_preprocess(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const void
     MPNL_TRY(check_ptr(ctx, inv_diag, 4, "inv_diag", false));
     MPNL_TRY(check_ptr(ctx, perm, 1, "perm", false));
     MPNL_TRY(check_ptr(ctx, Z, 8, "Z", false));
-    cudaError_t e = mpnl::launch_preprocess(d->n_sc, d->n_sym, d->nr, d->nt, (const float2 *)H,
-                                            (const float2 *)Y, (float2 *)R, inv_diag, perm,
-                                            (float2 *)Z, (cudaStream_t)stream);
+    cudaError_t e = mpnl::launch_preprocess(d->n_sc, d->n_sym, d->nr, d->nt, sigma,
+                                            (const float2 *)H, (const float2 *)Y, (float2 *)R,
+                                            inv_diag, perm, (float2 *)Z, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, "preprocess launch", e);
     return MPNL_OK;
+}
+
+int mpnl_preprocess(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const void *Y, void *R,
+                    float *inv_diag, uint8_t *perm, void *Z, void *ws, void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_dims(ctx, d, false, kNrTall));
+    return preprocess_impl(ctx, d, H, Y, 0.f, R, inv_diag, perm, Z, stream);
+}
+
+int mpnl_preprocess_mmse(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const void *Y,
+                         float sigma2, void *R, float *inv_diag, uint8_t *perm, void *Z, void *ws,
+                         void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_dims(ctx, d, false, kNrAugmented));
+    MPNL_TRY(check_sigma2(ctx, sigma2));
+    return preprocess_impl(ctx, d, H, Y, sqrtf(sigma2), R, inv_diag, perm, Z, stream);
 }
 
 int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, float sigma2,

@@ -8,7 +8,8 @@
 
 namespace mpnl {
 
-cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, const float2 *H,
+// sigma > 0: MMSE-extended factorisation of [H; sigma I] (mpnl_preprocess_mmse).
+cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *H,
                               const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,
                               float2 *Z, cudaStream_t stream);
 

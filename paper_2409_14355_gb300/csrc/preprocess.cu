@@ -36,7 +36,7 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int nr, int nt, int n_sym)
     s.off_y = o;
     o += n_sym * nr * 8;
     s.off_q = o;
-    o += nr * 8;
+    o += (nr + nt) * 8;
     s.off_rt = o;
     o += nt * nt * 8;
     s.off_z = o;
@@ -49,9 +49,13 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int nr, int nt, int n_sym)
     return s;
 }
 
+// sigma > 0 selects the MMSE-extended variant: the channel columns are
+// augmented with sigma * I below the nr antenna rows and the symbol columns
+// with zeros (H_a = [H; sigma I], y_a = [y; 0]), so the factorisation has
+// nr + nt rows; nr may then be smaller than nt.
 template <int NR, int CS>
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
-sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ H,
+sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *__restrict__ H,
                 const float2 *__restrict__ Y, float2 *__restrict__ Rp,
                 float *__restrict__ inv_diag, uint8_t *__restrict__ perm_out,
                 float2 *__restrict__ Z)
@@ -80,6 +84,7 @@ sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ 
     __syncwarp();
 
     const int ncols = nt + n_sym;
+    const int nra = sigma > 0.f ? nr + nt : nr;  // rows of the (augmented) matrix
     float2 col[CS][NR];
 #pragma unroll
     for (int cs = 0; cs < CS; ++cs) {
@@ -90,6 +95,8 @@ sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ 
             if (r < nr) {
                 if (c < nt) v = sH[r * nt + c];
                 else if (c < ncols) v = sY[(c - nt) * nr + r];
+            } else if (r < nra && c < nt && r - nr == c) {
+                v = make_float2(sigma, 0.f);
             }
             col[cs][r] = v;
         }
@@ -125,7 +132,7 @@ sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ 
             const float inv = 1.0f / rii;
 #pragma unroll
             for (int r = 0; r < NR; ++r)
-                if (r < nr) sQ[r] = make_float2(col[0][r].x * inv, col[0][r].y * inv);
+                if (r < nra) sQ[r] = make_float2(col[0][r].x * inv, col[0][r].y * inv);
             sRd[i] = rii;
             sPerm[i] = piv;
             placed = true;
@@ -141,7 +148,7 @@ sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ 
                 float ax = 0.f, ay = 0.f;  // q^H col
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    if (r < nr) {
+                    if (r < nra) {
                         const float2 q = sQ[r];
                         ax = fmaf(q.x, col[cs][r].x, fmaf(q.y, col[cs][r].y, ax));
                         ay = fmaf(q.x, col[cs][r].y, fmaf(-q.y, col[cs][r].x, ay));
@@ -149,7 +156,7 @@ sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ 
                 }
 #pragma unroll
                 for (int r = 0; r < NR; ++r) {
-                    if (r < nr) {
+                    if (r < nra) {
                         const float2 q = sQ[r];
                         col[cs][r].x -= ax * q.x - ay * q.y;
                         col[cs][r].y -= ax * q.y + ay * q.x;
@@ -183,8 +190,9 @@ sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ 
 }
 
 template <int NR, int CS>
-cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, const float2 *H, const float2 *Y,
-                       float2 *R, float *inv_diag, uint8_t *perm, float2 *Z, cudaStream_t stream)
+cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *H,
+                       const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm, float2 *Z,
+                       cudaStream_t stream)
 {
     const WarpSmem L = warp_smem_layout(nr, nt, n_sym);
     const size_t smem = (size_t)L.bytes * kWarpsPerCta;
@@ -194,25 +202,26 @@ cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, const float2 *H, con
         if (e != cudaSuccess) return e;
     }
     const int grid = (n_sc + kWarpsPerCta - 1) / kWarpsPerCta;
-    sqrd_qhy_kernel<NR, CS><<<grid, kWarpsPerCta * 32, smem, stream>>>(n_sc, n_sym, nr, nt, H, Y, R,
-                                                                       inv_diag, perm, Z);
+    sqrd_qhy_kernel<NR, CS><<<grid, kWarpsPerCta * 32, smem, stream>>>(n_sc, n_sym, nr, nt, sigma,
+                                                                       H, Y, R, inv_diag, perm, Z);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, const float2 *H,
+cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *H,
                               const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,
                               float2 *Z, cudaStream_t stream)
 {
     if (n_sc == 0) return cudaSuccess;
     const bool two = nt + n_sym > 32;
-#define MPNL_PRE(NRV)                                                                         \
-    return two ? launch_tpl<NRV, 2>(n_sc, n_sym, nr, nt, H, Y, R, inv_diag, perm, Z, stream)  \
-               : launch_tpl<NRV, 1>(n_sc, n_sym, nr, nt, H, Y, R, inv_diag, perm, Z, stream)
-    if (nr <= 4) MPNL_PRE(4);
-    if (nr <= 8) MPNL_PRE(8);
-    if (nr <= 16) MPNL_PRE(16);
+    const int rows = sigma > 0.f ? nr + nt : nr;
+#define MPNL_PRE(NRV)                                                                          \
+    return two ? launch_tpl<NRV, 2>(n_sc, n_sym, nr, nt, sigma, H, Y, R, inv_diag, perm, Z, stream) \
+               : launch_tpl<NRV, 1>(n_sc, n_sym, nr, nt, sigma, H, Y, R, inv_diag, perm, Z, stream)
+    if (rows <= 4) MPNL_PRE(4);
+    if (rows <= 8) MPNL_PRE(8);
+    if (rows <= 16) MPNL_PRE(16);
     MPNL_PRE(32);
 #undef MPNL_PRE
 }

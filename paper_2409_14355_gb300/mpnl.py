@@ -35,7 +35,8 @@ ERR_CUDA = -3
 ERR_TIMEOUT = -4
 
 EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_bytes",
-            "mpnl_preprocess", "mpnl_select_paths", "mpnl_detect", "mpnl_detect_mixed",
+            "mpnl_preprocess", "mpnl_preprocess_mmse", "mpnl_select_paths", "mpnl_detect",
+            "mpnl_detect_mixed",
             "mpnl_linear_mmse", "mpnl_check_status")
 PRECISIONS = ("fp32", "fp16")
 
@@ -77,6 +78,8 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_workspace_bytes.restype = S
         lib.mpnl_preprocess.argtypes = [P, D, P, P, P, P, P, P, P, P]
         lib.mpnl_preprocess.restype = I
+        lib.mpnl_preprocess_mmse.argtypes = [P, D, P, P, F, P, P, P, P, P, P]
+        lib.mpnl_preprocess_mmse.restype = I
         lib.mpnl_select_paths.argtypes = [P, D, P, F, P, P, P]
         lib.mpnl_select_paths.restype = I
         lib.mpnl_detect.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
@@ -140,8 +143,9 @@ def workspace_bytes(n_sc, n_sym, nr, nt, qam, n_pe) -> int:
     return int(load_library().mpnl_workspace_bytes(ctypes.byref(d)))
 
 
-def preprocess(H: torch.Tensor, Y: torch.Tensor, out=None):
-    """Sorted QR + z = Q^H y.  Returns (R, inv_diag, perm, Z)."""
+def preprocess(H: torch.Tensor, Y: torch.Tensor, out=None, sigma2: float | None = None):
+    """Sorted QR + z = Q^H y.  Returns (R, inv_diag, perm, Z).  With sigma2,
+    the MMSE-extended factorisation of [H; sqrt(sigma2) I] (allows nt > nr)."""
     dev = _dev_of(H)
     n_sc, nr, nt = H.shape
     n_sym = Y.shape[1]
@@ -156,8 +160,14 @@ def preprocess(H: torch.Tensor, Y: torch.Tensor, out=None):
         R, inv_diag, perm, Z = out
     ctx = context(dev.index)
     d = Dims(n_sc, n_sym, nr, nt, 4, 1)
-    st = load_library().mpnl_preprocess(ctx, ctypes.byref(d), _ptr(H), _ptr(Y), _ptr(R),
-                                        _ptr(inv_diag), _ptr(perm), _ptr(Z), None, _stream(dev))
+    lib = load_library()
+    if sigma2 is None:
+        st = lib.mpnl_preprocess(ctx, ctypes.byref(d), _ptr(H), _ptr(Y), _ptr(R), _ptr(inv_diag),
+                                 _ptr(perm), _ptr(Z), None, _stream(dev))
+    else:
+        st = lib.mpnl_preprocess_mmse(ctx, ctypes.byref(d), _ptr(H), _ptr(Y), float(sigma2),
+                                      _ptr(R), _ptr(inv_diag), _ptr(perm), _ptr(Z), None,
+                                      _stream(dev))
     _raise(st, ctx)
     return R, inv_diag, perm, Z
 
@@ -258,11 +268,13 @@ class SlotBuffers:
 
 
 def run_slot(buf: SlotBuffers, H, Y, sigma2: float, mmse: bool = True,
-             precision: str = "fp32") -> None:
+             precision: str = "fp32", mmse_qr: bool = False) -> None:
     """The whole path on device tensors H, Y (enqueued on the current stream):
-    preprocess -> select_paths -> detect (hard, LLR, PED pair) [-> MMSE]."""
+    preprocess -> select_paths -> detect (hard, LLR, PED pair) [-> MMSE].
+    mmse_qr selects the MMSE-extended pre-processing (needed when nt > nr)."""
     n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
-    preprocess(H, Y, out=(buf.R, buf.inv_diag, buf.perm, buf.Z))
+    preprocess(H, Y, out=(buf.R, buf.inv_diag, buf.perm, buf.Z),
+               sigma2=sigma2 if mmse_qr else None)
     select_paths(buf.R, sigma2, qam, n_pe, nt, out=buf.paths)
     detect(buf.R, buf.inv_diag, buf.perm, buf.paths, buf.Z, sigma2, qam,
            out=(buf.hard, buf.llr, buf.ped2), precision=precision)
@@ -271,7 +283,8 @@ def run_slot(buf: SlotBuffers, H, Y, sigma2: float, mmse: bool = True,
 
 
 def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
-                buffers: SlotBuffers | None = None, device=None, precision: str = "fp32"):
+                buffers: SlotBuffers | None = None, device=None, precision: str = "fp32",
+                mmse_qr: bool = False):
     """End-to-end call a user makes: accepts host (ideally pinned) or device
     tensors.  Host inputs are copied to the device, the path runs, and the
     hard decisions and LLRs (and MMSE outputs with ``mmse``) come back as host
@@ -288,7 +301,7 @@ def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
         Hd, Yd = buf.H, buf.Y
     else:
         Hd, Yd = H, Y
-    run_slot(buf, Hd, Yd, sigma2, mmse, precision)
+    run_slot(buf, Hd, Yd, sigma2, mmse, precision, mmse_qr)
     out = dict(hard=buf.hard, llr=buf.llr, ped2=buf.ped2)
     if mmse:
         out["mmse_hard"] = buf.mmse_hard

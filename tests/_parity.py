@@ -25,11 +25,17 @@ TIE_EPS = 1e-4        # stage-isolated ranking near-tie width, constellation dis
 E2E_KAPPA_FACTOR = 64 * 2.0 ** -24
 
 
-def e2e_reference(H, Y, sigma2, qam, n_pe, with_mmse=True):
+def e2e_reference(H, Y, sigma2, qam, n_pe, with_mmse=True, mmse_qr=False):
     """Oracle run of a whole slot plus per-subcarrier near-tie floors and
-    tolerances for comparing the end-to-end GPU path."""
-    ref = oracle.detect_slot(H, Y, sigma2, qam, n_pe, with_mmse=with_mmse)
-    kappa = np.linalg.cond(np.asarray(H, np.complex128))
+    tolerances for comparing the end-to-end GPU path.  With mmse_qr the
+    factorised matrix, and so kappa, is the augmented [H; sigma I]."""
+    ref = oracle.detect_slot(H, Y, sigma2, qam, n_pe, with_mmse=with_mmse, mmse_qr=mmse_qr)
+    H = np.asarray(H, np.complex128)
+    if mmse_qr:
+        nt = H.shape[-1]
+        aug = np.broadcast_to(np.sqrt(sigma2) * np.eye(nt), (H.shape[0], nt, nt))
+        H = np.concatenate([H, aug], axis=1)
+    kappa = np.linalg.cond(H)
     eps = np.maximum(TIE_EPS * 0.1, E2E_KAPPA_FACTOR * kappa)
     ff = np.zeros(ref["ped2"].shape[:2])
     for c in range(H.shape[0]):
@@ -66,6 +72,20 @@ def oracle_front(H: np.ndarray, Y: np.ndarray):
     for c in range(n_sc):
         Q, R[c], perm[c], gap[c] = oracle.sqrd(H[c])
         Z[c] = oracle.qhy(Q, Y[c])
+    return R, perm, Z, gap
+
+
+def oracle_front_mmse(H: np.ndarray, Y: np.ndarray, sigma2: float):
+    """Oracle MMSE-extended sorted QR + z = Q_a^H [y; 0] per subcarrier."""
+    n_sc, nr, nt = H.shape
+    R = np.zeros((n_sc, nt, nt), np.complex128)
+    perm = np.zeros((n_sc, nt), np.int32)
+    Z = np.zeros((n_sc, Y.shape[1], nt), np.complex128)
+    gap = np.zeros((n_sc, nt))
+    for c in range(n_sc):
+        Q, R[c], perm[c], gap[c] = oracle.sqrd_mmse(H[c], sigma2)
+        Ya = np.concatenate([Y[c], np.zeros((Y.shape[1], nt), np.complex128)], axis=1)
+        Z[c] = oracle.qhy(Q, Ya)
     return R, perm, Z, gap
 
 
