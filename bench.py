@@ -45,7 +45,7 @@ FP32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["mpnl", "reference"], default="mpnl")
     ap.add_argument("--workload", default="16x16-64qam-3276sc")
@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32",
+                    help="walk residuals in FP32 (mpnl_detect) or FP16 (mpnl_detect_mixed)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the N_pe / precision sweep reported beside the main line")
     ap.add_argument("--n-sc", type=int, default=None,
                     help="override the subcarrier count (smaller profiling cases)")
     return ap.parse_args()
@@ -133,10 +137,10 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle timing (baseline only)
 # --------------------------------------------------------------------------
-def time_oracle(sl, qam, n_pe, seconds: float, max_sc: int | None = None):
+def time_oracle(sl, qam, n_pe, seconds: float, max_sc: int | None = None, n_threads: int = 0):
     """Run the oracle on growing prefixes of the slot's subcarriers until one
     run takes >= `seconds` (or the cap is reached).  Returns (dets/s, threads,
-    subcarriers, elapsed)."""
+    subcarriers, elapsed).  n_threads 0 = all host cores."""
     import oracle
 
     n = 4
@@ -144,7 +148,8 @@ def time_oracle(sl, qam, n_pe, seconds: float, max_sc: int | None = None):
     while True:
         n = min(n, cap)
         t0 = time.perf_counter()
-        out = oracle.detect_slot(sl.H[:n], sl.Y[:n], sl.sigma2, qam, n_pe, with_mmse=True)
+        out = oracle.detect_slot(sl.H[:n], sl.Y[:n], sl.sigma2, qam, n_pe, with_mmse=True,
+                                 n_threads=n_threads)
         dt = time.perf_counter() - t0
         if dt >= seconds or n >= cap:
             return n * sl.n_sym / dt, out["threads"], n, dt
@@ -285,17 +290,20 @@ def run_mpnl(args):
     buf = mpnl.SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, dev, mmse=True)
     stream = torch.cuda.current_stream(dev)
 
-    def step(i, ev=None):
+    def run_step(b, npe, precision, i, ev=None):
         H, Y, s2 = ring[i % len(ring)]
-        mpnl.preprocess(H, Y, out=(buf.R, buf.inv_diag, buf.perm, buf.Z))
-        mpnl.select_paths(buf.R, s2, qam, n_pe, nt, out=buf.paths)
+        mpnl.preprocess(H, Y, out=(b.R, b.inv_diag, b.perm, b.Z))
+        mpnl.select_paths(b.R, s2, qam, npe, nt, out=b.paths)
         if ev is not None:
             ev[0].record(stream)
-        mpnl.detect(buf.R, buf.inv_diag, buf.perm, buf.paths, buf.Z, s2, qam,
-                    out=(buf.hard, buf.llr, buf.ped2))
+        mpnl.detect(b.R, b.inv_diag, b.perm, b.paths, b.Z, s2, qam,
+                    out=(b.hard, b.llr, b.ped2), precision=precision)
         if ev is not None:
             ev[1].record(stream)
-        mpnl.linear_mmse(H, Y, s2, qam, out=(buf.mmse_hard, buf.mmse_llr))
+        mpnl.linear_mmse(H, Y, s2, qam, out=(b.mmse_hard, b.mmse_llr))
+
+    def step(i, ev=None):
+        run_step(buf, n_pe, args.precision, i, ev)
 
     for i in range(args.warmup):
         step(i)
@@ -341,12 +349,13 @@ def run_mpnl(args):
     if args.e2e_steps > 0:
         for i in range(2):
             mpnl.detect_slot(hs[i % len(hs)][0], hs[i % len(hs)][1], sigma2, qam, n_pe,
-                             mmse=True, buffers=buf)
+                             mmse=True, buffers=buf, precision=args.precision)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
             Hh, Yh = hs[i % len(hs)]
-            out = mpnl.detect_slot(Hh, Yh, sigma2, qam, n_pe, mmse=True, buffers=buf)
+            out = mpnl.detect_slot(Hh, Yh, sigma2, qam, n_pe, mmse=True, buffers=buf,
+                                   precision=args.precision)
         e2e_dt = time.perf_counter() - t0
         h2d = hs[0][0].numel() * 8 + hs[0][1].numel() * 8
         d2h = sum(v.numel() * v.element_size() for v in out.values())
@@ -355,8 +364,56 @@ def run_mpnl(args):
     dets_per_step = n_sc * n_sym
     value, elapsed = whole_job_rate(K * dets_per_step, elapsed, dev)
 
-    # ---- roofline of the dominant kernel (walk kernel, FP32 ALU bound)
+    # ---- the other N_pe points of this workload and the other precision
+    # (fewer steps; reported beside the main line, not instead of it)
+    sweep = None
+    if not args.no_sweep:
+        sweep = []
+        points = [(p, args.precision) for p in (64, 128, 256) if p != n_pe and p <= qam ** nt]
+        points.append((n_pe, "fp16" if args.precision == "fp32" else "fp32"))
+        ks = max(10, K // 4)
+        for npe, prec in points:
+            b2 = mpnl.SlotBuffers(n_sc, n_sym, nr, nt, qam, npe, dev, mmse=True)
+            for i in range(args.warmup):
+                run_step(b2, npe, prec, i)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(ks)]
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for i in range(ks):
+                run_step(b2, npe, prec, args.warmup + i, ev[i])
+            a1.record(stream)
+            torch.cuda.synchronize()
+            mpnl.check_status(local)
+            t = a0.elapsed_time(a1) / 1e3
+            dms = sum(x.elapsed_time(y) for x, y in ev) / ks
+            v, _ = whole_job_rate(ks * dets_per_step, t, dev)
+            fl = npe * (4 * nt * nt + 4 * nt) * dets_per_step
+            sweep.append({"n_pe": npe, "precision": prec, "steps": ks, "value": v,
+                          "ms_per_step": 1e3 * t / ks, "detect_ms": dms,
+                          "detect_tflops": fl / (dms / 1e3) / 1e12})
+            del b2
+
+    # ---- measured FP32 FMA throughput (probe kernel), beside the derived peak
+    probe_tflops = None
     props = torch.cuda.get_device_properties(dev)
+    n_blk = props.multi_processor_count * 8
+    pout = torch.empty(n_blk * 256, dtype=torch.float32, device=dev)
+    best = None
+    for _ in range(6):
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        fl = mpnl.probe_ffma(n_blk, 8192, pout)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t = a0.elapsed_time(a1) / 1e3
+        best = t if best is None else min(best, t)
+    probe_tflops = fl / best / 1e12
+
+    # ---- roofline of the dominant kernel (walk kernel, FP32 ALU bound)
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak_tflops = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     flop_per_det = n_pe * (4 * nt * nt + 4 * nt)
@@ -371,14 +428,19 @@ def run_mpnl(args):
         if world == 1 and not args.no_cpu_baseline:
             sl0 = inputs.workload_slot(args.workload, args.snr_index, extra_seed=1)
             v, thr, n_used, dt = time_oracle(sl0, qam, n_pe, args.cpu_seconds)
+            v1, _, n1, dt1 = time_oracle(sl0, qam, n_pe, args.cpu_seconds / 3, n_threads=1)
             cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{n_used} of {n_sc} subcarriers x 14 symbols of one slot "
-                             f"(whole path incl. MMSE), FP64, {dt:.1f} s"}
+                             f"(whole path incl. MMSE), FP64, {dt:.1f} s",
+                   "one_core": {"value": v1, "cores": 1,
+                                "sample": f"{n1} subcarriers x 14 symbols, {dt1:.1f} s"}}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "f16+f32", "data": "synthetic",
             "config": dict(workload_config(args, w), parallelism=f"replicas{world}",
+                           precision=args.precision,
                            l2=f"ring of {len(ring)} distinct slots, {ring_bytes / 1e6:.0f} MB of "
                               f"H+Y > 129 MB L2"),
             "gb_per_s": value * nt * B / 1e9,
@@ -390,7 +452,10 @@ def run_mpnl(args):
                          "flop_per_launch": flop_per_det * dets_per_step,
                          "launch_ms": det_avg,
                          "peak_note": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
-                                      f"{sm_max:.0f} MHz (max SM clock)"},
+                                      f"{sm_max:.0f} MHz (max SM clock)",
+                         "peak_measured_ffma": probe_tflops,
+                         "frac_of_measured_ffma": achieved_tflops / probe_tflops},
+            "sweep": sweep,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else
                    {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -181,6 +181,18 @@ int mpnl_linear_mmse(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const 
  * MPNL_ERR_INVALID_ARG (with a message) or MPNL_ERR_CUDA. */
 int mpnl_check_status(mpnl_ctx *ctx, void *stream);
 
+/* Measurement helper, not part of the detector (the paper has no
+ * counterpart): enqueue an FP32 FMA throughput kernel of n_blocks CTAs of 256
+ * threads, each thread running 8 independent fmaf chains for `iters` rounds,
+ * and store the number of floating-point operations it performs (2 per fmaf)
+ * in *flops.  `out` is device memory of n_blocks * 256 floats (overwritten
+ * with the chain sums).  Timing it with events on `stream` gives the measured
+ * FP32 peak beside the one derived from SM count and clock.
+ * Errors: MPNL_ERR_INVALID_ARG (n_blocks < 1, iters < 1, NULL or host
+ * `out`/`flops`), MPNL_ERR_CUDA. */
+int mpnl_probe_ffma(mpnl_ctx *ctx, int n_blocks, int iters, float *out, double *flops,
+                    void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -268,43 +268,44 @@ __device__ __forceinline__ void nearest_list(float bx, float by, int len, float4
 // per-walk state helpers
 // --------------------------------------------------------------------------
 
-// The NT rank bytes of one table row (rows are NT-byte aligned in shared memory).
-template <int NT>
-struct RowRanks {
-    uint32_t w[NT / 4];
-    __device__ __forceinline__ void load(const uint8_t *row)
-    {
-        if constexpr (NT == 16) {
-            const uint4 v = *reinterpret_cast<const uint4 *>(row);
-            w[0] = v.x;
-            w[1] = v.y;
-            w[2] = v.z;
-            w[3] = v.w;
-        } else if constexpr (NT == 8) {
-            const uint2 v = *reinterpret_cast<const uint2 *>(row);
-            w[0] = v.x;
-            w[1] = v.y;
-        } else {
-            w[0] = *reinterpret_cast<const uint32_t *>(row);
-        }
-    }
-    __device__ __forceinline__ int get(int l) const { return (w[l >> 2] >> (8 * (l & 3))) & 0xff; }
-};
-
-// Labels of the NT levels of one walk, B bits each, packed into 32-bit words.
+// Labels of the NT levels of one walk, B bits each, packed contiguously:
+// level l occupies bits [B l, B l + B) of the WORDS-word integer.  The walk
+// visits levels nt-1 .. 0 and pushes each label in at the bottom, so no
+// register is ever indexed by the (run-time) level.
 template <int NT, int B>
 struct Labels {
-    static constexpr int PER = 32 / B;                  // levels per word
-    static constexpr int WORDS = (NT + PER - 1) / PER;
+    static constexpr int WORDS = (NT * B + 31) / 32;
     uint32_t w[WORDS];
     __device__ __forceinline__ void clear()
     {
 #pragma unroll
         for (int k = 0; k < WORDS; ++k) w[k] = 0;
     }
-    __device__ __forceinline__ void set(int l, int lab) { w[l / PER] |= (uint32_t)lab << (B * (l % PER)); }
-    __device__ __forceinline__ int get(int l) const { return (w[l / PER] >> (B * (l % PER))) & ((1 << B) - 1); }
+    __device__ __forceinline__ void push(int lab)
+    {
+#pragma unroll
+        for (int k = WORDS - 1; k > 0; --k) w[k] = __funnelshift_l(w[k - 1], w[k], B);
+        w[0] = (w[0] << B) | (uint32_t)lab;
+    }
+    // level l (a compile-time constant after unrolling)
+    __device__ __forceinline__ int get(int l) const
+    {
+        const int bit = B * l, k = bit >> 5, off = bit & 31;
+        uint32_t v = w[k] >> off;
+        if (off + B > 32 && k + 1 < WORDS) v |= w[k + 1] << (32 - off);
+        return (int)(v & ((1u << B) - 1));
+    }
 };
+
+// Level l's label from packed words in memory (run-time l).
+template <int B>
+__device__ __forceinline__ int label_at(const uint32_t *w, int l)
+{
+    const int bit = B * l, k = bit >> 5, off = bit & 31;
+    uint32_t v = w[k] >> off;
+    if (off + B > 32) v |= w[k + 1] << (32 - off);
+    return (int)(v & ((1u << B) - 1));
+}
 
 __host__ __device__ inline int a16(int o) { return (o + 15) & ~15; }
 __host__ __device__ inline int pow2_at_least(int n)
@@ -459,6 +460,94 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
     }
 }
 
+// Interference cancellation fused with the shift of the residual register
+// file after level l is decided: e'[i] = e[i+1] - R_{l-1-i, l} s for i < W
+// (W >= l; col = the staged column l of R, bottom-up, two entries per 16-byte
+// broadcast load serving both symbols).  e'[i] for i >= W is not needed.
+template <int W, int NT>
+__device__ __forceinline__ void cancel_shift(float (&ex)[2][NT], float (&ey)[2][NT],
+                                             const float2 *col, const float (&sx)[2],
+                                             const float (&sy)[2])
+{
+    static_assert(W < NT, "the shift reads entry W");
+    const float4 *c4 = reinterpret_cast<const float4 *>(col);
+#pragma unroll
+    for (int i2 = 0; i2 < (W + 1) / 2; ++i2) {
+        const float4 r = c4[i2];
+        const int i = 2 * i2;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            ex[k][i] = fmaf(-r.x, sx[k], fmaf(r.y, sy[k], ex[k][i + 1]));
+            ey[k][i] = fmaf(-r.x, sy[k], fmaf(-r.y, sx[k], ey[k][i + 1]));
+            if (i + 1 < W) {
+                ex[k][i + 1] = fmaf(-r.z, sx[k], fmaf(r.w, sy[k], ex[k][i + 2]));
+                ey[k][i + 1] = fmaf(-r.z, sy[k], fmaf(-r.w, sx[k], ey[k][i + 2]));
+            }
+        }
+    }
+}
+
+// half2 variant: e + (-Re,-Re)*(sx,sy) + (Im,-Im)*(sy,sx) per complex term.
+template <int W, int NT>
+__device__ __forceinline__ void cancel_shift_h(__half2 (&eh)[2][NT], const uint2 *colh,
+                                               const __half2 (&sh)[2], const __half2 (&sw)[2])
+{
+    static_assert(W < NT, "the shift reads entry W");
+    const uint4 *c4 = reinterpret_cast<const uint4 *>(colh);
+#pragma unroll
+    for (int i2 = 0; i2 < (W + 1) / 2; ++i2) {
+        const uint4 r = c4[i2];
+        const __half2 a0 = *reinterpret_cast<const __half2 *>(&r.x);
+        const __half2 b0 = *reinterpret_cast<const __half2 *>(&r.y);
+        const __half2 a1 = *reinterpret_cast<const __half2 *>(&r.z);
+        const __half2 b1 = *reinterpret_cast<const __half2 *>(&r.w);
+        const int i = 2 * i2;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            eh[k][i] = __hfma2(b0, sw[k], __hfma2(a0, sh[k], eh[k][i + 1]));
+            if (i + 1 < W) eh[k][i + 1] = __hfma2(b1, sw[k], __hfma2(a1, sh[k], eh[k][i + 2]));
+        }
+    }
+}
+
+// Width dispatch: levels are grouped four at a time so that a level pays for
+// at most three unused terms (widths 15, 11, 7, 3 for NT = 16); level 0
+// needs no cancellation.  l is warp-uniform, so the branches do not diverge.
+template <int NT>
+__device__ __forceinline__ void cancel_level(int l, float (&ex)[2][NT], float (&ey)[2][NT],
+                                             const float2 *col, const float (&sx)[2],
+                                             const float (&sy)[2])
+{
+    if constexpr (NT == 16) {
+        if (l > 11) cancel_shift<15>(ex, ey, col, sx, sy);
+        else if (l > 7) cancel_shift<11>(ex, ey, col, sx, sy);
+        else if (l > 3) cancel_shift<7>(ex, ey, col, sx, sy);
+        else if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
+    } else if constexpr (NT == 8) {
+        if (l > 3) cancel_shift<7>(ex, ey, col, sx, sy);
+        else if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
+    } else {
+        if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void cancel_level_h(int l, __half2 (&eh)[2][NT], const uint2 *colh,
+                                               const __half2 (&sh)[2], const __half2 (&sw)[2])
+{
+    if constexpr (NT == 16) {
+        if (l > 11) cancel_shift_h<15>(eh, colh, sh, sw);
+        else if (l > 7) cancel_shift_h<11>(eh, colh, sh, sw);
+        else if (l > 3) cancel_shift_h<7>(eh, colh, sh, sw);
+        else if (l > 0) cancel_shift_h<3>(eh, colh, sh, sw);
+    } else if constexpr (NT == 8) {
+        if (l > 3) cancel_shift_h<7>(eh, colh, sh, sw);
+        else if (l > 0) cancel_shift_h<3>(eh, colh, sh, sw);
+    } else {
+        if (l > 0) cancel_shift_h<3>(eh, colh, sh, sw);
+    }
+}
+
 // F16: the interference-cancelled residuals e are kept as half2 (re, im) and
 // updated with two HFMA2 per complex term; b, the ranking and the PED stay in
 // FP32, and the final best and runner-up paths are re-checked in FP32.
@@ -479,7 +568,9 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
     const int nrows = chunks * 32;
     const int np2 = pow2_at_least(nrows);
     const DetSmem S = det_layout(NT, B, n_pe, n_sym, WORDS);
-    float2 *sRc = reinterpret_cast<float2 *>(smem + S.off_rc);  // sRc[l*NT + i] = R_il, i < l
+    // sRr[l*NT + i] = R_{l-1-i, l} for i < l (column l of R above the
+    // diagonal, bottom-up: the order the shift-register walk consumes it)
+    float2 *sRr = reinterpret_cast<float2 *>(smem + S.off_rc);
     float *sR2 = reinterpret_cast<float *>(smem + S.off_r2);
     float *sInvd = reinterpret_cast<float *>(smem + S.off_invd);
     int *sPerm = reinterpret_cast<int *>(smem + S.off_perm);
@@ -496,7 +587,7 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
     __shared__ int s_k1[QAM + 1], s_off1[QAM + 1];
     __shared__ int s_use2;
     uint8_t *sLut = smem + S.off_lut;
-    uint2 *sRh = reinterpret_cast<uint2 *>(smem + S.off_rh);  // {(-Re,-Re), (Im,-Im)} as half2
+    uint2 *sRh = reinterpret_cast<uint2 *>(smem + S.off_rh);  // sRr as {(-Re,-Re), (Im,-Im)} half2
     unsigned long long *sKey2 = reinterpret_cast<unsigned long long *>(smem + S.off_key2);
     uint32_t *sBlab2 = reinterpret_cast<uint32_t *>(smem + S.off_blab2);
     __shared__ int s_kmax;
@@ -507,24 +598,24 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
 
     // ---- stage the subcarrier
     const int P = nt * (nt + 1) / 2;
-    for (int k = tid; k < P; k += kThreads) {
-        int i = 0, rem = k;
-        while (rem >= nt - i) {
-            rem -= nt - i;
-            ++i;
+    const float2 *gR = Rp + (size_t)sc * P;
+    for (int k = tid; k < NT * NT; k += kThreads) {
+        const int l = k / NT, i = k - l * NT;
+        float2 v = make_float2(0.f, 0.f);  // entries i >= l feed only stale registers
+        if (l < nt && i < l) {
+            const int r = l - 1 - i;  // R_{r,l}: packed row r starts at r nt - r(r-1)/2
+            v = gR[r * nt - (r * (r - 1)) / 2 + (l - r)];
         }
-        const int j = i + rem;
-        const float2 v = Rp[(size_t)sc * P + k];
-        if (i == j) {
-            sR2[i] = v.x * v.x;
-        } else {
-            sRc[j * NT + i] = v;
-            if constexpr (F16) {
-                const __half2 a = __floats2half2_rn(-v.x, -v.x), b = __floats2half2_rn(v.y, -v.y);
-                sRh[j * NT + i] = make_uint2(*reinterpret_cast<const unsigned *>(&a),
-                                             *reinterpret_cast<const unsigned *>(&b));
-            }
+        sRr[k] = v;
+        if constexpr (F16) {
+            const __half2 a = __floats2half2_rn(-v.x, -v.x), b = __floats2half2_rn(v.y, -v.y);
+            sRh[k] = make_uint2(*reinterpret_cast<const unsigned *>(&a),
+                                *reinterpret_cast<const unsigned *>(&b));
         }
+    }
+    for (int l = tid; l < nt; l += kThreads) {
+        const float2 v = gR[l * nt - (l * (l - 1)) / 2];
+        sR2[l] = v.x * v.x;
     }
     for (int k = tid; k < NT; k += kThreads) {
         if (k < nt) {
@@ -624,7 +715,7 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
         const int kmx = s_kmax;
         const int l = nt - 2;
         const float iv = sInvd[l];
-        const float2 r = sRc[(nt - 1) * NT + l];  // R_{nt-2, nt-1}
+        const float2 r = sRr[(nt - 1) * NT];  // R_{nt-2, nt-1}
         for (int it = tid; it < (n_sym + 1) * kmx; it += kThreads) {  // one thread per list
             const int s = it / kmx, a = 1 + it - s * kmx;
             const int len = s_k1[a];
@@ -641,25 +732,28 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
 
     // ---- walks: warp item = (chunk of 32 rows, pair of symbols)
     const int pairs = (n_sym + 1) >> 1;
+    const int l_list = use2 ? nt - 2 : nt - 1;  // levels >= l_list are list-served
     for (int item = warp; item < chunks * pairs; item += kWarps) {
         const int chunk = item / pairs, s0 = 2 * (item - chunk * pairs);
         const bool has1 = s0 + 1 < n_sym;
         const int row = (int)(sOrder[chunk * 32 + lane] & 0xfffu);
         const bool active = row < n_pe;
-        RowRanks<NT> pr;
-        pr.load(sTab + row * NT);
+        const uint8_t *trow = sTab + row * NT;
+        // shift register: when level l is decided, e[k][i] = e_{l-i} of
+        // symbol s0 + k; entries i > l are stale and never read
         float ex[2][NT], ey[2][NT];
         __half2 eh[2][NT];
 #pragma unroll
-        for (int l = 0; l < NT; ++l) {
+        for (int i = 0; i < NT; ++i) {
+            const int lz = nt - 1 - i;
 #pragma unroll
             for (int k = 0; k < 2; ++k) {
-                const float2 z = sZ[(s0 + k) * NT + l];
+                const float2 z = lz >= 0 ? sZ[(s0 + k) * NT + lz] : make_float2(0.f, 0.f);
                 if constexpr (F16) {
-                    eh[k][l] = __floats2half2_rn(z.x, z.y);
+                    eh[k][i] = __floats2half2_rn(z.x, z.y);
                 } else {
-                    ex[k][l] = z.x;
-                    ey[k][l] = z.y;
+                    ex[k][i] = z.x;
+                    ey[k][i] = z.y;
                 }
             }
         }
@@ -667,125 +761,94 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
         lab[0].clear();
         lab[1].clear();
         float d[2] = {0.f, 0.f};
-#pragma unroll
-        for (int l = NT - 1; l >= 0; --l) {
-            if (l < nt) {
-                const int p = pr.get(l);
-                float sx[2], sy[2], dist[2];
-                int lb[2];
-                if (l == nt - 1 || (use2 && l == nt - 2)) {  // list-served levels
-                    const float4 *lst = l == nt - 1 ? sTop + s0 * kTopList + p - 1
-                                                    : sL2 + s0 * kList2 + s_off1[pr.get(nt - 1)] + p - 1;
-                    const int stride = l == nt - 1 ? kTopList : kList2;
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        const float4 q = lst[k * stride];
-                        sx[k] = q.x;
-                        sy[k] = q.y;
-                        dist[k] = q.z;
-                        lb[k] = __float_as_int(q.w);
-                    }
+        int p_top = 1;
+#pragma unroll 1
+        for (int l = nt - 1; l >= 0; --l) {
+            const int p = trow[l];
+            float sx[2], sy[2], dist[2];
+            int lb[2];
+            if (l >= l_list) {  // list-served levels (warp-uniform branch)
+                const float4 *lst;
+                int stride;
+                if (l == nt - 1) {
+                    p_top = p;
+                    lst = sTop + s0 * kTopList + p - 1;
+                    stride = kTopList;
                 } else {
-                    const float iv = sInvd[l];
-                    int ire[2], iim[2];
-                    float dre[2], dim[2];
-#pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        float bx, by;
-                        if constexpr (F16) {
-                            const float2 f = __half22float2(eh[k][l]);
-                            bx = f.x * iv;
-                            by = f.y * iv;
-                        } else {
-                            bx = ex[k][l] * iv;
-                            by = ey[k][l] * iv;
-                        }
-                        ire[k] = axis_round<QAM>(bx, dre[k]);
-                        iim[k] = axis_round<QAM>(by, dim[k]);
-                        if (p == 2) {
-                            // second nearest: the next point along one axis
-                            const int nre = axis_next<QAM>(bx, ire[k]);
-                            const int nim = axis_next<QAM>(by, iim[k]);
-                            float a = bx - axis_pos<QAM>(nre), c = by - axis_pos<QAM>(nim);
-                            const float d_re = a * a + dim[k];  // (nre, iim)
-                            const float d_im = dre[k] + c * c;  // (ire, nim)
-                            bool take_re = d_re < d_im;
-                            if (d_re == d_im)
-                                take_re = sLut[nre * 8 + iim[k]] < sLut[ire[k] * 8 + nim];
-                            if (take_re) {
-                                ire[k] = nre;
-                                dre[k] = d_re;
-                                dim[k] = 0.f;
-                            } else {
-                                iim[k] = nim;
-                                dre[k] = d_im;
-                                dim[k] = 0.f;
-                            }
-                        } else if (p > 2) {
-                            int oi, oj;
-                            dre[k] = kth_point_slow<QAM>(bx, by, p, ire[k], iim[k], oi, oj);
-                            dim[k] = 0.f;
-                            ire[k] = oi;
-                            iim[k] = oj;
-                        }
-                        dist[k] = dre[k] + dim[k];
-                        sx[k] = axis_pos<QAM>(ire[k]);
-                        sy[k] = axis_pos<QAM>(iim[k]);
-                        lb[k] = sLut[ire[k] * 8 + iim[k]];
-                    }
+                    lst = sL2 + s0 * kList2 + s_off1[p_top] + p - 1;
+                    stride = kList2;
                 }
-                const float r2 = sR2[l];
 #pragma unroll
                 for (int k = 0; k < 2; ++k) {
-                    d[k] = fmaf(r2, dist[k], d[k]);
-                    lab[k].set(l, lb[k]);
+                    const float4 q = lst[k * stride];
+                    sx[k] = q.x;
+                    sy[k] = q.y;
+                    dist[k] = q.z;
+                    lb[k] = __float_as_int(q.w);
                 }
-                if constexpr (F16) {
-                    // e_i -= R_il s: e + (-Re,-Re)*(sx,sy) + (Im,-Im)*(sy,sx)
-                    const uint4 *colh = reinterpret_cast<const uint4 *>(sRh + l * NT);
-                    __half2 sh[2], sw[2];
+            } else {
+                const float iv = sInvd[l];
+                int ire[2], iim[2];
+                float dre[2], dim[2];
 #pragma unroll
-                    for (int k = 0; k < 2; ++k) {
-                        sh[k] = __floats2half2_rn(sx[k], sy[k]);
-                        sw[k] = __floats2half2_rn(sy[k], sx[k]);
+                for (int k = 0; k < 2; ++k) {
+                    float bx, by;
+                    if constexpr (F16) {
+                        const float2 f = __half22float2(eh[k][0]);
+                        bx = f.x * iv;
+                        by = f.y * iv;
+                    } else {
+                        bx = ex[k][0] * iv;
+                        by = ey[k][0] * iv;
                     }
-#pragma unroll
-                    for (int i2 = 0; i2 < NT / 2; ++i2) {
-                        if (2 * i2 < l) {
-                            const uint4 r = colh[i2];  // entries 2 i2 and 2 i2 + 1
-                            const __half2 a0 = *reinterpret_cast<const __half2 *>(&r.x);
-                            const __half2 b0 = *reinterpret_cast<const __half2 *>(&r.y);
-                            const __half2 a1 = *reinterpret_cast<const __half2 *>(&r.z);
-                            const __half2 b1 = *reinterpret_cast<const __half2 *>(&r.w);
-#pragma unroll
-                            for (int k = 0; k < 2; ++k) {
-                                eh[k][2 * i2] = __hfma2(b0, sw[k], __hfma2(a0, sh[k], eh[k][2 * i2]));
-                                if (2 * i2 + 1 < l)
-                                    eh[k][2 * i2 + 1] =
-                                        __hfma2(b1, sw[k], __hfma2(a1, sh[k], eh[k][2 * i2 + 1]));
-                            }
+                    ire[k] = axis_round<QAM>(bx, dre[k]);
+                    iim[k] = axis_round<QAM>(by, dim[k]);
+                    if (p == 2) {
+                        // second nearest: the next point along one axis
+                        const int nre = axis_next<QAM>(bx, ire[k]);
+                        const int nim = axis_next<QAM>(by, iim[k]);
+                        float a = bx - axis_pos<QAM>(nre), c = by - axis_pos<QAM>(nim);
+                        const float d_re = a * a + dim[k];  // (nre, iim)
+                        const float d_im = dre[k] + c * c;  // (ire, nim)
+                        bool take_re = d_re < d_im;
+                        if (d_re == d_im) take_re = sLut[nre * 8 + iim[k]] < sLut[ire[k] * 8 + nim];
+                        if (take_re) {
+                            ire[k] = nre;
+                            dre[k] = d_re;
+                        } else {
+                            iim[k] = nim;
+                            dre[k] = d_im;
                         }
+                        dim[k] = 0.f;
+                    } else if (p > 2) {
+                        int oi, oj;
+                        dre[k] = kth_point_slow<QAM>(bx, by, p, ire[k], iim[k], oi, oj);
+                        dim[k] = 0.f;
+                        ire[k] = oi;
+                        iim[k] = oj;
                     }
-                } else {
-                const float4 *col = reinterpret_cast<const float4 *>(sRc + l * NT);
-#pragma unroll
-                for (int i2 = 0; i2 < NT / 2; ++i2) {
-                    if (2 * i2 < l) {
-                        const float4 r = col[i2];  // R_{2i2,l}, R_{2i2+1,l}
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            ex[k][2 * i2] = fmaf(-r.x, sx[k], fmaf(r.y, sy[k], ex[k][2 * i2]));
-                            ey[k][2 * i2] = fmaf(-r.x, sy[k], fmaf(-r.y, sx[k], ey[k][2 * i2]));
-                            if (2 * i2 + 1 < l) {
-                                ex[k][2 * i2 + 1] =
-                                    fmaf(-r.z, sx[k], fmaf(r.w, sy[k], ex[k][2 * i2 + 1]));
-                                ey[k][2 * i2 + 1] =
-                                    fmaf(-r.z, sy[k], fmaf(-r.w, sx[k], ey[k][2 * i2 + 1]));
-                            }
-                        }
-                    }
+                    dist[k] = dre[k] + dim[k];
+                    sx[k] = axis_pos<QAM>(ire[k]);
+                    sy[k] = axis_pos<QAM>(iim[k]);
+                    lb[k] = sLut[ire[k] * 8 + iim[k]];
                 }
+            }
+            const float r2 = sR2[l];
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                d[k] = fmaf(r2, dist[k], d[k]);
+                lab[k].push(lb[k]);
+            }
+            if constexpr (F16) {
+                __half2 sh[2], sw[2];
+#pragma unroll
+                for (int k = 0; k < 2; ++k) {
+                    sh[k] = __floats2half2_rn(sx[k], sy[k]);
+                    sw[k] = __floats2half2_rn(sy[k], sx[k]);
                 }
+                cancel_level_h<NT>(l, eh, sRh + l * NT, sh, sw);
+            } else {
+                cancel_level<NT>(l, ex, ey, sRr + l * NT, sx, sy);
             }
         }
         warp_reduce_symbol<NT, B>(true, active, row, chunk, chunks, nt, d[0], lab[0], s0, sBest,
@@ -839,9 +902,10 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                 const float2 z = sZ[s * NT + lane];
                 float t1x = z.x, t1y = z.y, t2x = z.x, t2y = z.y;
                 for (int j = lane; j < nt; ++j) {
-                    const float2 r = j == lane ? make_float2(sqrtf(sR2[j]), 0.f) : sRc[j * NT + lane];
-                    const int lb1 = (w1[j / Lab::PER] >> (B * (j % Lab::PER))) & ((1 << B) - 1);
-                    const int lb2 = (w2[j / Lab::PER] >> (B * (j % Lab::PER))) & ((1 << B) - 1);
+                    const float2 r =
+                        j == lane ? make_float2(sqrtf(sR2[j]), 0.f) : sRr[j * NT + (j - 1 - lane)];
+                    const int lb1 = label_at<B>(w1, j);
+                    const int lb2 = label_at<B>(w2, j);
                     const float2 p1 = label_point<QAM>(lb1), p2 = label_point<QAM>(lb2);
                     t1x -= r.x * p1.x - r.y * p1.y;
                     t1y -= r.x * p1.y + r.y * p1.x;
@@ -859,19 +923,14 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
             if (!have2) m2 = INFINITY;
             const bool swap = have2 && m2 < m1;
             const uint32_t *wb = swap ? w2 : w1;
-            if (lane < nt) {
-                const uint32_t w = wb[lane / Lab::PER];
-                hard[det * nt + sPerm[lane]] = (uint8_t)((w >> (B * (lane % Lab::PER))) & ((1 << B) - 1));
-            }
+            if (lane < nt) hard[det * nt + sPerm[lane]] = (uint8_t)label_at<B>(wb, lane);
             if (ped2 != nullptr && lane == 0) {
                 ped2[det * 2] = fminf(m1, m2);
                 ped2[det * 2 + 1] = fmaxf(m1, m2);
             }
         } else {
-        if (lane < nt) {
-            const uint32_t w = sBlab[(s * chunks + bc) * WORDS + lane / Lab::PER];
-            hard[det * nt + sPerm[lane]] = (uint8_t)((w >> (B * (lane % Lab::PER))) & ((1 << B) - 1));
-        }
+        if (lane < nt)
+            hard[det * nt + sPerm[lane]] = (uint8_t)label_at<B>(sBlab + (s * chunks + bc) * WORDS, lane);
         if (ped2 != nullptr) {
             unsigned sec = kInfBits;
             for (int c = lane; c < chunks; c += 32)

@@ -27,6 +27,10 @@ cudaError_t launch_mmse(int n_sc, int n_sym, int nr, int nt, int qam, float sigm
                         const float2 *H, const float2 *Y, uint8_t *hard, float *llr,
                         cudaStream_t stream);
 
+// FP32 FMA throughput probe (mpnl_probe_ffma): 256-thread CTAs.
+cudaError_t launch_ffma_probe(int n_blocks, int iters, float *out, cudaStream_t stream);
+double ffma_probe_flops(int n_blocks, int iters);
+
 // Device status bits (mpnl_check_status).
 constexpr unsigned kStatusBadPathEntry = 1u;
 

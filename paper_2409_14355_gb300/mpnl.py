@@ -37,7 +37,7 @@ ERR_TIMEOUT = -4
 EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_bytes",
             "mpnl_preprocess", "mpnl_preprocess_mmse", "mpnl_select_paths", "mpnl_detect",
             "mpnl_detect_mixed",
-            "mpnl_linear_mmse", "mpnl_check_status")
+            "mpnl_linear_mmse", "mpnl_check_status", "mpnl_probe_ffma")
 PRECISIONS = ("fp32", "fp16")
 
 
@@ -90,6 +90,8 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_linear_mmse.restype = I
         lib.mpnl_check_status.argtypes = [P, P]
         lib.mpnl_check_status.restype = I
+        lib.mpnl_probe_ffma.argtypes = [P, I, I, P, ctypes.POINTER(ctypes.c_double), P]
+        lib.mpnl_probe_ffma.restype = I
         _lib = lib
         return lib
 
@@ -244,6 +246,18 @@ def check_status(device: int | None = None) -> None:
     dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
     ctx = context(dev.index)
     _raise(load_library().mpnl_check_status(ctx, _stream(dev)), ctx)
+
+
+def probe_ffma(n_blocks: int, iters: int, out: torch.Tensor) -> float:
+    """Enqueue the FP32 FMA throughput probe on the current stream (measurement
+    helper, not part of the detector); returns the flops it performs."""
+    dev = out.device
+    _need(out, torch.float32, (n_blocks * 256,), "out")
+    ctx = context(dev.index)
+    f = ctypes.c_double(0.0)
+    _raise(load_library().mpnl_probe_ffma(ctx, int(n_blocks), int(iters), _ptr(out),
+                                          ctypes.byref(f), _stream(dev)), ctx)
+    return f.value
 
 
 class SlotBuffers:

@@ -48,6 +48,8 @@ def test_host_side_errors_without_gpu(lib):
                            ctypes.c_float(1.0), None, None, None, None, None) == mpnl.ERR_INVALID_ARG
     assert lib.mpnl_create(None, 0) == mpnl.ERR_INVALID_ARG
     assert lib.mpnl_workspace_bytes(ctypes.byref(d)) == 0
+    f = ctypes.c_double(0.0)
+    assert lib.mpnl_probe_ffma(None, 1, 1, None, ctypes.byref(f), None) == mpnl.ERR_INVALID_ARG
     lib.mpnl_destroy(None)
 
 
