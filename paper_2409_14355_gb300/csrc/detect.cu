@@ -367,7 +367,34 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     return s;
 }
 
+// In-warp transpose of a 32 x 32 bit matrix: lane p holds row p on entry
+// and column p on return (bit q of the result = bit p of lane q's row).
+// Five butterfly stages exchange ever smaller blocks with the partner lane.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
+{
+    const int lane = threadIdx.x & 31;
+    const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int t = 0; t < 5; ++t) {
+        const int j = 16 >> t;
+        const uint32_t m = masks[t];
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
 // Warp-level results of one symbol for the 32 walks a warp just finished.
+//
+// The 32 keys (PED bits, table row, sorted position) are sorted across the
+// warp (bitonic, over shuffles).  Position 0 is the warp's best walk,
+// position 1 its runner-up.  For the LLRs, X = label bits XOR the best
+// walk's label bits marks, per (level, bit), the walks on the other side of
+// the best walk's bit.  With X laid out by sorted position, a bit transpose
+// gives lane t, for packed bit j = 32 k + t, the set of positions that have
+// bit j; the first of them has the smallest PED, which is the other side's
+// warp minimum.  So every (level, bit) costs one shared atomicMin per side,
+// on addresses distinct across lanes.
 template <int NT, int B>
 __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int row, int chunk,
                                                    int chunks, int nt, float d,
@@ -380,6 +407,7 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
 {
     using Lab = Labels<NT, B>;
     constexpr int WORDS = Lab::WORDS;
+    constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const unsigned db = active ? fbits(d) : kInfBits;
     // key: PED bits, table row (the tie-break), then the sorted position
@@ -387,75 +415,60 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
         active ? (((unsigned long long)db << 32) | ((unsigned)row << 16) | (unsigned)(chunk * 32 + lane))
                : ~0ull;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, key, o);
-        key = k2 < key ? k2 : key;
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(FULL, key, j);
+            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+            key = keep_min ? (o < key ? o : key) : (o > key ? o : key);
+        }
     }
-    const int blane = (int)(key & 31u);  // lane of the warp's best row
-    const unsigned wmin = (unsigned)(key >> 32);
-    const unsigned second = __reduce_min_sync(0xffffffffu, lane == blane ? kInfBits : db);
+    const unsigned long long best = __shfl_sync(FULL, key, 0);
+    const unsigned long long runner = __shfl_sync(FULL, key, 1);
+    const int blane = (int)(best & 31u);  // lane of the warp's best row
+    const unsigned wmin = (unsigned)(best >> 32);
+    const unsigned second = (unsigned)(runner >> 32);
     Lab bl;
 #pragma unroll
-    for (int k = 0; k < WORDS; ++k) bl.w[k] = __shfl_sync(0xffffffffu, lab.w[k], blane);
+    for (int k = 0; k < WORDS; ++k) bl.w[k] = __shfl_sync(FULL, lab.w[k], blane);
     if (sKey2 != nullptr) {
         // the warp's runner-up row (key and labels), for the FP32 re-check
-        unsigned long long k2 = (active && lane != blane)
-                                    ? (((unsigned long long)db << 32) | ((unsigned)row << 16) |
-                                       (unsigned)(chunk * 32 + lane))
-                                    : ~0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long k3 = __shfl_xor_sync(0xffffffffu, k2, o);
-            k2 = k3 < k2 ? k3 : k2;
-        }
-        const int rlane = (int)(k2 & 31u);
+        const int rlane = (int)(runner & 31u);
         uint32_t rw[WORDS];
 #pragma unroll
-        for (int k = 0; k < WORDS; ++k) rw[k] = __shfl_sync(0xffffffffu, lab.w[k], rlane);
+        for (int k = 0; k < WORDS; ++k) rw[k] = __shfl_sync(FULL, lab.w[k], rlane);
         if (valid && lane == 0) {
-            sKey2[s * chunks + chunk] = k2;
+            sKey2[s * chunks + chunk] = runner;
 #pragma unroll
             for (int k = 0; k < WORDS; ++k) sBlab2[(s * chunks + chunk) * WORDS + k] = rw[k];
         }
     }
     if (!valid) return;  // (warp-uniform) second symbol slot beyond n_sym
     if (lane == 0) {
-        atomicMin(&sBest[s], key);
+        atomicMin(&sBest[s], best);
         sWmin[s * chunks + chunk] = wmin;
         sSecond[s * chunks + chunk] = second;
 #pragma unroll
         for (int k = 0; k < WORDS; ++k) sBlab[(s * chunks + chunk) * WORDS + k] = bl.w[k];
     }
     if (!want_llr) return;
-    // per (level, bit): the warp-best row's bit value bb has minimum wmin; the
-    // other value's minimum comes from one redux
-    unsigned mine_other[3] = {kInfBits, kInfBits, kInfBits};
-    int mine_bb[3] = {0, 0, 0};
+    const int src = (int)(key & 31u);  // original lane of this sorted position
+    const bool real = key != ~0ull;
+    const unsigned dp = (unsigned)(key >> 32);
 #pragma unroll
-    for (int l = 0; l < NT; ++l) {
-        if (l < nt) {
-            const int x = lab.get(l) ^ bl.get(l);  // bits that differ from the best row
-            const int bbl = bl.get(l);
-#pragma unroll
-            for (int b = 0; b < B; ++b) {
-                const int sh = B - 1 - b;
-                const unsigned v = ((x >> sh) & 1) ? db : kInfBits;
-                const unsigned mo = __reduce_min_sync(0xffffffffu, v);
-                const int slot = l * B + b;
-                if (lane == (slot & 31)) {
-                    mine_other[slot >> 5] = mo;
-                    mine_bb[slot >> 5] = (bbl >> sh) & 1;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-        const int slot = lane + 32 * q;
-        if (slot < nt * B) {
-            unsigned *mm = sM + (s * NT * B + slot) * 2;
-            atomicMin(mm + mine_bb[q], wmin);
-            atomicMin(mm + (1 - mine_bb[q]), mine_other[q]);
+    for (int k = 0; k < WORDS; ++k) {
+        const uint32_t xm = lab.w[k] ^ bl.w[k];
+        const uint32_t xs = __shfl_sync(FULL, xm, src);
+        const uint32_t col = warp_transpose32(real ? xs : 0u);  // positions having bit 32 k + lane
+        const int owner = col ? __ffs(col) - 1 : 0;
+        const unsigned dmin = __shfl_sync(FULL, dp, owner);
+        const int j = 32 * k + lane;  // packed bit: level j / B, bit (j % B) from the LSB
+        if (j < nt * B) {
+            const int l = j / B, bpos = j - l * B;
+            const int bb = (bl.w[k] >> lane) & 1;  // the best row's bit
+            unsigned *mm = sM + (s * NT * B + l * B + (B - 1 - bpos)) * 2;
+            atomicMin(mm + bb, wmin);
+            if (col) atomicMin(mm + (1 - bb), dmin);
         }
     }
 }
