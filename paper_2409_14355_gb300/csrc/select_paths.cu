@@ -1,4 +1,4 @@
-// Position-vector pre-selection, one CTA per subcarrier.
+// Position-vector pre-selection, one warp per subcarrier.
 //
 // Each level l gets a cost weight w_l = -log Pe_l from its SNR
 // gamma_l = R_ll^2 / sigma2 (square-QAM symbol-error rate, floored); with the
@@ -21,9 +21,10 @@
 // Truncating to N_pe after every level is exact: a vector in the final top
 // N_pe has its restriction to the levels seen so far (ones elsewhere) ahead of
 // it in the order, so that restriction is in the partial top N_pe.
-// Each merge is a merge path: every thread finds where its slice of the
-// output starts by one co-rank binary search and merges from there, so all
-// threads work at once.
+// Each merge is a merge path: every lane finds where its slice of the output
+// (N_pe / 32 entries) starts by one co-rank binary search and merges from
+// there, so the search is paid once per slice and the warp needs no
+// CTA-wide barrier between merges.  A CTA holds several independent warps.
 //
 // A vector is keyed by 16 bytes (two u64, level nt-1 in the most significant
 // byte): comparing keys as unsigned integers is the lexicographic order from
@@ -48,29 +49,40 @@ __device__ __forceinline__ void level_shift(int nt, int l, bool &in_hi, int &shi
     shift = in_hi ? 56 - 8 * t : 56 - 8 * (t - 8);
 }
 
+constexpr int kSelMaxWarps = 4;
+
+__host__ __device__ inline size_t sel_warp_bytes(int n_pe)
+{
+    // 3 lists x (8 + 8 + 4) bytes, then w[]; 16-byte multiple so that the
+    // next warp's 8-byte keys stay aligned
+    return ((size_t)n_pe * 60 + kMaxNt * 4 + 15) & ~(size_t)15;
+}
+
 template <int QAM>
-__global__ void __launch_bounds__(256)
-select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
+__global__ void __launch_bounds__(kSelMaxWarps * 32)
+select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
                     uint8_t *__restrict__ paths)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int sc = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int T = blockDim.x;
+    constexpr unsigned FULL = 0xffffffffu;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int sc = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (sc >= n_sc) return;  // warp-uniform; the warps share no data and no barrier
 
     // three lists (struct of arrays) addressed as base + list * n_pe, so that
     // the list index stays arithmetic (no pointer arrays in local memory)
-    unsigned long long *HI = reinterpret_cast<unsigned long long *>(smem_raw);
+    unsigned char *base = smem_raw + (size_t)warp * sel_warp_bytes(n_pe);
+    unsigned long long *HI = reinterpret_cast<unsigned long long *>(base);
     unsigned long long *LO = HI + 3 * n_pe;
     float *CO = reinterpret_cast<float *>(LO + 3 * n_pe);
+    float *w = CO + 3 * n_pe;
 #define hi(b) (HI + (size_t)(b) * n_pe)
 #define lo(b) (LO + (size_t)(b) * n_pe)
 #define cost(b) (CO + (size_t)(b) * n_pe)
-    __shared__ float w[kMaxNt];
 
     const int P = nt * (nt + 1) / 2;
-    if (tid < nt) {
-        const int l = tid;
+    if (lane < nt) {
+        const int l = lane;
         const float rll = Rp[(size_t)sc * P + l * nt - l * (l - 1) / 2].x;
         const float gamma = rll * rll / sigma2;
         const float x = sqrtf(3.0f * gamma / (float)(QAM - 1));
@@ -81,27 +93,45 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
         pe = fmaxf(pe, kPeFloor);
         w[l] = -logf(pe);
     }
-    __syncthreads();
+    __syncwarp();
     // Upper bound on the final N_pe-th cost: the vectors that deviate from
     // all-ones at a single level (cost j w_l) plus all-ones itself are valid
     // vectors, so if N_pe of them cost <= v, the answer's N_pe-th cost is
     // <= v.  Shifts whose first entry j w_m exceeds the bound cannot
     // contribute and are skipped (the bound is padded against rounding).
-    __shared__ unsigned s_bound;
-    if (tid == 0) s_bound = 0x7f800000u;  // +inf
-    __syncthreads();
-    for (int k = tid; k < nt * (QAM - 1); k += T) {
-        const int l = k / (QAM - 1), j = 1 + k % (QAM - 1);
-        const float v = (float)j * w[l];
-        int cnt = 1;
-        for (int m = 0; m < nt; ++m) {
-            const int c = (int)floorf(v * (1.0f - 1e-6f) / w[m]);
-            cnt += c < 0 ? 0 : (c > QAM - 1 ? QAM - 1 : c);
+    // The count of single-deviation vectors with cost <= j w_l is monotone in
+    // j, so lane l binary-searches the smallest j that reaches N_pe.  The
+    // count never exceeds the exact one: v (1 - 1e-6) / w_m is formed with a
+    // rounded reciprocal (relative error below 2^-22 << 1e-6), so the
+    // quotient stays below the exact v / w_m and its floor cannot overshoot.
+    unsigned bbits = 0x7f800000u;  // +inf
+    if (lane < nt) {
+        const float wl = w[lane];
+        float inv[kMaxNt];
+#pragma unroll
+        for (int m = 0; m < kMaxNt; ++m) inv[m] = m < nt ? 1.0f / w[m] : 0.f;
+        auto count = [&](int j) {
+            const float v = (float)j * wl * (1.0f - 1e-6f);
+            int cnt = 1;
+#pragma unroll
+            for (int m = 0; m < kMaxNt; ++m) {
+                const int c = (int)floorf(v * inv[m]);
+                cnt += m < nt ? (c < 0 ? 0 : (c > QAM - 1 ? QAM - 1 : c)) : 0;
+            }
+            return cnt;
+        };
+        if (count(QAM - 1) >= n_pe) {
+            int lo_j = 1, hi_j = QAM - 1;  // count(hi_j) >= n_pe
+            while (lo_j < hi_j) {
+                const int mid = (lo_j + hi_j) >> 1;
+                if (count(mid) >= n_pe) hi_j = mid;
+                else lo_j = mid + 1;
+            }
+            const float v = (float)lo_j * wl;
+            bbits = __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f);
         }
-        if (cnt >= n_pe) atomicMin(&s_bound, __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f));
     }
-    __syncthreads();
-    const float bound = __uint_as_float(s_bound);
+    const float bound = __uint_as_float(__reduce_min_sync(FULL, bbits));
     // The first level processed (nt-1) in closed form: starting from the
     // all-ones vector, its list is the arithmetic sequence j * w (rank j + 1
     // at that level), already sorted, cut at N_pe, at M and at the bound --
@@ -122,14 +152,14 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
         bool in_hi;
         int sh;
         level_shift(nt, mt, in_hi, sh);
-        for (int j = tid; j < nL; j += T) {
+        for (int j = lane; j < nL; j += 32) {
             const unsigned long long add = (unsigned long long)j << sh;
             hi(0)[j] = h + (in_hi ? add : 0ull);
             lo(0)[j] = o + (in_hi ? 0ull : add);
             cost(0)[j] = (float)j * wt;
         }
     }
-    __syncthreads();
+    __syncwarp();
     for (int m = nt - 2; m >= 0; --m) {
         const float wm = w[m];
         bool in_hi;
@@ -151,11 +181,11 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
                     break;
             }
             const int nOut = min(n_pe, nB + nL);
-            // Merge path: thread t writes outputs [k0, k1).  A co-rank binary
+            // Merge path: lane t writes outputs [k0, k1).  A co-rank binary
             // search finds how many of the first k0 outputs come from B (the
-            // rest from the shifted list C), then the thread merges onward.
-            const int per = (nOut + T - 1) / T;
-            const int k0 = min(nOut, tid * per), k1 = min(nOut, k0 + per);
+            // rest from the shifted list C), then the lane merges onward.
+            const int per = (nOut + 31) >> 5;
+            const int k0 = min(nOut, lane * per), k1 = min(nOut, k0 + per);
             if (k0 < k1) {
                 int lo_i = max(0, k0 - nL), hi_i = min(k0, nB);
                 while (lo_i < hi_i) {
@@ -188,7 +218,7 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
                     else ++jj;
                 }
             }
-            __syncthreads();
+            __syncwarp();
             nB = nOut;
             // next output goes to the buffer that is neither L nor the new B
             bi = oi;
@@ -196,12 +226,11 @@ select_paths_kernel(int nt, int n_pe, float sigma2, const float2 *__restrict__ R
         }
         li = bi;
         nL = nB;
-        __syncthreads();
     }
 
     // write the table: row r, level l -> byte of the key
     uint8_t *out = paths + (size_t)sc * n_pe * nt;
-    for (int k = tid; k < n_pe * nt; k += T) {
+    for (int k = lane; k < n_pe * nt; k += 32) {
         const int r = k / nt, l = k - r * nt;
         bool in_hi;
         int sh;
@@ -219,14 +248,18 @@ template <int QAM>
 cudaError_t launch_tpl(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
                        uint8_t *paths, cudaStream_t stream)
 {
-    const size_t smem = (size_t)n_pe * 60;  // 3 lists x (8 + 8 + 4) bytes
+    // as many warps (subcarriers) per CTA as fit in about 200 KB of shared memory
+    const size_t per = sel_warp_bytes(n_pe);
+    int warps = (int)((200 * 1024) / per);
+    warps = warps < 1 ? 1 : (warps > kSelMaxWarps ? kSelMaxWarps : warps);
+    const size_t smem = per * warps;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(select_paths_kernel<QAM>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    int threads = n_pe >= 256 ? 256 : (n_pe >= 128 ? 128 : (n_pe >= 64 ? 64 : 32));
-    select_paths_kernel<QAM><<<n_sc, threads, smem, stream>>>(nt, n_pe, sigma2, R, paths);
+    const int grid = (n_sc + warps - 1) / warps;
+    select_paths_kernel<QAM><<<grid, warps * 32, smem, stream>>>(n_sc, nt, n_pe, sigma2, R, paths);
     return cudaGetLastError();
 }
 

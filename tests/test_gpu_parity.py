@@ -98,7 +98,7 @@ def _scores(paths, pe):
 ])
 def test_select_paths_matches_oracle(dev, nt, qam, n_pe, snr_db):
     mpnl = _mpnl()
-    n_sc = 24
+    n_sc = 25  # not a multiple of the subcarriers one CTA takes
     sl = inputs.make_slot(nt, nt, qam, n_sc, 1, snr_db, "iid", 0.3, 7 + nt * qam + n_pe)
     Rr, _, _, _ = P.oracle_front(sl.H.astype(np.complex128), sl.Y.astype(np.complex128))
     R32 = Rr.astype(np.complex64)
