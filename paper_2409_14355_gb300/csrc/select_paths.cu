@@ -1,4 +1,4 @@
-// Position-vector pre-selection, one warp per subcarrier.
+// Position-vector pre-selection, one group of G warps per subcarrier.
 //
 // Each level l gets a cost weight w_l = -log Pe_l from its SNR
 // gamma_l = R_ll^2 / sigma2 (square-QAM symbol-error rate, floored); with the
@@ -21,10 +21,11 @@
 // Truncating to N_pe after every level is exact: a vector in the final top
 // N_pe has its restriction to the levels seen so far (ones elsewhere) ahead of
 // it in the order, so that restriction is in the partial top N_pe.
-// Each merge is a merge path: every lane finds where its slice of the output
-// (N_pe / 32 entries) starts by one co-rank binary search and merges from
-// there, so the search is paid once per slice and the warp needs no
-// CTA-wide barrier between merges.  A CTA holds several independent warps.
+// Each merge is a merge path: every thread finds where its slice of the
+// output (N_pe / (32 G) entries) starts by one co-rank binary search and
+// merges from there.  G = 1 (a warp, no barrier) for short lists; G = 2 for
+// N_pe >= 256, where halving the serial slice outweighs a two-warp named
+// barrier per merge.  A CTA holds several independent groups.
 //
 // A vector is keyed by 16 bytes (two u64, level nt-1 in the most significant
 // byte): comparing keys as unsigned integers is the lexicographic order from
@@ -51,38 +52,53 @@ __device__ __forceinline__ void level_shift(int nt, int l, bool &in_hi, int &shi
 
 constexpr int kSelMaxWarps = 4;
 
-__host__ __device__ inline size_t sel_warp_bytes(int n_pe)
+__host__ __device__ inline size_t sel_group_bytes(int n_pe)
 {
-    // 3 lists x (8 + 8 + 4) bytes, then w[]; 16-byte multiple so that the
-    // next warp's 8-byte keys stay aligned
-    return ((size_t)n_pe * 60 + kMaxNt * 4 + 15) & ~(size_t)15;
+    // 3 lists x (8 + 8 + 4) bytes, then w[] and the bound; 16-byte multiple
+    // so that the next group's 8-byte keys stay aligned
+    return ((size_t)n_pe * 60 + kMaxNt * 4 + 4 + 15) & ~(size_t)15;
 }
 
-template <int QAM>
+template <int G>
+__device__ __forceinline__ void group_sync(int group)
+{
+    static_assert(G == 1 || kSelMaxWarps / G <= 2, "named barriers 1 and 2 only");
+    if constexpr (G == 1) {
+        __syncwarp();
+    } else if (group == 0) {
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * G) : "memory");
+    } else {
+        asm volatile("bar.sync 2, %0;" ::"n"(32 * G) : "memory");
+    }
+}
+
+template <int QAM, int G>
 __global__ void __launch_bounds__(kSelMaxWarps * 32)
 select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
                     uint8_t *__restrict__ paths)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr unsigned FULL = 0xffffffffu;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sc = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (sc >= n_sc) return;  // warp-uniform; the warps share no data and no barrier
+    constexpr int T = 32 * G;  // threads per subcarrier
+    const int group = threadIdx.x / T, tid = threadIdx.x % T;
+    const int sc = blockIdx.x * (blockDim.x / T) + group;
+    if (sc >= n_sc) return;  // whole groups leave; each group syncs only itself
 
     // three lists (struct of arrays) addressed as base + list * n_pe, so that
     // the list index stays arithmetic (no pointer arrays in local memory)
-    unsigned char *base = smem_raw + (size_t)warp * sel_warp_bytes(n_pe);
+    unsigned char *base = smem_raw + (size_t)group * sel_group_bytes(n_pe);
     unsigned long long *HI = reinterpret_cast<unsigned long long *>(base);
     unsigned long long *LO = HI + 3 * n_pe;
     float *CO = reinterpret_cast<float *>(LO + 3 * n_pe);
     float *w = CO + 3 * n_pe;
+    unsigned *s_bound = reinterpret_cast<unsigned *>(w + kMaxNt);
 #define hi(b) (HI + (size_t)(b) * n_pe)
 #define lo(b) (LO + (size_t)(b) * n_pe)
 #define cost(b) (CO + (size_t)(b) * n_pe)
 
     const int P = nt * (nt + 1) / 2;
-    if (lane < nt) {
-        const int l = lane;
+    if (tid < nt) {
+        const int l = tid;
         const float rll = Rp[(size_t)sc * P + l * nt - l * (l - 1) / 2].x;
         const float gamma = rll * rll / sigma2;
         const float x = sqrtf(3.0f * gamma / (float)(QAM - 1));
@@ -93,45 +109,51 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
         pe = fmaxf(pe, kPeFloor);
         w[l] = -logf(pe);
     }
-    __syncwarp();
+    group_sync<G>(group);
     // Upper bound on the final N_pe-th cost: the vectors that deviate from
     // all-ones at a single level (cost j w_l) plus all-ones itself are valid
     // vectors, so if N_pe of them cost <= v, the answer's N_pe-th cost is
     // <= v.  Shifts whose first entry j w_m exceeds the bound cannot
     // contribute and are skipped (the bound is padded against rounding).
     // The count of single-deviation vectors with cost <= j w_l is monotone in
-    // j, so lane l binary-searches the smallest j that reaches N_pe.  The
-    // count never exceeds the exact one: v (1 - 1e-6) / w_m is formed with a
-    // rounded reciprocal (relative error below 2^-22 << 1e-6), so the
-    // quotient stays below the exact v / w_m and its floor cannot overshoot.
-    unsigned bbits = 0x7f800000u;  // +inf
-    if (lane < nt) {
-        const float wl = w[lane];
-        float inv[kMaxNt];
+    // j, so thread l of the first warp binary-searches the smallest j that
+    // reaches N_pe.  The count never exceeds the exact one: v (1 - 1e-6) /
+    // w_m is formed with a rounded reciprocal (relative error below 2^-22 <<
+    // 1e-6), so the quotient stays below the exact v / w_m and its floor
+    // cannot overshoot.
+    if (tid < 32) {
+        unsigned bbits = 0x7f800000u;  // +inf
+        if (tid < nt) {
+            const float wl = w[tid];
+            float inv[kMaxNt];
 #pragma unroll
-        for (int m = 0; m < kMaxNt; ++m) inv[m] = m < nt ? 1.0f / w[m] : 0.f;
-        auto count = [&](int j) {
-            const float v = (float)j * wl * (1.0f - 1e-6f);
-            int cnt = 1;
+            for (int m = 0; m < kMaxNt; ++m) inv[m] = m < nt ? 1.0f / w[m] : 0.f;
+            auto count = [&](int j) {
+                const float v = (float)j * wl * (1.0f - 1e-6f);
+                int cnt = 1;
 #pragma unroll
-            for (int m = 0; m < kMaxNt; ++m) {
-                const int c = (int)floorf(v * inv[m]);
-                cnt += m < nt ? (c < 0 ? 0 : (c > QAM - 1 ? QAM - 1 : c)) : 0;
+                for (int m = 0; m < kMaxNt; ++m) {
+                    const int c = (int)floorf(v * inv[m]);
+                    cnt += m < nt ? (c < 0 ? 0 : (c > QAM - 1 ? QAM - 1 : c)) : 0;
+                }
+                return cnt;
+            };
+            if (count(QAM - 1) >= n_pe) {
+                int lo_j = 1, hi_j = QAM - 1;  // count(hi_j) >= n_pe
+                while (lo_j < hi_j) {
+                    const int mid = (lo_j + hi_j) >> 1;
+                    if (count(mid) >= n_pe) hi_j = mid;
+                    else lo_j = mid + 1;
+                }
+                const float v = (float)lo_j * wl;
+                bbits = __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f);
             }
-            return cnt;
-        };
-        if (count(QAM - 1) >= n_pe) {
-            int lo_j = 1, hi_j = QAM - 1;  // count(hi_j) >= n_pe
-            while (lo_j < hi_j) {
-                const int mid = (lo_j + hi_j) >> 1;
-                if (count(mid) >= n_pe) hi_j = mid;
-                else lo_j = mid + 1;
-            }
-            const float v = (float)lo_j * wl;
-            bbits = __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f);
         }
+        bbits = __reduce_min_sync(FULL, bbits);
+        if (tid == 0) *s_bound = bbits;
     }
-    const float bound = __uint_as_float(__reduce_min_sync(FULL, bbits));
+    group_sync<G>(group);
+    const float bound = __uint_as_float(*s_bound);
     // The first level processed (nt-1) in closed form: starting from the
     // all-ones vector, its list is the arithmetic sequence j * w (rank j + 1
     // at that level), already sorted, cut at N_pe, at M and at the bound --
@@ -152,14 +174,14 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
         bool in_hi;
         int sh;
         level_shift(nt, mt, in_hi, sh);
-        for (int j = lane; j < nL; j += 32) {
+        for (int j = tid; j < nL; j += T) {
             const unsigned long long add = (unsigned long long)j << sh;
             hi(0)[j] = h + (in_hi ? add : 0ull);
             lo(0)[j] = o + (in_hi ? 0ull : add);
             cost(0)[j] = (float)j * wt;
         }
     }
-    __syncwarp();
+    group_sync<G>(group);
     for (int m = nt - 2; m >= 0; --m) {
         const float wm = w[m];
         bool in_hi;
@@ -181,11 +203,11 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
                     break;
             }
             const int nOut = min(n_pe, nB + nL);
-            // Merge path: lane t writes outputs [k0, k1).  A co-rank binary
+            // Merge path: thread t writes outputs [k0, k1).  A co-rank binary
             // search finds how many of the first k0 outputs come from B (the
-            // rest from the shifted list C), then the lane merges onward.
-            const int per = (nOut + 31) >> 5;
-            const int k0 = min(nOut, lane * per), k1 = min(nOut, k0 + per);
+            // rest from the shifted list C), then the thread merges onward.
+            const int per = (nOut + T - 1) / T;
+            const int k0 = min(nOut, tid * per), k1 = min(nOut, k0 + per);
             if (k0 < k1) {
                 int lo_i = max(0, k0 - nL), hi_i = min(k0, nB);
                 while (lo_i < hi_i) {
@@ -218,7 +240,7 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
                     else ++jj;
                 }
             }
-            __syncwarp();
+            group_sync<G>(group);
             nB = nOut;
             // next output goes to the buffer that is neither L nor the new B
             bi = oi;
@@ -230,7 +252,7 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
 
     // write the table: row r, level l -> byte of the key
     uint8_t *out = paths + (size_t)sc * n_pe * nt;
-    for (int k = lane; k < n_pe * nt; k += 32) {
+    for (int k = tid; k < n_pe * nt; k += T) {
         const int r = k / nt, l = k - r * nt;
         bool in_hi;
         int sh;
@@ -238,29 +260,38 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
         const unsigned long long v = in_hi ? hi(li)[r] : lo(li)[r];
         out[k] = (uint8_t)((v >> sh) & 0xffull);
     }
-}
-
 #undef hi
 #undef lo
 #undef cost
+}
+
+template <int QAM, int G>
+cudaError_t launch_group(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
+                         uint8_t *paths, cudaStream_t stream)
+{
+    // as many groups (subcarriers) per CTA as fit in about 100 KB of shared
+    // memory, at most kSelMaxWarps warps
+    const size_t per = sel_group_bytes(n_pe);
+    int groups = (int)((100 * 1024) / per);
+    groups = groups < 1 ? 1 : (groups > kSelMaxWarps / G ? kSelMaxWarps / G : groups);
+    const size_t smem = per * groups;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(select_paths_kernel<QAM, G>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = (n_sc + groups - 1) / groups;
+    select_paths_kernel<QAM, G><<<grid, groups * G * 32, smem, stream>>>(n_sc, nt, n_pe, sigma2, R,
+                                                                        paths);
+    return cudaGetLastError();
+}
 
 template <int QAM>
 cudaError_t launch_tpl(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
                        uint8_t *paths, cudaStream_t stream)
 {
-    // as many warps (subcarriers) per CTA as fit in about 200 KB of shared memory
-    const size_t per = sel_warp_bytes(n_pe);
-    int warps = (int)((200 * 1024) / per);
-    warps = warps < 1 ? 1 : (warps > kSelMaxWarps ? kSelMaxWarps : warps);
-    const size_t smem = per * warps;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(select_paths_kernel<QAM>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    const int grid = (n_sc + warps - 1) / warps;
-    select_paths_kernel<QAM><<<grid, warps * 32, smem, stream>>>(n_sc, nt, n_pe, sigma2, R, paths);
-    return cudaGetLastError();
+    return n_pe >= 256 ? launch_group<QAM, 2>(n_sc, nt, n_pe, sigma2, R, paths, stream)
+                       : launch_group<QAM, 1>(n_sc, nt, n_pe, sigma2, R, paths, stream);
 }
 
 }  // namespace
