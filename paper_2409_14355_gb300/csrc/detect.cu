@@ -43,29 +43,41 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTopList = 64;  // entries of the first-level neighbour list
-constexpr int kList2 = 64;    // per symbol: entries of all second-level lists together
+constexpr int kList2 = 128;   // per symbol: entries of all second-level lists together
 
 // --------------------------------------------------------------------------
 // ranking
 // --------------------------------------------------------------------------
 
 // Nearest grid index along one axis by rounding (an exact midpoint goes to
-// the smaller axis label); returns the index, writes the squared distance.
+// the smaller axis label); returns the index, writes the squared distance and
+// the grid coordinate.  Round-half-even is corrected only on the rare exact
+// midpoint (|u - rint(u)| == 0.5, where u - 0.5 is the floor exactly).
 template <int QAM>
-__device__ __forceinline__ int axis_round(float x, float &d)
+__device__ __forceinline__ int axis_round(float x, float &d, float &pos)
 {
     constexpr int L = Qam<QAM>::L;
     const float u = fmaf(x, 0.5f * Qam<QAM>::kScale, 0.5f * (float)(L - 1));
-    float fr = fminf(fmaxf(rintf(u), 0.f), (float)(L - 1));
-    const float fl = floorf(u);
-    if (u - fl == 0.5f && fl >= 0.f && fl < (float)(L - 1)) {
-        const int a = (int)fl;
-        fr = Qam<QAM>::axis_label(a) < Qam<QAM>::axis_label(a + 1) ? fl : fl + 1.f;
+    float fr = rintf(u);
+    if (fabsf(u - fr) == 0.5f) {
+        const float fl = u - 0.5f;
+        if (fl >= 0.f && fl < (float)(L - 1)) {
+            const int a = (int)fl;
+            fr = Qam<QAM>::axis_label(a) < Qam<QAM>::axis_label(a + 1) ? fl : fl + 1.f;
+        }
     }
-    const float pos = fmaf(fr, 2.f * Qam<QAM>::kInvScale, -(float)(L - 1) * Qam<QAM>::kInvScale);
+    fr = fminf(fmaxf(fr, 0.f), (float)(L - 1));
+    pos = fmaf(fr, 2.f * Qam<QAM>::kInvScale, -(float)(L - 1) * Qam<QAM>::kInvScale);
     const float df = x - pos;
     d = df * df;
     return (int)fr;
+}
+
+template <int QAM>
+__device__ __forceinline__ int axis_round(float x, float &d)
+{
+    float pos;
+    return axis_round<QAM>(x, d, pos);
 }
 
 // The next grid index after i0 in distance order along an axis (one step
@@ -814,8 +826,8 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                         bx = ex[k][0] * iv;
                         by = ey[k][0] * iv;
                     }
-                    ire[k] = axis_round<QAM>(bx, dre[k]);
-                    iim[k] = axis_round<QAM>(by, dim[k]);
+                    ire[k] = axis_round<QAM>(bx, dre[k], sx[k]);
+                    iim[k] = axis_round<QAM>(by, dim[k], sy[k]);
                     if (p == 2) {
                         // second nearest: the next point along one axis
                         const int nre = axis_next<QAM>(bx, ire[k]);
@@ -828,9 +840,11 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                         if (take_re) {
                             ire[k] = nre;
                             dre[k] = d_re;
+                            sx[k] = axis_pos<QAM>(nre);
                         } else {
                             iim[k] = nim;
                             dre[k] = d_im;
+                            sy[k] = axis_pos<QAM>(nim);
                         }
                         dim[k] = 0.f;
                     } else if (p > 2) {
@@ -839,10 +853,10 @@ detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__re
                         dim[k] = 0.f;
                         ire[k] = oi;
                         iim[k] = oj;
+                        sx[k] = axis_pos<QAM>(oi);
+                        sy[k] = axis_pos<QAM>(oj);
                     }
                     dist[k] = dre[k] + dim[k];
-                    sx[k] = axis_pos<QAM>(ire[k]);
-                    sy[k] = axis_pos<QAM>(iim[k]);
                     lb[k] = sLut[ire[k] * 8 + iim[k]];
                 }
             }
@@ -977,9 +991,8 @@ cudaError_t launch_prec(int n_sc, int n_sym, int nt, int n_pe, float sigma2, con
 {
     const DetSmem S = det_layout(NT, Qam<QAM>::B, n_pe, n_sym, Labels<NT, Qam<QAM>::B>::WORDS);
     const size_t smem = S.bytes;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(detect_walk_kernel<NT, QAM, F16>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = allow_dynamic_smem(detect_walk_kernel<NT, QAM, F16>, smem);
         if (e != cudaSuccess) return e;
     }
     detect_walk_kernel<NT, QAM, F16><<<n_sc, kThreads, smem, stream>>>(

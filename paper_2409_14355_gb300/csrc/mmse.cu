@@ -226,9 +226,8 @@ cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, float sigma2, const 
 {
     const MmseSmem S = mmse_smem_layout(nr, nt, n_sym);
     const size_t smem = (size_t)S.bytes * kWarps;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(mmse_kernel<NT, QAM>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = allow_dynamic_smem(mmse_kernel<NT, QAM>, smem);
         if (e != cudaSuccess) return e;
     }
     const int grid = (n_sc + kWarps - 1) / kWarps;

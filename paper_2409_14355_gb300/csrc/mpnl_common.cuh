@@ -97,4 +97,17 @@ __device__ __forceinline__ int axis_nearest(float x, float &dist)
 
 __device__ __forceinline__ unsigned fbits(float x) { return __float_as_uint(x); }
 
+// Opt a kernel in to `dyn` bytes of dynamic shared memory when its static
+// plus dynamic shared memory exceeds the 48 KB available without opt-in.
+template <typename Kernel>
+inline cudaError_t allow_dynamic_smem(Kernel kernel, size_t dyn)
+{
+    if (dyn <= 32 * 1024) return cudaSuccess;  // every kernel here has < 16 KB static
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    if (dyn + a.sharedSizeBytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+}
+
 }  // namespace mpnl

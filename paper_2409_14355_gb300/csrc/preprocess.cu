@@ -196,9 +196,8 @@ cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, float sigma, const f
 {
     const WarpSmem L = warp_smem_layout(nr, nt, n_sym);
     const size_t smem = (size_t)L.bytes * kWarpsPerCta;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sqrd_qhy_kernel<NR, CS>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = allow_dynamic_smem(sqrd_qhy_kernel<NR, CS>, smem);
         if (e != cudaSuccess) return e;
     }
     const int grid = (n_sc + kWarpsPerCta - 1) / kWarpsPerCta;

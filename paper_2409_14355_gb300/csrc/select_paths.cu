@@ -275,9 +275,8 @@ cudaError_t launch_group(int n_sc, int nt, int n_pe, float sigma2, const float2 
     int groups = (int)((100 * 1024) / per);
     groups = groups < 1 ? 1 : (groups > kSelMaxWarps / G ? kSelMaxWarps / G : groups);
     const size_t smem = per * groups;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(select_paths_kernel<QAM, G>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = allow_dynamic_smem(select_paths_kernel<QAM, G>, smem);
         if (e != cudaSuccess) return e;
     }
     const int grid = (n_sc + groups - 1) / groups;
