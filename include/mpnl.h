@@ -181,6 +181,83 @@ int mpnl_linear_mmse(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const 
  * MPNL_ERR_INVALID_ARG (with a message) or MPNL_ERR_CUDA. */
 int mpnl_check_status(mpnl_ctx *ctx, void *stream);
 
+/* Mixed-size batches in persistent launches ---------------------------------
+ *
+ * A batch holds the slots of many radio units with different sizes.  Each
+ * stage (sorted QR + z, selection, walks, MMSE baseline) is ONE persistent
+ * launch for the whole batch: its workers (a warp, a group of warps or a
+ * CTA) take (unit, subcarrier) items from a device counter, largest units
+ * first, and run the kernel instance that fits each unit.  With
+ * MPNL_RUN_GRAPH the stages are captured once into a CUDA graph and replayed.
+ * The results are those of the per-call API on each unit alone. */
+typedef struct {
+    mpnl_dims dims;
+    float sigma2;
+    int flags;            /* MPNL_ITEM_MMSE_QR, MPNL_ITEM_LINEAR_MMSE */
+    const void *H;        /* in  c64 [n_sc][nr][nt] */
+    const void *Y;        /* in  c64 [n_sc][n_sym][nr] */
+    void *R;              /* out c64 [n_sc][nt(nt+1)/2]  (unit state, as mpnl_preprocess) */
+    float *inv_diag;      /* out f32 [n_sc][nt] */
+    uint8_t *perm;        /* out u8  [n_sc][nt] */
+    void *Z;              /* out c64 [n_sc][n_sym][nt] */
+    uint8_t *paths;       /* out u8  [n_sc][n_pe][nt]    (as mpnl_select_paths) */
+    uint8_t *hard;        /* out u8  [n_sc][n_sym][nt]   (as mpnl_detect) */
+    float *llr;           /* out f32 [n_sc][n_sym][nt][log2 qam] (NULL: skip) */
+    float *ped2;          /* out f32 [n_sc][n_sym][2]    (NULL: skip) */
+    uint8_t *mmse_hard;   /* out u8  [n_sc][n_sym][nt]   with MPNL_ITEM_LINEAR_MMSE */
+    float *mmse_llr;      /* out f32 [n_sc][n_sym][nt][log2 qam] (NULL: skip) */
+} mpnl_batch_item;
+
+#define MPNL_ITEM_MMSE_QR 1      /* MMSE-extended QR (mpnl_preprocess_mmse); allows nt > nr */
+#define MPNL_ITEM_LINEAR_MMSE 2  /* also run the linear MMSE baseline */
+
+#define MPNL_STAGE_PREPROCESS 1
+#define MPNL_STAGE_SELECT 2
+#define MPNL_STAGE_DETECT 4
+#define MPNL_STAGE_MMSE 8
+#define MPNL_STAGES_ALL 15
+#define MPNL_RUN_GRAPH 16  /* capture the stages into a CUDA graph once, then replay it */
+
+typedef struct mpnl_batch mpnl_batch;
+
+/* Validate `n_items` items (each as the per-call API would), order them
+ * largest first and copy their descriptors to the device.  The batch keeps
+ * the items' pointers (not the host array); it allocates its descriptor
+ * table and counters here, never when it runs.  Errors: as the per-call
+ * checks (MPNL_ERR_INVALID_ARG with the item index in the message),
+ * MPNL_ERR_UNSUPPORTED if a unit needs more shared memory than an SM has,
+ * MPNL_ERR_CUDA. */
+int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
+                      mpnl_batch **batch);
+
+/* Enqueue the stages in `stages` (MPNL_STAGE_* bits, in pipeline order) on
+ * `stream`; with MPNL_RUN_GRAPH the stream must not be the legacy default
+ * stream (NULL).  Device-side argument errors go to mpnl_check_status. */
+int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *batch, int stages, void *stream);
+
+/* Release a batch (NULL is ignored); its work must have completed. */
+void mpnl_batch_destroy(mpnl_batch *batch);
+
+/* Launch-shape knobs.  They change how the work is spread over threads,
+ * never the results.  Indexed by problem class: nt class (0: nt <= 4,
+ * 1: nt <= 8, 2: nt <= 16), qam class (0: 4, 1: 16, 2: 64) and N_pe class
+ * (0: n_pe < 256, 1: n_pe >= 256).  An entry of 0 means the built-in choice.
+ * The package's autotuner measures the candidates and sets them. */
+typedef struct {
+    uint8_t detect_sym[3][3][2];    /* symbols per lane in the walk kernel: 1 or 2 (built-in 2) */
+    uint8_t select_warps[3][3][2];  /* warps per subcarrier in the selection: 1, 2 or 4
+                                       (built-in: 2 for n_pe >= 256, else 1) */
+    uint8_t persistent_ctas_per_sm; /* CTAs per SM of the batch (persistent) walk launch: 1 or 2
+                                       (built-in 2) */
+} mpnl_tuning;
+
+/* Set the knobs of this context (NULL restores the built-in choices);
+ * values outside the ranges above are rejected (MPNL_ERR_INVALID_ARG). */
+int mpnl_set_tuning(mpnl_ctx *ctx, const mpnl_tuning *tuning);
+
+/* Copy this context's knobs to *tuning (zeros for built-in choices). */
+int mpnl_get_tuning(mpnl_ctx *ctx, mpnl_tuning *tuning);
+
 /* Measurement helper, not part of the detector (the paper has no
  * counterpart): enqueue an FP32 FMA throughput kernel of n_blocks CTAs of 256
  * threads, each thread running 8 independent fmaf chains for `iters` rounds,

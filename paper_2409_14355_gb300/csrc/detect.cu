@@ -1,1052 +1,26 @@
-// Evaluation of the N_pe position vectors of every (subcarrier, symbol):
-// SIC / partial-Euclidean-distance walks, argmin, max-log LLRs.
-//
-// One CTA per subcarrier; R, 1/R_ll, perm, the table and the subcarrier's z
-// vectors are staged in shared memory once.  A warp takes 32 rows of the
-// table for two OFDM symbols; each lane runs the walks of one row for both
-// symbols with the whole state in registers:
-//
-//   e := z
-//   for l = nt-1 .. 0:
-//     b   = e_l / R_ll
-//     s_l = the p_l-th closest constellation point to b (distance, then label)
-//     d  += R_ll^2 |b - s_l|^2
-//     e_i -= R_il s_l   for every i < l          (4 FFMA per complex term)
-//
-// Column l of R is read with 16-byte shared loads that all lanes issue for the
-// same address (broadcast) and that serve both symbols.
-//
-// Ranking.  Rank 1 (the SIC choice; ~90% of the entries below the first
-// level) is per-axis rounding to the grid; rank 2 compares the two next
-// neighbours; higher ranks enumerate the nearest points in order (out of
-// line).  The first detected level sees the same b for every row, so its
-// ordered neighbour list is built once per symbol and looked up.  Rows are
-// sorted in the CTA by how far they deviate from rank 1 below the first
-// level, so that lanes needing the slower paths share warps.
-//
-// Reductions, without contended atomics:
-//   warp:  argmin key (d, row) by shuffles; runner-up d and, for every
-//          (level, bit), the minimum d over the warp's rows whose bit differs
-//          from the warp-best row's bit, by redux.sync;
-//   CTA:   per (symbol, level, bit, value) a u32 atomicMin on shared memory
-//          (one per warp, distinct addresses across lanes); per symbol a
-//          64-bit atomicMin on the argmin key (one per warp);
-//   final: one lane per (symbol, level, bit) forms the LLR.
-#include <cuda_fp16.h>
-
-#include "mpnl_common.cuh"
-#include "mpnl_internal.h"
+// Evaluation of the N_pe position vectors (walks, argmin, max-log LLRs):
+// host-side dispatch.  The kernels are in detect_impl.cuh and are instantiated
+// in detect_f32.cu and detect_f16.cu.
+#include "detect_impl.cuh"
 
 namespace mpnl {
-namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int kTopList = 64;  // entries of the first-level neighbour list
-constexpr int kList2 = 128;   // per symbol: entries of all second-level lists together
-
-// --------------------------------------------------------------------------
-// ranking
-// --------------------------------------------------------------------------
-
-// Nearest grid index along one axis by rounding (an exact midpoint goes to
-// the smaller axis label); returns the index, writes the squared distance and
-// the grid coordinate.  Round-half-even is corrected only on the rare exact
-// midpoint (|u - rint(u)| == 0.5, where u - 0.5 is the floor exactly).
-template <int QAM>
-__device__ __forceinline__ int axis_round(float x, float &d, float &pos)
+size_t detect_smem_bytes(int nt, int qam, int n_pe, int n_sym)
 {
-    constexpr int L = Qam<QAM>::L;
-    const float u = fmaf(x, 0.5f * Qam<QAM>::kScale, 0.5f * (float)(L - 1));
-    float fr = rintf(u);
-    if (fabsf(u - fr) == 0.5f) {
-        const float fl = u - 0.5f;
-        if (fl >= 0.f && fl < (float)(L - 1)) {
-            const int a = (int)fl;
-            fr = Qam<QAM>::axis_label(a) < Qam<QAM>::axis_label(a + 1) ? fl : fl + 1.f;
-        }
-    }
-    fr = fminf(fmaxf(fr, 0.f), (float)(L - 1));
-    pos = fmaf(fr, 2.f * Qam<QAM>::kInvScale, -(float)(L - 1) * Qam<QAM>::kInvScale);
-    const float df = x - pos;
-    d = df * df;
-    return (int)fr;
+    const int NT = nt <= 4 ? 4 : (nt <= 8 ? 8 : 16);
+    const int B = qam == 4 ? 2 : (qam == 16 ? 4 : 6);
+    return det_layout(NT, B, n_pe, n_sym, (NT * B + 31) / 32).bytes;
 }
-
-template <int QAM>
-__device__ __forceinline__ int axis_round(float x, float &d)
-{
-    float pos;
-    return axis_round<QAM>(x, d, pos);
-}
-
-// The next grid index after i0 in distance order along an axis (one step
-// towards x, or away when the constellation ends there).
-template <int QAM>
-__device__ __forceinline__ int axis_next(float x, int i0)
-{
-    constexpr int L = Qam<QAM>::L;
-    const int s = x >= axis_pos<QAM>(i0) ? 1 : -1;
-    const int n = i0 + s;
-    return (n >= 0 && n < L) ? n : i0 - s;
-}
-
-// Grid indices of one axis in order of distance to x: the nearest index i0,
-// then alternately one step towards x and one step away, until one side runs
-// out, then the rest of the longer side.  (For x within half a spacing of
-// grid point i0 the distances grow as f, 2 - f, 2 + f, 4 - f, ... in
-// half-spacing units, f <= 1, so the zig-zag is the sorted order.)
-template <int QAM>
-struct AxisOrder {
-    int i0, s, m, lon;
-    __device__ __forceinline__ AxisOrder(float x, int nearest)
-    {
-        constexpr int L = Qam<QAM>::L;
-        i0 = nearest;
-        s = (x >= axis_pos<QAM>(i0)) ? 1 : -1;
-        const int a = s > 0 ? L - 1 - i0 : i0;  // room on the near side
-        const int c = L - 1 - a;                  // room on the far side
-        m = a < c ? a : c;
-        lon = a > c ? s : -s;                     // direction of the longer side
-    }
-    __device__ __forceinline__ int idx(int n) const
-    {
-        if (n <= 2 * m) {
-            const int k = (n + 1) >> 1;
-            return (n & 1) ? i0 + s * k : i0 - s * k;
-        }
-        return i0 + lon * (n - m);
-    }
-};
-
-template <int QAM>
-__device__ __forceinline__ int grid_label(int ire, int iim)
-{
-    return join_label<QAM>(Qam<QAM>::axis_label(ire), Qam<QAM>::axis_label(iim));
-}
-
-// Coordinates of a label (inverse of grid_label).
-template <int QAM>
-__device__ __forceinline__ float2 label_point(int lab)
-{
-    constexpr int H = Qam<QAM>::B / 2;
-    constexpr int L = Qam<QAM>::L;
-    int lre = 0, lim = 0;
-#pragma unroll
-    for (int t = 0; t < H; ++t) {
-        lre = (lre << 1) | ((lab >> (2 * (H - 1 - t) + 1)) & 1);
-        lim = (lim << 1) | ((lab >> (2 * (H - 1 - t))) & 1);
-    }
-    int ire = 0, iim = 0;
-#pragma unroll
-    for (int i = 0; i < L; ++i) {
-        if (Qam<QAM>::axis_label(i) == lre) ire = i;
-        if (Qam<QAM>::axis_label(i) == lim) iim = i;
-    }
-    return make_float2(axis_pos<QAM>(ire), axis_pos<QAM>(iim));
-}
-
-// p-th closest point (p >= 3) by (squared distance, label): the 2-D order is
-// enumerated over the "staircase" of (row a, column c) pairs of the two axis
-// orders: popping (a, c) exposes (a, c + 1), popping (a, 0) also exposes
-// (a + 1, 0); every pair's predecessor sorts no later, so p pops reach the
-// p-th point.  The per-row column pointers are packed 4 bits each.
-// Writes the grid indices, returns the squared distance.
-template <int QAM>
-__device__ __noinline__ float kth_point_slow(float bx, float by, int p, int ire, int iim,
-                                             int &oi, int &oj)
-{
-    constexpr int L = Qam<QAM>::L;
-    const AxisOrder<QAM> ore(bx, ire), oim(by, iim);
-    unsigned cols = 0;
-    int na = 1;
-    int ba = 0, bi = ire, bj = iim;
-    float bd = 0.f;
-    for (int pop = 1; pop <= QAM; ++pop) {
-        ba = -1;
-        bd = INFINITY;
-        int blab = 0;
-        for (int a = 0; a < na; ++a) {
-            const int c = (cols >> (4 * a)) & 0xF;
-            if (c >= L) continue;
-            const int ia = ore.idx(a), ic = oim.idx(c);
-            const float dx = bx - axis_pos<QAM>(ia), dy = by - axis_pos<QAM>(ic);
-            const float v = dx * dx + dy * dy;
-            bool take = ba < 0 || v < bd;  // ba < 0 takes the first candidate (NaN-safe)
-            if (!take && v == bd) {        // exact tie: lower label first
-                if (blab < 0) blab = grid_label<QAM>(bi, bj);
-                take = grid_label<QAM>(ia, ic) < blab;
-            }
-            if (take) {
-                ba = a;
-                bi = ia;
-                bj = ic;
-                bd = v;
-                blab = -1;
-            }
-        }
-        if (pop >= p) break;
-        const int bc = (cols >> (4 * ba)) & 0xF;
-        if (bc == 0 && ba == na - 1 && na < L) ++na;
-        cols += 1u << (4 * ba);
-    }
-    oi = bi;
-    oj = bj;
-    return bd;
-}
-
-// The first detected level sees the same b = z_{nt-1} / R for every row, so
-// its ordered neighbour list is built once per symbol by one warp: lane j
-// holds points j and j + 32; a point's rank is the number of points before it
-// in (distance, label) order.  Entry r: (x, y, distance, label).
-template <int QAM>
-__device__ __forceinline__ void top_list(float bx, float by, int kmax, float4 *list)
-{
-    constexpr int M = QAM;
-    constexpr int PER = (M + 31) / 32;
-    const int lane = threadIdx.x & 31;
-    float dq[PER], xq[PER], yq[PER];
-    int lq[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int q = lane + 32 * k;  // q = grid index: iy * L + ix
-        const int ix = q % Qam<QAM>::L, iy = q / Qam<QAM>::L;
-        xq[k] = axis_pos<QAM>(ix);
-        yq[k] = axis_pos<QAM>(iy);
-        const float dx = bx - xq[k], dy = by - yq[k];
-        dq[k] = q < M ? dx * dx + dy * dy : INFINITY;
-        lq[k] = q < M ? grid_label<QAM>(ix, iy) : 0x7fffffff;
-    }
-    int rank[PER];
-#pragma unroll
-    for (int k = 0; k < PER; ++k) rank[k] = 0;
-    for (int j = 0; j < 32; ++j) {
-#pragma unroll
-        for (int kk = 0; kk < PER; ++kk) {
-            const float dj = __shfl_sync(0xffffffffu, dq[kk], j);
-            const int lj = __shfl_sync(0xffffffffu, lq[kk], j);
-#pragma unroll
-            for (int k = 0; k < PER; ++k)
-                rank[k] += (dj < dq[k] || (dj == dq[k] && lj < lq[k])) ? 1 : 0;
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < PER; ++k) {
-        const int q = lane + 32 * k;
-        if (q < M && rank[k] < kmax)
-            list[rank[k]] = make_float4(xq[k], yq[k], dq[k], __int_as_float(lq[k]));
-    }
-}
-
-// The len nearest points to b in order, by one thread: the staircase
-// enumeration of kth_point_slow, emitting every pop.  Entry r: (x, y,
-// distance, label).
-template <int QAM>
-__device__ __forceinline__ void nearest_list(float bx, float by, int len, float4 *out)
-{
-    constexpr int L = Qam<QAM>::L;
-    float d0;
-    const int ire = axis_round<QAM>(bx, d0);
-    const int iim = axis_round<QAM>(by, d0);
-    const AxisOrder<QAM> ore(bx, ire), oim(by, iim);
-    unsigned cols = 0;
-    int na = 1;
-    for (int pop = 0; pop < len; ++pop) {
-        int ba = -1, bi = 0, bj = 0, blab = 0;
-        float bd = INFINITY;
-        for (int a = 0; a < na; ++a) {
-            const int c = (cols >> (4 * a)) & 0xF;
-            if (c >= L) continue;
-            const int ia = ore.idx(a), ic = oim.idx(c);
-            const float dx = bx - axis_pos<QAM>(ia), dy = by - axis_pos<QAM>(ic);
-            const float v = dx * dx + dy * dy;
-            const int lv = grid_label<QAM>(ia, ic);
-            if (ba < 0 || v < bd || (v == bd && lv < blab)) {
-                ba = a;
-                bi = ia;
-                bj = ic;
-                bd = v;
-                blab = lv;
-            }
-        }
-        out[pop] = make_float4(axis_pos<QAM>(bi), axis_pos<QAM>(bj), bd, __int_as_float(blab));
-        const int bc = (cols >> (4 * ba)) & 0xF;
-        if (bc == 0 && ba == na - 1 && na < L) ++na;
-        cols += 1u << (4 * ba);
-    }
-}
-
-// --------------------------------------------------------------------------
-// per-walk state helpers
-// --------------------------------------------------------------------------
-
-// Labels of the NT levels of one walk, B bits each, packed contiguously:
-// level l occupies bits [B l, B l + B) of the WORDS-word integer.  The walk
-// visits levels nt-1 .. 0 and pushes each label in at the bottom, so no
-// register is ever indexed by the (run-time) level.
-template <int NT, int B>
-struct Labels {
-    static constexpr int WORDS = (NT * B + 31) / 32;
-    uint32_t w[WORDS];
-    __device__ __forceinline__ void clear()
-    {
-#pragma unroll
-        for (int k = 0; k < WORDS; ++k) w[k] = 0;
-    }
-    __device__ __forceinline__ void push(int lab)
-    {
-#pragma unroll
-        for (int k = WORDS - 1; k > 0; --k) w[k] = __funnelshift_l(w[k - 1], w[k], B);
-        w[0] = (w[0] << B) | (uint32_t)lab;
-    }
-    // level l (a compile-time constant after unrolling)
-    __device__ __forceinline__ int get(int l) const
-    {
-        const int bit = B * l, k = bit >> 5, off = bit & 31;
-        uint32_t v = w[k] >> off;
-        if (off + B > 32 && k + 1 < WORDS) v |= w[k + 1] << (32 - off);
-        return (int)(v & ((1u << B) - 1));
-    }
-};
-
-// Level l's label from packed words in memory (run-time l).
-template <int B>
-__device__ __forceinline__ int label_at(const uint32_t *w, int l)
-{
-    const int bit = B * l, k = bit >> 5, off = bit & 31;
-    uint32_t v = w[k] >> off;
-    if (off + B > 32) v |= w[k + 1] << (32 - off);
-    return (int)(v & ((1u << B) - 1));
-}
-
-__host__ __device__ inline int a16(int o) { return (o + 15) & ~15; }
-__host__ __device__ inline int pow2_at_least(int n)
-{
-    int p = 1;
-    while (p < n) p <<= 1;
-    return p;
-}
-
-struct DetSmem {
-    int off_rc, off_r2, off_invd, off_perm, off_z, off_tab, off_order, off_m, off_best, off_wmin,
-        off_second, off_blab, off_top, off_l2, off_lut, off_rh, off_key2, off_blab2, bytes;
-};
-
-__host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym, int WORDS)
-{
-    const int chunks = (n_pe + 31) / 32;
-    const int np2 = pow2_at_least(chunks * 32);
-    DetSmem s;
-    int o = 0;
-    s.off_rc = o;
-    o = a16(o + NT * NT * 8);
-    s.off_r2 = o;
-    o = a16(o + NT * 4);
-    s.off_invd = o;
-    o = a16(o + NT * 4);
-    s.off_perm = o;
-    o = a16(o + NT * 4);
-    s.off_z = o;
-    o = a16(o + (n_sym + 1) * NT * 8);
-    s.off_tab = o;
-    o = a16(o + chunks * 32 * NT);
-    s.off_order = o;
-    o = a16(o + np2 * 4);
-    s.off_m = o;
-    o = a16(o + n_sym * NT * B * 2 * 4);
-    s.off_best = o;
-    o = a16(o + n_sym * 8);
-    s.off_wmin = o;
-    o = a16(o + n_sym * chunks * 4);
-    s.off_second = o;
-    o = a16(o + n_sym * chunks * 4);
-    s.off_blab = o;
-    o = a16(o + n_sym * chunks * WORDS * 4);
-    s.off_top = o;
-    o = a16(o + (n_sym + 1) * kTopList * 16);
-    s.off_l2 = o;
-    o = a16(o + (n_sym + 1) * kList2 * 16);
-    s.off_lut = o;  // 2-D label of grid point (ire, iim) at ire * 8 + iim
-    o = a16(o + 64);
-    // mixed precision only: R columns as half2 pairs, runner-up key and labels
-    s.off_rh = o;
-    o = a16(o + NT * NT * 8);
-    s.off_key2 = o;
-    o = a16(o + n_sym * chunks * 8);
-    s.off_blab2 = o;
-    o = a16(o + n_sym * chunks * WORDS * 4);
-    s.bytes = o;
-    return s;
-}
-
-// In-warp transpose of a 32 x 32 bit matrix: lane p holds row p on entry
-// and column p on return (bit q of the result = bit p of lane q's row).
-// Five butterfly stages exchange ever smaller blocks with the partner lane.
-__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x)
-{
-    const int lane = threadIdx.x & 31;
-    const uint32_t masks[5] = {0x0000ffffu, 0x00ff00ffu, 0x0f0f0f0fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-        const int j = 16 >> t;
-        const uint32_t m = masks[t];
-        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
-        x = (lane & j) ? (((y >> j) & m) | (x & ~m)) : ((x & m) | ((y & m) << j));
-    }
-    return x;
-}
-
-// Warp-level results of one symbol for the 32 walks a warp just finished.
-//
-// The 32 keys (PED bits, table row, sorted position) are sorted across the
-// warp (bitonic, over shuffles).  Position 0 is the warp's best walk,
-// position 1 its runner-up.  For the LLRs, X = label bits XOR the best
-// walk's label bits marks, per (level, bit), the walks on the other side of
-// the best walk's bit.  With X laid out by sorted position, a bit transpose
-// gives lane t, for packed bit j = 32 k + t, the set of positions that have
-// bit j; the first of them has the smallest PED, which is the other side's
-// warp minimum.  So every (level, bit) costs one shared atomicMin per side,
-// on addresses distinct across lanes.
-template <int NT, int B>
-__device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int row, int chunk,
-                                                   int chunks, int nt, float d,
-                                                   const Labels<NT, B> &lab, int s,
-                                                   unsigned long long *sBest, unsigned *sWmin,
-                                                   unsigned *sSecond, uint32_t *sBlab,
-                                                   unsigned *sM, bool want_llr,
-                                                   unsigned long long *sKey2 = nullptr,
-                                                   uint32_t *sBlab2 = nullptr)
-{
-    using Lab = Labels<NT, B>;
-    constexpr int WORDS = Lab::WORDS;
-    constexpr unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const unsigned db = active ? fbits(d) : kInfBits;
-    // key: PED bits, table row (the tie-break), then the sorted position
-    unsigned long long key =
-        active ? (((unsigned long long)db << 32) | ((unsigned)row << 16) | (unsigned)(chunk * 32 + lane))
-               : ~0ull;
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(FULL, key, j);
-            const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
-            key = keep_min ? (o < key ? o : key) : (o > key ? o : key);
-        }
-    }
-    const unsigned long long best = __shfl_sync(FULL, key, 0);
-    const unsigned long long runner = __shfl_sync(FULL, key, 1);
-    const int blane = (int)(best & 31u);  // lane of the warp's best row
-    const unsigned wmin = (unsigned)(best >> 32);
-    const unsigned second = (unsigned)(runner >> 32);
-    Lab bl;
-#pragma unroll
-    for (int k = 0; k < WORDS; ++k) bl.w[k] = __shfl_sync(FULL, lab.w[k], blane);
-    if (sKey2 != nullptr) {
-        // the warp's runner-up row (key and labels), for the FP32 re-check
-        const int rlane = (int)(runner & 31u);
-        uint32_t rw[WORDS];
-#pragma unroll
-        for (int k = 0; k < WORDS; ++k) rw[k] = __shfl_sync(FULL, lab.w[k], rlane);
-        if (valid && lane == 0) {
-            sKey2[s * chunks + chunk] = runner;
-#pragma unroll
-            for (int k = 0; k < WORDS; ++k) sBlab2[(s * chunks + chunk) * WORDS + k] = rw[k];
-        }
-    }
-    if (!valid) return;  // (warp-uniform) second symbol slot beyond n_sym
-    if (lane == 0) {
-        atomicMin(&sBest[s], best);
-        sWmin[s * chunks + chunk] = wmin;
-        sSecond[s * chunks + chunk] = second;
-#pragma unroll
-        for (int k = 0; k < WORDS; ++k) sBlab[(s * chunks + chunk) * WORDS + k] = bl.w[k];
-    }
-    if (!want_llr) return;
-    const int src = (int)(key & 31u);  // original lane of this sorted position
-    const bool real = key != ~0ull;
-    const unsigned dp = (unsigned)(key >> 32);
-#pragma unroll
-    for (int k = 0; k < WORDS; ++k) {
-        const uint32_t xm = lab.w[k] ^ bl.w[k];
-        const uint32_t xs = __shfl_sync(FULL, xm, src);
-        const uint32_t col = warp_transpose32(real ? xs : 0u);  // positions having bit 32 k + lane
-        const int owner = col ? __ffs(col) - 1 : 0;
-        const unsigned dmin = __shfl_sync(FULL, dp, owner);
-        const int j = 32 * k + lane;  // packed bit: level j / B, bit (j % B) from the LSB
-        if (j < nt * B) {
-            const int l = j / B, bpos = j - l * B;
-            const int bb = (bl.w[k] >> lane) & 1;  // the best row's bit
-            unsigned *mm = sM + (s * NT * B + l * B + (B - 1 - bpos)) * 2;
-            atomicMin(mm + bb, wmin);
-            if (col) atomicMin(mm + (1 - bb), dmin);
-        }
-    }
-}
-
-// Interference cancellation fused with the shift of the residual register
-// file after level l is decided: e'[i] = e[i+1] - R_{l-1-i, l} s for i < W
-// (W >= l; col = the staged column l of R, bottom-up, two entries per 16-byte
-// broadcast load serving both symbols).  e'[i] for i >= W is not needed.
-template <int W, int NT>
-__device__ __forceinline__ void cancel_shift(float (&ex)[2][NT], float (&ey)[2][NT],
-                                             const float2 *col, const float (&sx)[2],
-                                             const float (&sy)[2])
-{
-    static_assert(W < NT, "the shift reads entry W");
-    const float4 *c4 = reinterpret_cast<const float4 *>(col);
-#pragma unroll
-    for (int i2 = 0; i2 < (W + 1) / 2; ++i2) {
-        const float4 r = c4[i2];
-        const int i = 2 * i2;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            ex[k][i] = fmaf(-r.x, sx[k], fmaf(r.y, sy[k], ex[k][i + 1]));
-            ey[k][i] = fmaf(-r.x, sy[k], fmaf(-r.y, sx[k], ey[k][i + 1]));
-            if (i + 1 < W) {
-                ex[k][i + 1] = fmaf(-r.z, sx[k], fmaf(r.w, sy[k], ex[k][i + 2]));
-                ey[k][i + 1] = fmaf(-r.z, sy[k], fmaf(-r.w, sx[k], ey[k][i + 2]));
-            }
-        }
-    }
-}
-
-// half2 variant: e + (-Re,-Re)*(sx,sy) + (Im,-Im)*(sy,sx) per complex term.
-template <int W, int NT>
-__device__ __forceinline__ void cancel_shift_h(__half2 (&eh)[2][NT], const uint2 *colh,
-                                               const __half2 (&sh)[2], const __half2 (&sw)[2])
-{
-    static_assert(W < NT, "the shift reads entry W");
-    const uint4 *c4 = reinterpret_cast<const uint4 *>(colh);
-#pragma unroll
-    for (int i2 = 0; i2 < (W + 1) / 2; ++i2) {
-        const uint4 r = c4[i2];
-        const __half2 a0 = *reinterpret_cast<const __half2 *>(&r.x);
-        const __half2 b0 = *reinterpret_cast<const __half2 *>(&r.y);
-        const __half2 a1 = *reinterpret_cast<const __half2 *>(&r.z);
-        const __half2 b1 = *reinterpret_cast<const __half2 *>(&r.w);
-        const int i = 2 * i2;
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            eh[k][i] = __hfma2(b0, sw[k], __hfma2(a0, sh[k], eh[k][i + 1]));
-            if (i + 1 < W) eh[k][i + 1] = __hfma2(b1, sw[k], __hfma2(a1, sh[k], eh[k][i + 2]));
-        }
-    }
-}
-
-// Width dispatch: levels are grouped four at a time so that a level pays for
-// at most three unused terms (widths 15, 11, 7, 3 for NT = 16); level 0
-// needs no cancellation.  l is warp-uniform, so the branches do not diverge.
-template <int NT>
-__device__ __forceinline__ void cancel_level(int l, float (&ex)[2][NT], float (&ey)[2][NT],
-                                             const float2 *col, const float (&sx)[2],
-                                             const float (&sy)[2])
-{
-    if constexpr (NT == 16) {
-        if (l > 11) cancel_shift<15>(ex, ey, col, sx, sy);
-        else if (l > 7) cancel_shift<11>(ex, ey, col, sx, sy);
-        else if (l > 3) cancel_shift<7>(ex, ey, col, sx, sy);
-        else if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
-    } else if constexpr (NT == 8) {
-        if (l > 3) cancel_shift<7>(ex, ey, col, sx, sy);
-        else if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
-    } else {
-        if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
-    }
-}
-
-template <int NT>
-__device__ __forceinline__ void cancel_level_h(int l, __half2 (&eh)[2][NT], const uint2 *colh,
-                                               const __half2 (&sh)[2], const __half2 (&sw)[2])
-{
-    if constexpr (NT == 16) {
-        if (l > 11) cancel_shift_h<15>(eh, colh, sh, sw);
-        else if (l > 7) cancel_shift_h<11>(eh, colh, sh, sw);
-        else if (l > 3) cancel_shift_h<7>(eh, colh, sh, sw);
-        else if (l > 0) cancel_shift_h<3>(eh, colh, sh, sw);
-    } else if constexpr (NT == 8) {
-        if (l > 3) cancel_shift_h<7>(eh, colh, sh, sw);
-        else if (l > 0) cancel_shift_h<3>(eh, colh, sh, sw);
-    } else {
-        if (l > 0) cancel_shift_h<3>(eh, colh, sh, sw);
-    }
-}
-
-// F16: the interference-cancelled residuals e are kept as half2 (re, im) and
-// updated with two HFMA2 per complex term; b, the ranking and the PED stay in
-// FP32, and the final best and runner-up paths are re-checked in FP32.
-template <int NT, int QAM, bool F16>
-__global__ void __launch_bounds__(kThreads, 2)
-detect_walk_kernel(int n_sym, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
-                   const float *__restrict__ inv_diag, const uint8_t *__restrict__ perm,
-                   const uint8_t *__restrict__ paths, const float2 *__restrict__ Z,
-                   uint8_t *__restrict__ hard, float *__restrict__ llr, float *__restrict__ ped2,
-                   unsigned *__restrict__ status)
-{
-    constexpr int B = Qam<QAM>::B;
-    constexpr int L = Qam<QAM>::L;
-    using Lab = Labels<NT, B>;
-    constexpr int WORDS = Lab::WORDS;
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int chunks = (n_pe + 31) / 32;
-    const int nrows = chunks * 32;
-    const int np2 = pow2_at_least(nrows);
-    const DetSmem S = det_layout(NT, B, n_pe, n_sym, WORDS);
-    // sRr[l*NT + i] = R_{l-1-i, l} for i < l (column l of R above the
-    // diagonal, bottom-up: the order the shift-register walk consumes it)
-    float2 *sRr = reinterpret_cast<float2 *>(smem + S.off_rc);
-    float *sR2 = reinterpret_cast<float *>(smem + S.off_r2);
-    float *sInvd = reinterpret_cast<float *>(smem + S.off_invd);
-    int *sPerm = reinterpret_cast<int *>(smem + S.off_perm);
-    float2 *sZ = reinterpret_cast<float2 *>(smem + S.off_z);
-    uint8_t *sTab = smem + S.off_tab;
-    unsigned *sOrder = reinterpret_cast<unsigned *>(smem + S.off_order);
-    unsigned *sM = reinterpret_cast<unsigned *>(smem + S.off_m);
-    unsigned long long *sBest = reinterpret_cast<unsigned long long *>(smem + S.off_best);
-    unsigned *sWmin = reinterpret_cast<unsigned *>(smem + S.off_wmin);
-    unsigned *sSecond = reinterpret_cast<unsigned *>(smem + S.off_second);
-    uint32_t *sBlab = reinterpret_cast<uint32_t *>(smem + S.off_blab);
-    float4 *sTop = reinterpret_cast<float4 *>(smem + S.off_top);
-    float4 *sL2 = reinterpret_cast<float4 *>(smem + S.off_l2);
-    __shared__ int s_k1[QAM + 1], s_off1[QAM + 1];
-    __shared__ int s_use2;
-    uint8_t *sLut = smem + S.off_lut;
-    uint2 *sRh = reinterpret_cast<uint2 *>(smem + S.off_rh);  // sRr as {(-Re,-Re), (Im,-Im)} half2
-    unsigned long long *sKey2 = reinterpret_cast<unsigned long long *>(smem + S.off_key2);
-    uint32_t *sBlab2 = reinterpret_cast<uint32_t *>(smem + S.off_blab2);
-    __shared__ int s_kmax;
-
-    const int sc = blockIdx.x;
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-
-    // ---- stage the subcarrier
-    const int P = nt * (nt + 1) / 2;
-    const float2 *gR = Rp + (size_t)sc * P;
-    for (int k = tid; k < NT * NT; k += kThreads) {
-        const int l = k / NT, i = k - l * NT;
-        float2 v = make_float2(0.f, 0.f);  // entries i >= l feed only stale registers
-        if (l < nt && i < l) {
-            const int r = l - 1 - i;  // R_{r,l}: packed row r starts at r nt - r(r-1)/2
-            v = gR[r * nt - (r * (r - 1)) / 2 + (l - r)];
-        }
-        sRr[k] = v;
-        if constexpr (F16) {
-            const __half2 a = __floats2half2_rn(-v.x, -v.x), b = __floats2half2_rn(v.y, -v.y);
-            sRh[k] = make_uint2(*reinterpret_cast<const unsigned *>(&a),
-                                *reinterpret_cast<const unsigned *>(&b));
-        }
-    }
-    for (int l = tid; l < nt; l += kThreads) {
-        const float2 v = gR[l * nt - (l * (l - 1)) / 2];
-        sR2[l] = v.x * v.x;
-    }
-    for (int k = tid; k < NT; k += kThreads) {
-        if (k < nt) {
-            sInvd[k] = inv_diag[(size_t)sc * nt + k];
-            sPerm[k] = perm[(size_t)sc * nt + k];
-        }
-    }
-    for (int k = tid; k < (n_sym + 1) * NT; k += kThreads) {
-        const int s = k / NT, l = k - s * NT;
-        sZ[k] = (s < n_sym && l < nt) ? Z[((size_t)sc * n_sym + s) * nt + l] : make_float2(0.f, 0.f);
-    }
-    if (tid < L * 8) {
-        const int ire = tid >> 3, iim = tid & 7;
-        sLut[tid] = (uint8_t)(iim < L ? grid_label<QAM>(ire, iim) : 0);
-    }
-    if (tid == 0) s_kmax = 1;
-    for (int k = tid; k <= QAM; k += kThreads) s_k1[k] = 0;
-    __syncthreads();
-    // table, clamped; the sort key of a row: how far it deviates from rank 1
-    // below the two list-served levels (largest rank, then rank sum), then
-    // the row.  Also: the largest first-level rank, and per first-level rank
-    // the largest second-level rank (the lengths of the second-level lists).
-    int kmax = 1;
-    for (int r = tid; r < np2; r += kThreads) {
-        unsigned key = 0xffffffffu;
-        if (r < nrows) {
-            int mx = 1, sum = 0, top = 1, second = 1;
-            for (int l = 0; l < NT; ++l) {
-                int v = 1;  // padding rows and levels: rank 1
-                if (r < n_pe && l < nt) {
-                    v = paths[((size_t)sc * n_pe + r) * nt + l];
-                    if (v < 1 || v > QAM) {
-                        atomicOr(status, kStatusBadPathEntry);
-                        v = v < 1 ? 1 : QAM;
-                    }
-                    if (l == nt - 1) {
-                        kmax = max(kmax, v);
-                        top = v;
-                    } else if (l == nt - 2) {
-                        second = v;
-                    } else {
-                        mx = max(mx, v);
-                        sum += v - 1;
-                    }
-                }
-                sTab[r * NT + l] = (uint8_t)v;
-            }
-            if (r < n_pe && nt >= 2) atomicMax(&s_k1[top], second);
-            key = r < n_pe ? ((unsigned)min(mx, 255) << 24) | ((unsigned)min(sum, 4095) << 12) |
-                                 (unsigned)r
-                           : (0xfffu << 20) | (unsigned)r;
-        }
-        sOrder[r] = key;
-    }
-    atomicMax(&s_kmax, kmax);
-    for (int k = tid; k < n_sym * NT * B * 2; k += kThreads) sM[k] = kInfBits;
-    for (int k = tid; k < n_sym; k += kThreads) sBest[k] = ~0ull;
-    __syncthreads();
-    // bitonic sort of the row keys
-    for (int k = 2; k <= np2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < np2; i += kThreads) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned a = sOrder[i], b = sOrder[ixj];
-                    if ((a > b) == ((i & k) == 0)) {
-                        sOrder[i] = b;
-                        sOrder[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // ordered neighbours of b = z_{nt-1} / R_{nt-1,nt-1}, one warp per symbol
-    {
-        const int kmx = s_kmax;
-        const float iv = sInvd[nt - 1];
-        for (int s = warp; s <= n_sym; s += kWarps) {
-            const float2 z = sZ[s * NT + nt - 1];
-            top_list<QAM>(z.x * iv, z.y * iv, kmx, sTop + s * kTopList);
-        }
-        if (tid == 0) {  // offsets of the second-level lists (one per first-level rank)
-            int o = 0;
-            for (int a = 1; a <= kmx; ++a) {
-                s_off1[a] = o;
-                o += s_k1[a];
-            }
-            s_use2 = nt >= 2 && o <= kList2;
-        }
-    }
-    __syncthreads();
-    // Second level: rows that took the same first-level rank a see the same
-    // b = (z_{nt-2} - R_{nt-2,nt-1} s(a)) / R_{nt-2,nt-2}, so one ordered list
-    // per (symbol, a) serves them all -- as long as the lists fit.
-    if (s_use2) {
-        const int kmx = s_kmax;
-        const int l = nt - 2;
-        const float iv = sInvd[l];
-        const float2 r = sRr[(nt - 1) * NT];  // R_{nt-2, nt-1}
-        for (int it = tid; it < (n_sym + 1) * kmx; it += kThreads) {  // one thread per list
-            const int s = it / kmx, a = 1 + it - s * kmx;
-            const int len = s_k1[a];
-            if (len == 0) continue;
-            const float4 q = sTop[s * kTopList + a - 1];
-            const float2 z = sZ[s * NT + l];
-            const float ex = z.x - (r.x * q.x - r.y * q.y);
-            const float ey = z.y - (r.x * q.y + r.y * q.x);
-            nearest_list<QAM>(ex * iv, ey * iv, len, sL2 + s * kList2 + s_off1[a]);
-        }
-        __syncthreads();
-    }
-    const bool use2 = s_use2 != 0;
-
-    // ---- walks: warp item = (chunk of 32 rows, pair of symbols)
-    const int pairs = (n_sym + 1) >> 1;
-    const int l_list = use2 ? nt - 2 : nt - 1;  // levels >= l_list are list-served
-    for (int item = warp; item < chunks * pairs; item += kWarps) {
-        const int chunk = item / pairs, s0 = 2 * (item - chunk * pairs);
-        const bool has1 = s0 + 1 < n_sym;
-        const int row = (int)(sOrder[chunk * 32 + lane] & 0xfffu);
-        const bool active = row < n_pe;
-        const uint8_t *trow = sTab + row * NT;
-        // shift register: when level l is decided, e[k][i] = e_{l-i} of
-        // symbol s0 + k; entries i > l are stale and never read
-        float ex[2][NT], ey[2][NT];
-        __half2 eh[2][NT];
-#pragma unroll
-        for (int i = 0; i < NT; ++i) {
-            const int lz = nt - 1 - i;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const float2 z = lz >= 0 ? sZ[(s0 + k) * NT + lz] : make_float2(0.f, 0.f);
-                if constexpr (F16) {
-                    eh[k][i] = __floats2half2_rn(z.x, z.y);
-                } else {
-                    ex[k][i] = z.x;
-                    ey[k][i] = z.y;
-                }
-            }
-        }
-        Lab lab[2];
-        lab[0].clear();
-        lab[1].clear();
-        float d[2] = {0.f, 0.f};
-        int p_top = 1;
-#pragma unroll 1
-        for (int l = nt - 1; l >= 0; --l) {
-            const int p = trow[l];
-            float sx[2], sy[2], dist[2];
-            int lb[2];
-            if (l >= l_list) {  // list-served levels (warp-uniform branch)
-                const float4 *lst;
-                int stride;
-                if (l == nt - 1) {
-                    p_top = p;
-                    lst = sTop + s0 * kTopList + p - 1;
-                    stride = kTopList;
-                } else {
-                    lst = sL2 + s0 * kList2 + s_off1[p_top] + p - 1;
-                    stride = kList2;
-                }
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    const float4 q = lst[k * stride];
-                    sx[k] = q.x;
-                    sy[k] = q.y;
-                    dist[k] = q.z;
-                    lb[k] = __float_as_int(q.w);
-                }
-            } else {
-                const float iv = sInvd[l];
-                int ire[2], iim[2];
-                float dre[2], dim[2];
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    float bx, by;
-                    if constexpr (F16) {
-                        const float2 f = __half22float2(eh[k][0]);
-                        bx = f.x * iv;
-                        by = f.y * iv;
-                    } else {
-                        bx = ex[k][0] * iv;
-                        by = ey[k][0] * iv;
-                    }
-                    ire[k] = axis_round<QAM>(bx, dre[k], sx[k]);
-                    iim[k] = axis_round<QAM>(by, dim[k], sy[k]);
-                    if (p == 2) {
-                        // second nearest: the next point along one axis
-                        const int nre = axis_next<QAM>(bx, ire[k]);
-                        const int nim = axis_next<QAM>(by, iim[k]);
-                        float a = bx - axis_pos<QAM>(nre), c = by - axis_pos<QAM>(nim);
-                        const float d_re = a * a + dim[k];  // (nre, iim)
-                        const float d_im = dre[k] + c * c;  // (ire, nim)
-                        bool take_re = d_re < d_im;
-                        if (d_re == d_im) take_re = sLut[nre * 8 + iim[k]] < sLut[ire[k] * 8 + nim];
-                        if (take_re) {
-                            ire[k] = nre;
-                            dre[k] = d_re;
-                            sx[k] = axis_pos<QAM>(nre);
-                        } else {
-                            iim[k] = nim;
-                            dre[k] = d_im;
-                            sy[k] = axis_pos<QAM>(nim);
-                        }
-                        dim[k] = 0.f;
-                    } else if (p > 2) {
-                        int oi, oj;
-                        dre[k] = kth_point_slow<QAM>(bx, by, p, ire[k], iim[k], oi, oj);
-                        dim[k] = 0.f;
-                        ire[k] = oi;
-                        iim[k] = oj;
-                        sx[k] = axis_pos<QAM>(oi);
-                        sy[k] = axis_pos<QAM>(oj);
-                    }
-                    dist[k] = dre[k] + dim[k];
-                    lb[k] = sLut[ire[k] * 8 + iim[k]];
-                }
-            }
-            const float r2 = sR2[l];
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                d[k] = fmaf(r2, dist[k], d[k]);
-                lab[k].push(lb[k]);
-            }
-            if constexpr (F16) {
-                __half2 sh[2], sw[2];
-#pragma unroll
-                for (int k = 0; k < 2; ++k) {
-                    sh[k] = __floats2half2_rn(sx[k], sy[k]);
-                    sw[k] = __floats2half2_rn(sy[k], sx[k]);
-                }
-                cancel_level_h<NT>(l, eh, sRh + l * NT, sh, sw);
-            } else {
-                cancel_level<NT>(l, ex, ey, sRr + l * NT, sx, sy);
-            }
-        }
-        warp_reduce_symbol<NT, B>(true, active, row, chunk, chunks, nt, d[0], lab[0], s0, sBest,
-                                  sWmin, sSecond, sBlab, sM, llr != nullptr,
-                                  F16 ? sKey2 : nullptr, sBlab2);
-        warp_reduce_symbol<NT, B>(has1, active, row, chunk, chunks, nt, d[1], lab[1], s0 + 1,
-                                  sBest, sWmin, sSecond, sBlab, sM, llr != nullptr,
-                                  F16 ? sKey2 : nullptr, sBlab2);
-    }
-    __syncthreads();
-
-    // ---- per-symbol results
-    for (int s = warp; s < n_sym; s += kWarps) {
-        const size_t det = (size_t)sc * n_sym + s;
-        const unsigned long long key = sBest[s];
-        const unsigned bd = (unsigned)(key >> 32);
-        int bc = (int)((key & 0xffffu) >> 5);  // chunk of the best row's sorted position
-        if (bc >= chunks) bc = 0;
-        if constexpr (F16) {
-            // runner-up: the best chunk's second row or another chunk's best
-            unsigned long long rk = ~0ull;
-            int rsrc = -1;  // >= 0: sBlab of chunk rsrc; -1: sBlab2 of chunk bc
-            for (int c = lane; c < chunks; c += 32) {
-                const unsigned long long kc = c == bc ? sKey2[s * chunks + c]
-                                                      : ((unsigned long long)sWmin[s * chunks + c] << 32);
-                if (kc < rk) {
-                    rk = kc;
-                    rsrc = c == bc ? -1 : c;
-                }
-            }
-            // warp min of (rk, rsrc): chunk keys of other chunks only carry the PED
-            // (their rows are unique per chunk), ties -> lower chunk
-            unsigned long long best_rk = rk;
-            int best_src = rsrc;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best_rk, o);
-                const int s2 = __shfl_xor_sync(0xffffffffu, best_src, o);
-                if (k2 < best_rk || (k2 == best_rk && s2 < best_src)) {
-                    best_rk = k2;
-                    best_src = s2;
-                }
-            }
-            // FP32 metrics ||z - R s||^2 of both paths: lane l owns row l of R
-            const uint32_t *w1 = sBlab + (s * chunks + bc) * WORDS;
-            const uint32_t *w2 = best_src < 0 ? sBlab2 + (s * chunks + bc) * WORDS
-                                              : sBlab + (s * chunks + best_src) * WORDS;
-            const bool have2 = best_rk != ~0ull;
-            float m1 = 0.f, m2 = 0.f;
-            if (lane < nt) {
-                const float2 z = sZ[s * NT + lane];
-                float t1x = z.x, t1y = z.y, t2x = z.x, t2y = z.y;
-                for (int j = lane; j < nt; ++j) {
-                    const float2 r =
-                        j == lane ? make_float2(sqrtf(sR2[j]), 0.f) : sRr[j * NT + (j - 1 - lane)];
-                    const int lb1 = label_at<B>(w1, j);
-                    const int lb2 = label_at<B>(w2, j);
-                    const float2 p1 = label_point<QAM>(lb1), p2 = label_point<QAM>(lb2);
-                    t1x -= r.x * p1.x - r.y * p1.y;
-                    t1y -= r.x * p1.y + r.y * p1.x;
-                    t2x -= r.x * p2.x - r.y * p2.y;
-                    t2y -= r.x * p2.y + r.y * p2.x;
-                }
-                m1 = t1x * t1x + t1y * t1y;
-                m2 = t2x * t2x + t2y * t2y;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-                m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-            }
-            if (!have2) m2 = INFINITY;
-            const bool swap = have2 && m2 < m1;
-            const uint32_t *wb = swap ? w2 : w1;
-            if (lane < nt) hard[det * nt + sPerm[lane]] = (uint8_t)label_at<B>(wb, lane);
-            if (ped2 != nullptr && lane == 0) {
-                ped2[det * 2] = fminf(m1, m2);
-                ped2[det * 2 + 1] = fmaxf(m1, m2);
-            }
-        } else {
-        if (lane < nt)
-            hard[det * nt + sPerm[lane]] = (uint8_t)label_at<B>(sBlab + (s * chunks + bc) * WORDS, lane);
-        if (ped2 != nullptr) {
-            unsigned sec = kInfBits;
-            for (int c = lane; c < chunks; c += 32)
-                sec = min(sec, c == bc ? sSecond[s * chunks + c] : sWmin[s * chunks + c]);
-            sec = __reduce_min_sync(0xffffffffu, sec);
-            if (lane == 0) {
-                ped2[det * 2] = __uint_as_float(bd);
-                ped2[det * 2 + 1] = __uint_as_float(sec);
-            }
-        }
-        }
-        if (llr != nullptr) {
-            for (int slot = lane; slot < nt * B; slot += 32) {
-                const int l = slot / B, b = slot - l * B;
-                const unsigned *mm = sM + (s * NT * B + slot) * 2;
-                float v;
-                if (mm[1] == kInfBits) v = kLlrMax;
-                else if (mm[0] == kInfBits) v = -kLlrMax;
-                else v = (__uint_as_float(mm[1]) - __uint_as_float(mm[0])) / sigma2;
-                llr[(det * nt + sPerm[l]) * B + b] = v;
-            }
-        }
-    }
-}
-
-template <int NT, int QAM, bool F16>
-cudaError_t launch_prec(int n_sc, int n_sym, int nt, int n_pe, float sigma2, const float2 *R,
-                        const float *inv_diag, const uint8_t *perm, const uint8_t *paths,
-                        const float2 *Z, uint8_t *hard, float *llr, float *ped2,
-                        unsigned *status, cudaStream_t stream)
-{
-    const DetSmem S = det_layout(NT, Qam<QAM>::B, n_pe, n_sym, Labels<NT, Qam<QAM>::B>::WORDS);
-    const size_t smem = S.bytes;
-    {
-        cudaError_t e = allow_dynamic_smem(detect_walk_kernel<NT, QAM, F16>, smem);
-        if (e != cudaSuccess) return e;
-    }
-    detect_walk_kernel<NT, QAM, F16><<<n_sc, kThreads, smem, stream>>>(
-        n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard, llr, ped2, status);
-    return cudaGetLastError();
-}
-
-template <int NT, int QAM>
-cudaError_t launch_tpl(int n_sc, int n_sym, int nt, int n_pe, float sigma2, const float2 *R,
-                       const float *inv_diag, const uint8_t *perm, const uint8_t *paths,
-                       const float2 *Z, uint8_t *hard, float *llr, float *ped2, unsigned *status,
-                       bool f16, cudaStream_t stream)
-{
-    return f16 ? launch_prec<NT, QAM, true>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm,
-                                            paths, Z, hard, llr, ped2, status, stream)
-               : launch_prec<NT, QAM, false>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm,
-                                             paths, Z, hard, llr, ped2, status, stream);
-}
-
-template <int NT>
-cudaError_t launch_nt(int qam, int n_sc, int n_sym, int nt, int n_pe, float sigma2,
-                      const float2 *R, const float *inv_diag, const uint8_t *perm,
-                      const uint8_t *paths, const float2 *Z, uint8_t *hard, float *llr,
-                      float *ped2, unsigned *status, bool f16, cudaStream_t stream)
-{
-    switch (qam) {
-    case 4:
-        return launch_tpl<NT, 4>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                                 llr, ped2, status, f16, stream);
-    case 16:
-        return launch_tpl<NT, 16>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                                  llr, ped2, status, f16, stream);
-    default:
-        return launch_tpl<NT, 64>(n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                                  llr, ped2, status, f16, stream);
-    }
-}
-
-}  // namespace
 
 cudaError_t launch_detect(int n_sc, int n_sym, int nt, int qam, int n_pe, float sigma2,
                           const float2 *R, const float *inv_diag, const uint8_t *perm,
                           const uint8_t *paths, const float2 *Z, uint8_t *hard, float *llr,
-                          float *ped2, unsigned *status, bool f16, cudaStream_t stream)
+                          float *ped2, unsigned *status, bool f16, int sym, cudaStream_t stream)
 {
     if (n_sc == 0) return cudaSuccess;
-    if (nt <= 4)
-        return launch_nt<4>(qam, n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                            llr, ped2, status, f16, stream);
-    if (nt <= 8)
-        return launch_nt<8>(qam, n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                            llr, ped2, status, f16, stream);
-    return launch_nt<16>(qam, n_sc, n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard,
-                         llr, ped2, status, f16, stream);
+    const DetArgs a{n_sym, nt, n_pe, sigma2, R, inv_diag, perm, paths, Z, hard, llr, ped2, status};
+    return f16 ? launch_detect_f16(n_sc, a, qam, sym, stream)
+               : launch_detect_f32(n_sc, a, qam, sym, stream);
 }
 
 }  // namespace mpnl

@@ -51,21 +51,23 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b)  // a * conj(b)
     return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
 }
 
+// One subcarrier by one warp, in the warp's shared-memory region at byte
+// offset base_off (at least mmse_smem_layout(nr, nt, n_sym).bytes).  Inlined
+// into the per-call and the batch kernels alike (no contraction).
 template <int NT, int QAM>
-__global__ void __launch_bounds__(kWarps * 32, 4)
-mmse_kernel(int n_sc, int n_sym, int nr, int nt, float sigma2, const float2 *__restrict__ H,
-            const float2 *__restrict__ Y, uint8_t *__restrict__ hard, float *__restrict__ llr)
+__device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, float sigma2,
+                                       const float2 *__restrict__ H,
+                                       const float2 *__restrict__ Y,
+                                       uint8_t *__restrict__ hard, float *__restrict__ llr,
+                                       int base_off)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + base_off;
     constexpr int B = Qam<QAM>::B;
     constexpr int HB = B / 2;
     constexpr int LQ = Qam<QAM>::L;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sc = blockIdx.x * kWarps + warp;
-    if (sc >= n_sc) return;  // warp-local work only
-
+    const int lane = threadIdx.x & 31;
     const MmseSmem S = mmse_smem_layout(nr, nt, n_sym);
-    unsigned char *base = smem_raw + warp * S.bytes;
     float2 *sH = reinterpret_cast<float2 *>(base + S.off_h);
     float2 *sY = reinterpret_cast<float2 *>(base + S.off_y);
     float2 *sL = reinterpret_cast<float2 *>(base + S.off_l);  // A, then its Cholesky factor
@@ -218,6 +220,53 @@ mmse_kernel(int n_sc, int n_sym, int nr, int nt, float sigma2, const float2 *__r
             }
         }
     }
+    __syncwarp();  // the region may be reused for the warp's next subcarrier
+}
+
+template <int NT, int QAM>
+__global__ void __launch_bounds__(kWarps * 32, 4)
+mmse_kernel(int n_sc, int n_sym, int nr, int nt, float sigma2, const float2 *__restrict__ H,
+            const float2 *__restrict__ Y, uint8_t *__restrict__ hard, float *__restrict__ llr)
+{
+    const int warp = threadIdx.x >> 5;
+    const int sc = blockIdx.x * kWarps + warp;
+    if (sc >= n_sc) return;  // warp-local work only
+    const MmseSmem S = mmse_smem_layout(nr, nt, n_sym);
+    mmse_warp<NT, QAM>(sc, n_sym, nr, nt, sigma2, H, Y, hard, llr, warp * S.bytes);
+}
+
+template <int NT>
+__device__ __forceinline__ void mmse_warp_qam(const BatchItem &it, int sc, int base)
+{
+    switch (it.qam) {
+    case 4: mmse_warp<NT, 4>(sc, it.n_sym, it.nr, it.nt, it.sigma2, it.H, it.Y, it.mmse_hard, it.mmse_llr, base); break;
+    case 16: mmse_warp<NT, 16>(sc, it.n_sym, it.nr, it.nt, it.sigma2, it.H, it.Y, it.mmse_hard, it.mmse_llr, base); break;
+    default: mmse_warp<NT, 64>(sc, it.n_sym, it.nr, it.nt, it.sigma2, it.H, it.Y, it.mmse_hard, it.mmse_llr, base); break;
+    }
+}
+
+// Persistent variant over a batch of radio units of mixed sizes (units
+// without the baseline are skipped).
+__global__ void __launch_bounds__(kWarps * 32, 4)
+mmse_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ start, int n_items,
+                  int *__restrict__ counter, int warp_bytes)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = warp * warp_bytes;
+    const int total = start[n_items];
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const int i = find_item(start, n_items, w);
+        const BatchItem &it = items[i];
+        if (!it.mmse) continue;
+        const int sc = w - start[i];
+        if (it.nt <= 4) mmse_warp_qam<4>(it, sc, base);
+        else if (it.nt <= 8) mmse_warp_qam<8>(it, sc, base);
+        else mmse_warp_qam<16>(it, sc, base);
+    }
 }
 
 template <int NT, int QAM>
@@ -249,6 +298,19 @@ cudaError_t launch_nt(int qam, int n_sc, int n_sym, int nr, int nt, float sigma2
 }
 
 }  // namespace
+
+size_t mmse_warp_bytes(int n_sym, int nr, int nt) { return mmse_smem_layout(nr, nt, n_sym).bytes; }
+
+cudaError_t launch_mmse_batch(const BatchItem *items, const int *start, int n_items,
+                              int *counter, int warp_bytes, int grid, cudaStream_t stream)
+{
+    const size_t smem = (size_t)warp_bytes * kWarps;
+    cudaError_t e = allow_dynamic_smem(mmse_batch_kernel, smem);
+    if (e != cudaSuccess) return e;
+    mmse_batch_kernel<<<grid, kWarps * 32, smem, stream>>>(items, start, n_items, counter,
+                                                           warp_bytes);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mmse(int n_sc, int n_sym, int nr, int nt, int qam, float sigma2,
                         const float2 *H, const float2 *Y, uint8_t *hard, float *llr,

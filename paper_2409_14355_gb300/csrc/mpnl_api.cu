@@ -10,12 +10,16 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "mpnl.h"
 #include "mpnl_internal.h"
 
 struct mpnl_ctx {
     int device;
     unsigned *status;  // device word of kStatus* bits, cleared by mpnl_check_status
+    mpnl_tuning tuning;
     char err[512];
 };
 
@@ -38,6 +42,22 @@ int cuda_fail(mpnl_ctx *ctx, const char *what, cudaError_t e)
 }
 
 int bits_of(int qam) { return qam == 4 ? 2 : qam == 16 ? 4 : qam == 64 ? 6 : 0; }
+
+int nt_class(int nt) { return nt <= 4 ? 0 : (nt <= 8 ? 1 : 2); }
+int qam_class(int qam) { return qam == 4 ? 0 : (qam == 16 ? 1 : 2); }
+int pe_class(int n_pe) { return n_pe >= 256 ? 1 : 0; }
+
+int tuned_sym(const mpnl_ctx *ctx, const mpnl_dims *d)
+{
+    const int v = ctx->tuning.detect_sym[nt_class(d->nt)][qam_class(d->qam)][pe_class(d->n_pe)];
+    return v ? v : 2;
+}
+
+int tuned_select_warps(const mpnl_ctx *ctx, const mpnl_dims *d)
+{
+    const int v = ctx->tuning.select_warps[nt_class(d->nt)][qam_class(d->qam)][pe_class(d->n_pe)];
+    return v ? v : (d->n_pe >= 256 ? 2 : 1);
+}
 
 // Rules for nr: the plain sorted QR needs nt <= nr <= MPNL_MAX_NR (a square
 // or tall channel); the MMSE-extended one factors nr + nt rows and needs
@@ -120,7 +140,222 @@ int begin(mpnl_ctx *ctx)
 
 }  // namespace
 
+struct mpnl_batch {
+    int device;
+    int n_items;
+    mpnl::BatchItem *d_items;  // schedule order
+    int *d_start;              // n_items + 1 prefix sums of n_sc
+    int *d_counters;           // one per stage
+    bool any_mmse;
+    int pre_warp_bytes, sel_group_bytes, mmse_warp_bytes;
+    size_t det_smem;
+    int sel_warps, det_ctas;
+    int sms;
+    cudaGraphExec_t graph[MPNL_STAGES_ALL + 1];
+};
+
+namespace {
+
+// Rough per-subcarrier cost of a unit's walks, for largest-first ordering.
+double unit_cost(const mpnl_dims &d) { return (double)d.n_pe * d.nt * (d.nt + 4) * d.n_sym; }
+
+int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(ctx, "batch counter reset", e);
+    if (stages & MPNL_STAGE_PREPROCESS) {
+        e = mpnl::launch_preprocess_batch(b->d_items, b->d_start, b->n_items, b->d_counters + 0,
+                                          b->pre_warp_bytes, b->sms * 4, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "batch preprocess launch", e);
+    }
+    if (stages & MPNL_STAGE_SELECT) {
+        e = mpnl::launch_select_batch(b->d_items, b->d_start, b->n_items, b->d_counters + 1,
+                                      b->sel_group_bytes, b->sel_warps, b->sms * 4, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "batch select launch", e);
+    }
+    if (stages & MPNL_STAGE_DETECT) {
+        e = mpnl::launch_detect_batch(b->d_items, b->d_start, b->n_items, b->d_counters + 2,
+                                      ctx->status, b->det_smem, b->sms * b->det_ctas, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "batch detect launch", e);
+    }
+    if ((stages & MPNL_STAGE_MMSE) && b->any_mmse) {
+        e = mpnl::launch_mmse_batch(b->d_items, b->d_start, b->n_items, b->d_counters + 3,
+                                    b->mmse_warp_bytes, b->sms * 4, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "batch mmse launch", e);
+    }
+    return MPNL_OK;
+}
+
+}  // namespace
+
 extern "C" {
+
+int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
+                      mpnl_batch **out)
+{
+    MPNL_TRY(begin(ctx));
+    if (!out) return fail(ctx, MPNL_ERR_INVALID_ARG, "batch is NULL");
+    *out = nullptr;
+    if (n_items < 1 || !items) return fail(ctx, MPNL_ERR_INVALID_ARG, "need at least one item");
+    int dev_smem = 0, sms = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    std::vector<mpnl::BatchItem> host(n_items);
+    std::vector<int> order(n_items);
+    size_t pre = 16, sel = 16, mm = 16, det = 16;
+    bool any_mmse = false;
+    for (int i = 0; i < n_items; ++i) {
+        const mpnl_batch_item &it = items[i];
+        const mpnl_dims *d = &it.dims;
+        const bool mqr = it.flags & MPNL_ITEM_MMSE_QR, lin = it.flags & MPNL_ITEM_LINEAR_MMSE;
+        int st = check_dims(ctx, d, true, mqr ? kNrAugmented : kNrTall);
+        if (st == MPNL_OK) st = check_sigma2(ctx, it.sigma2);
+        if (st == MPNL_OK && (it.flags & ~(MPNL_ITEM_MMSE_QR | MPNL_ITEM_LINEAR_MMSE)))
+            st = fail(ctx, MPNL_ERR_INVALID_ARG, "unknown flags 0x%x", it.flags);
+        if (st == MPNL_OK && d->n_sc > 0) {
+            const void *req[] = {it.H, it.Y, it.R, it.inv_diag, it.perm, it.Z, it.paths, it.hard};
+            const char *nm[] = {"H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard"};
+            const size_t al[] = {8, 8, 8, 4, 1, 8, 1, 1};
+            for (int k = 0; k < 8 && st == MPNL_OK; ++k) st = check_ptr(ctx, req[k], al[k], nm[k], false);
+            if (st == MPNL_OK) st = check_ptr(ctx, it.llr, 4, "llr", true);
+            if (st == MPNL_OK) st = check_ptr(ctx, it.ped2, 4, "ped2", true);
+            if (st == MPNL_OK && lin) st = check_ptr(ctx, it.mmse_hard, 1, "mmse_hard", false);
+            if (st == MPNL_OK && lin) st = check_ptr(ctx, it.mmse_llr, 4, "mmse_llr", true);
+        }
+        if (st != MPNL_OK) {
+            char msg[sizeof ctx->err];
+            snprintf(msg, sizeof msg, "item %d: %s", i, ctx->err);
+            return fail(ctx, st, "%s", msg);
+        }
+        mpnl::BatchItem &b = host[i];
+        b.n_sc = d->n_sc;
+        b.n_sym = d->n_sym;
+        b.nr = d->nr;
+        b.nt = d->nt;
+        b.qam = d->qam;
+        b.n_pe = d->n_pe;
+        b.sigma2 = it.sigma2;
+        b.sigma = mqr ? sqrtf(it.sigma2) : 0.f;
+        b.sym = tuned_sym(ctx, d);
+        b.mmse = lin ? 1 : 0;
+        b.H = (const float2 *)it.H;
+        b.Y = (const float2 *)it.Y;
+        b.R = (float2 *)it.R;
+        b.inv_diag = it.inv_diag;
+        b.perm = it.perm;
+        b.Z = (float2 *)it.Z;
+        b.paths = it.paths;
+        b.hard = it.hard;
+        b.llr = it.llr;
+        b.ped2 = it.ped2;
+        b.mmse_hard = lin ? it.mmse_hard : nullptr;
+        b.mmse_llr = lin ? it.mmse_llr : nullptr;
+        any_mmse = any_mmse || lin;
+        const int rows = mqr ? d->nr + d->nt : d->nr;
+        pre = std::max(pre, mpnl::preprocess_warp_bytes(d->n_sym, rows, d->nt));
+        sel = std::max(sel, mpnl::select_group_bytes(d->n_pe));
+        det = std::max(det, mpnl::detect_smem_bytes(d->nt, d->qam, d->n_pe, d->n_sym));
+        if (lin) mm = std::max(mm, mpnl::mmse_warp_bytes(d->n_sym, d->nr, d->nt));
+        order[i] = i;
+    }
+    int sel_warps = 2;  // the persistent selection uses one group shape for every unit
+    {
+        const int v = ctx->tuning.select_warps[2][2][1];
+        if (v) sel_warps = v;
+    }
+    int det_ctas = ctx->tuning.persistent_ctas_per_sm ? ctx->tuning.persistent_ctas_per_sm : 2;
+    while (det_ctas > 1 && (size_t)det_ctas * det > (size_t)dev_smem) --det_ctas;
+    if (det > (size_t)dev_smem || pre * 4 > (size_t)dev_smem || mm * 4 > (size_t)dev_smem ||
+        sel * (4 / sel_warps) > (size_t)dev_smem)
+        return fail(ctx, MPNL_ERR_UNSUPPORTED, "a unit needs more shared memory than one SM has");
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return unit_cost(items[a].dims) > unit_cost(items[c].dims);
+    });
+    std::vector<mpnl::BatchItem> sorted(n_items);
+    std::vector<int> start(n_items + 1, 0);
+    for (int k = 0; k < n_items; ++k) {
+        sorted[k] = host[order[k]];
+        start[k + 1] = start[k] + sorted[k].n_sc;
+    }
+    mpnl_batch *b = (mpnl_batch *)calloc(1, sizeof(mpnl_batch));
+    if (!b) return fail(ctx, MPNL_ERR_CUDA, "out of host memory");
+    b->device = ctx->device;
+    b->n_items = n_items;
+    b->any_mmse = any_mmse;
+    b->pre_warp_bytes = (int)pre;
+    b->sel_group_bytes = (int)sel;
+    b->mmse_warp_bytes = (int)mm;
+    b->det_smem = det;
+    b->sel_warps = sel_warps;
+    b->det_ctas = det_ctas;
+    b->sms = sms > 0 ? sms : 1;
+    cudaError_t e = cudaMalloc(&b->d_items, sizeof(mpnl::BatchItem) * n_items);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_start, sizeof(int) * (n_items + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * 4);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_items, sorted.data(), sizeof(mpnl::BatchItem) * n_items,
+                       cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_start, start.data(), sizeof(int) * (n_items + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        mpnl_batch_destroy(b);
+        return cuda_fail(ctx, "batch create", e);
+    }
+    *out = b;
+    return MPNL_OK;
+}
+
+int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *b, int stages, void *stream)
+{
+    MPNL_TRY(begin(ctx));
+    if (!b) return fail(ctx, MPNL_ERR_INVALID_ARG, "batch is NULL");
+    if (b->device != ctx->device)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "batch lives on device %d, context on %d", b->device,
+                    ctx->device);
+    if (stages & ~(MPNL_STAGES_ALL | MPNL_RUN_GRAPH))
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "unknown stage bits 0x%x", stages);
+    const int mask = stages & MPNL_STAGES_ALL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!(stages & MPNL_RUN_GRAPH)) return enqueue_batch(ctx, b, mask, st);
+    if (!st) return fail(ctx, MPNL_ERR_INVALID_ARG, "graph capture needs a non-default stream");
+    if (!b->graph[mask]) {
+        cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(ctx, "graph capture begin", e);
+        const int rc = enqueue_batch(ctx, b, mask, st);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(st, &g);
+        if (rc != MPNL_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(ctx, "graph capture end", e);
+        e = cudaGraphInstantiate(&b->graph[mask], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            b->graph[mask] = nullptr;
+            return cuda_fail(ctx, "graph instantiate", e);
+        }
+    }
+    cudaError_t e = cudaGraphLaunch(b->graph[mask], st);
+    if (e != cudaSuccess) return cuda_fail(ctx, "graph launch", e);
+    return MPNL_OK;
+}
+
+void mpnl_batch_destroy(mpnl_batch *b)
+{
+    if (!b) return;
+    int prev = -1;
+    cudaGetDevice(&prev);
+    cudaSetDevice(b->device);
+    for (int k = 0; k <= MPNL_STAGES_ALL; ++k)
+        if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_start) cudaFree(b->d_start);
+    if (b->d_counters) cudaFree(b->d_counters);
+    free(b);
+    if (prev >= 0) cudaSetDevice(prev);
+}
+
 
 int mpnl_create(mpnl_ctx **out, int device)
 {
@@ -211,7 +446,8 @@ int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, float si
     MPNL_TRY(check_ptr(ctx, R, 8, "R", false));
     MPNL_TRY(check_ptr(ctx, paths, 1, "paths", false));
     cudaError_t e = mpnl::launch_select_paths(d->n_sc, d->nt, d->qam, d->n_pe, sigma2,
-                                              (const float2 *)R, paths, (cudaStream_t)stream);
+                                              (const float2 *)R, paths, tuned_select_warps(ctx, d),
+                                              (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, "select_paths launch", e);
     return MPNL_OK;
 }
@@ -234,7 +470,8 @@ static int detect_impl(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, const f
     MPNL_TRY(check_ptr(ctx, ped2, 4, "ped2", true));
     cudaError_t e = mpnl::launch_detect(d->n_sc, d->n_sym, d->nt, d->qam, d->n_pe, sigma2,
                                         (const float2 *)R, inv_diag, perm, paths, (const float2 *)Z,
-                                        hard, llr, ped2, ctx->status, f16, (cudaStream_t)stream);
+                                        hard, llr, ped2, ctx->status, f16, tuned_sym(ctx, d),
+                                        (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, "detect launch", e);
     return MPNL_OK;
 }
@@ -287,6 +524,38 @@ int mpnl_check_status(mpnl_ctx *ctx, void *stream)
     if (h & mpnl::kStatusBadPathEntry)
         return fail(ctx, MPNL_ERR_INVALID_ARG,
                     "detect: a position-vector entry was outside 1..qam (clamped)");
+    return MPNL_OK;
+}
+
+int mpnl_set_tuning(mpnl_ctx *ctx, const mpnl_tuning *t)
+{
+    if (!ctx) return MPNL_ERR_INVALID_ARG;
+    ctx->err[0] = '\0';
+    if (!t) {
+        memset(&ctx->tuning, 0, sizeof ctx->tuning);
+        return MPNL_OK;
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int c = 0; c < 2; ++c) {
+                const int s = t->detect_sym[a][b][c], w = t->select_warps[a][b][c];
+                if (s > 2) return fail(ctx, MPNL_ERR_INVALID_ARG, "detect_sym=%d not in {0,1,2}", s);
+                if (w != 0 && w != 1 && w != 2 && w != 4)
+                    return fail(ctx, MPNL_ERR_INVALID_ARG, "select_warps=%d not in {0,1,2,4}", w);
+            }
+    if (t->persistent_ctas_per_sm > 2)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "persistent_ctas_per_sm=%d not in {0,1,2}",
+                    t->persistent_ctas_per_sm);
+    ctx->tuning = *t;
+    return MPNL_OK;
+}
+
+int mpnl_get_tuning(mpnl_ctx *ctx, mpnl_tuning *t)
+{
+    if (!ctx) return MPNL_ERR_INVALID_ARG;
+    ctx->err[0] = '\0';
+    if (!t) return fail(ctx, MPNL_ERR_INVALID_ARG, "tuning is NULL");
+    *t = ctx->tuning;
     return MPNL_OK;
 }
 

@@ -8,20 +8,42 @@
 
 namespace mpnl {
 
+// Arguments of one detection problem (one radio unit's slot): sizes and the
+// caller's device arrays, indexed by subcarrier inside the walk kernel.
+struct DetArgs {
+    int n_sym, nt, n_pe;
+    float sigma2;
+    const float2 *Rp;
+    const float *inv_diag;
+    const uint8_t *perm;
+    const uint8_t *paths;
+    const float2 *Z;
+    uint8_t *hard;
+    float *llr;
+    float *ped2;
+    unsigned *status;
+};
+
 // sigma > 0: MMSE-extended factorisation of [H; sigma I] (mpnl_preprocess_mmse).
 cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *H,
                               const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,
                               float2 *Z, cudaStream_t stream);
 
+// warps: threads of one subcarrier's merges, 32 x (1, 2 or 4).
 cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,
-                                const float2 *R, uint8_t *paths, cudaStream_t stream);
+                                const float2 *R, uint8_t *paths, int warps, cudaStream_t stream);
 
 // f16: residuals in half2 with FP32 ranking / PED and an FP32 re-check of
 // the best and runner-up paths (mpnl_detect_mixed); false: all FP32.
+// sym: symbols per lane (1 or 2; a tuning knob, results do not depend on it).
 cudaError_t launch_detect(int n_sc, int n_sym, int nt, int qam, int n_pe, float sigma2,
                           const float2 *R, const float *inv_diag, const uint8_t *perm,
                           const uint8_t *paths, const float2 *Z, uint8_t *hard, float *llr,
-                          float *ped2, unsigned *status, bool f16, cudaStream_t stream);
+                          float *ped2, unsigned *status, bool f16, int sym, cudaStream_t stream);
+size_t detect_smem_bytes(int nt, int qam, int n_pe, int n_sym);
+// The two precisions' launchers live in their own translation units.
+cudaError_t launch_detect_f32(int n_sc, const DetArgs &a, int qam, int sym, cudaStream_t stream);
+cudaError_t launch_detect_f16(int n_sc, const DetArgs &a, int qam, int sym, cudaStream_t stream);
 
 cudaError_t launch_mmse(int n_sc, int n_sym, int nr, int nt, int qam, float sigma2,
                         const float2 *H, const float2 *Y, uint8_t *hard, float *llr,
@@ -30,6 +52,55 @@ cudaError_t launch_mmse(int n_sc, int n_sym, int nr, int nt, int qam, float sigm
 // FP32 FMA throughput probe (mpnl_probe_ffma): 256-thread CTAs.
 cudaError_t launch_ffma_probe(int n_blocks, int iters, float *out, cudaStream_t stream);
 double ffma_probe_flops(int n_blocks, int iters);
+
+// One radio unit's slot in a batch (mpnl_batch_*), as the persistent kernels
+// read it from device memory.  The work items of a batch are its units'
+// subcarriers; start[] holds their prefix sums (n_items + 1 entries).
+struct BatchItem {
+    int n_sc, n_sym, nr, nt, qam, n_pe;
+    float sigma2, sigma;  // sigma > 0: MMSE-extended QR (sigma = sqrt(sigma2))
+    int sym;              // symbols per lane of the walk kernel
+    int mmse;             // also run the linear MMSE baseline
+    const float2 *H, *Y;
+    float2 *R;
+    float *inv_diag;
+    uint8_t *perm;
+    float2 *Z;
+    uint8_t *paths;
+    uint8_t *hard;
+    float *llr;
+    float *ped2;
+    uint8_t *mmse_hard;
+    float *mmse_llr;
+};
+
+// Unit of work item w: the largest i with start[i] <= w.
+__device__ __forceinline__ int find_item(const int *start, int n_items, int w)
+{
+    int lo = 0, hi = n_items - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent batch launchers: `counter` is a device int reset to 0 before
+// the launch; shared memory per worker is the maximum over the batch.
+size_t preprocess_warp_bytes(int n_sym, int nr, int nt);
+cudaError_t launch_preprocess_batch(const BatchItem *items, const int *start, int n_items,
+                                    int *counter, int warp_bytes, int grid, cudaStream_t stream);
+size_t select_group_bytes(int n_pe);
+cudaError_t launch_select_batch(const BatchItem *items, const int *start, int n_items,
+                                int *counter, int group_bytes, int warps, int grid,
+                                cudaStream_t stream);
+cudaError_t launch_detect_batch(const BatchItem *items, const int *start, int n_items,
+                                int *counter, unsigned *status, size_t smem, int grid,
+                                cudaStream_t stream);
+size_t mmse_warp_bytes(int n_sym, int nr, int nt);
+cudaError_t launch_mmse_batch(const BatchItem *items, const int *start, int n_items,
+                              int *counter, int warp_bytes, int grid, cudaStream_t stream);
 
 // Device status bits (mpnl_check_status).
 constexpr unsigned kStatusBadPathEntry = 1u;

@@ -53,21 +53,23 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int nr, int nt, int n_sym)
 // augmented with sigma * I below the nr antenna rows and the symbol columns
 // with zeros (H_a = [H; sigma I], y_a = [y; 0]), so the factorisation has
 // nr + nt rows; nr may then be smaller than nt.
+// One subcarrier by one warp, in the warp's shared-memory region at byte
+// offset base_off of the dynamic shared memory (at least
+// warp_smem_layout(nr, nt, n_sym).bytes).  Inlined into the per-call and the batch
+// kernels alike (identical arithmetic: no contraction, see the build flags).
 template <int NR, int CS>
-__global__ void __launch_bounds__(kWarpsPerCta * 32)
-sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *__restrict__ H,
-                const float2 *__restrict__ Y, float2 *__restrict__ Rp,
-                float *__restrict__ inv_diag, uint8_t *__restrict__ perm_out,
-                float2 *__restrict__ Z)
+__device__ __forceinline__ void sqrd_qhy_warp(int sc, int n_sym, int nr, int nt, float sigma,
+                                           const float2 *__restrict__ H,
+                                           const float2 *__restrict__ Y,
+                                           float2 *__restrict__ Rp,
+                                           float *__restrict__ inv_diag,
+                                           uint8_t *__restrict__ perm_out,
+                                           float2 *__restrict__ Z, int base_off)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5;
+    unsigned char *base = smem_raw + base_off;
     const int lane = threadIdx.x & 31;
-    const int sc = blockIdx.x * kWarpsPerCta + warp;
-    if (sc >= n_sc) return;  // only __syncwarp below: per-warp early exit is safe
-
     const WarpSmem L = warp_smem_layout(nr, nt, n_sym);
-    unsigned char *base = smem_raw + warp * L.bytes;
     float2 *sH = reinterpret_cast<float2 *>(base + L.off_h);
     float2 *sY = reinterpret_cast<float2 *>(base + L.off_y);
     float2 *sQ = reinterpret_cast<float2 *>(base + L.off_q);
@@ -187,6 +189,59 @@ sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *
     }
     float2 *gZ = Z + (size_t)sc * n_sym * nt;
     for (int k = lane; k < n_sym * nt; k += 32) gZ[k] = sZ[k];
+    __syncwarp();  // the region may be reused for the warp's next subcarrier
+}
+
+template <int NR, int CS>
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *__restrict__ H,
+                const float2 *__restrict__ Y, float2 *__restrict__ Rp,
+                float *__restrict__ inv_diag, uint8_t *__restrict__ perm_out,
+                float2 *__restrict__ Z)
+{
+    const int warp = threadIdx.x >> 5;
+    const int sc = blockIdx.x * kWarpsPerCta + warp;
+    if (sc >= n_sc) return;  // only __syncwarp inside: per-warp early exit is safe
+    const WarpSmem L = warp_smem_layout(nr, nt, n_sym);
+    sqrd_qhy_warp<NR, CS>(sc, n_sym, nr, nt, sigma, H, Y, Rp, inv_diag, perm_out, Z,
+                          warp * L.bytes);
+}
+
+// Persistent variant over a batch of radio units of mixed sizes: every warp
+// takes (unit, subcarrier) work items from a global counter until the batch
+// is exhausted and runs the instance that fits the unit's sizes.
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+sqrd_qhy_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ start,
+                      int n_items, int *__restrict__ counter, int warp_bytes)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int base = warp * warp_bytes;
+    const int total = start[n_items];
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const int i = find_item(start, n_items, w);
+        const BatchItem &it = items[i];
+        const int sc = w - start[i];
+        const int rows = it.sigma > 0.f ? it.nr + it.nt : it.nr;
+        const bool two = it.nt + it.n_sym > 32;
+#define MPNL_PRE_W(NRV)                                                                          \
+    do {                                                                                         \
+        if (two)                                                                                 \
+            sqrd_qhy_warp<NRV, 2>(sc, it.n_sym, it.nr, it.nt, it.sigma, it.H, it.Y, it.R,        \
+                                  it.inv_diag, it.perm, it.Z, base);                             \
+        else                                                                                     \
+            sqrd_qhy_warp<NRV, 1>(sc, it.n_sym, it.nr, it.nt, it.sigma, it.H, it.Y, it.R,        \
+                                  it.inv_diag, it.perm, it.Z, base);                             \
+    } while (0)
+        if (rows <= 4) MPNL_PRE_W(4);
+        else if (rows <= 8) MPNL_PRE_W(8);
+        else if (rows <= 16) MPNL_PRE_W(16);
+        else MPNL_PRE_W(32);
+#undef MPNL_PRE_W
+    }
 }
 
 template <int NR, int CS>
@@ -207,6 +262,19 @@ cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, float sigma, const f
 }
 
 }  // namespace
+
+size_t preprocess_warp_bytes(int n_sym, int nr, int nt) { return warp_smem_layout(nr, nt, n_sym).bytes; }
+
+cudaError_t launch_preprocess_batch(const BatchItem *items, const int *start, int n_items,
+                                    int *counter, int warp_bytes, int grid, cudaStream_t stream)
+{
+    const size_t smem = (size_t)warp_bytes * kWarpsPerCta;
+    cudaError_t e = allow_dynamic_smem(sqrd_qhy_batch_kernel, smem);
+    if (e != cudaSuccess) return e;
+    sqrd_qhy_batch_kernel<<<grid, kWarpsPerCta * 32, smem, stream>>>(items, start, n_items, counter,
+                                                                     warp_bytes);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *H,
                               const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,

@@ -72,21 +72,22 @@ __device__ __forceinline__ void group_sync(int group)
     }
 }
 
+// One subcarrier by one group of G warps (thread tid of the group, which is
+// group number `group` of its CTA), in the group's shared-memory region at
+// byte offset base_off (at least sel_group_bytes(n_pe)).  Inlined into
+// the per-call and the batch kernels alike (no contraction).
 template <int QAM, int G>
-__global__ void __launch_bounds__(kSelMaxWarps * 32)
-select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
-                    uint8_t *__restrict__ paths)
+__device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, float sigma2,
+                                               const float2 *__restrict__ Rp,
+                                               uint8_t *__restrict__ paths, int base_off,
+                                               int group, int tid)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + base_off;
     constexpr unsigned FULL = 0xffffffffu;
     constexpr int T = 32 * G;  // threads per subcarrier
-    const int group = threadIdx.x / T, tid = threadIdx.x % T;
-    const int sc = blockIdx.x * (blockDim.x / T) + group;
-    if (sc >= n_sc) return;  // whole groups leave; each group syncs only itself
-
     // three lists (struct of arrays) addressed as base + list * n_pe, so that
     // the list index stays arithmetic (no pointer arrays in local memory)
-    unsigned char *base = smem_raw + (size_t)group * sel_group_bytes(n_pe);
     unsigned long long *HI = reinterpret_cast<unsigned long long *>(base);
     unsigned long long *LO = HI + 3 * n_pe;
     float *CO = reinterpret_cast<float *>(LO + 3 * n_pe);
@@ -263,6 +264,49 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
 #undef hi
 #undef lo
 #undef cost
+    group_sync<G>(group);  // the region may be reused for the group's next subcarrier
+}
+
+template <int QAM, int G>
+__global__ void __launch_bounds__(kSelMaxWarps * 32)
+select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
+                    uint8_t *__restrict__ paths)
+{
+    constexpr int T = 32 * G;
+    const int group = threadIdx.x / T, tid = threadIdx.x % T;
+    const int sc = blockIdx.x * (blockDim.x / T) + group;
+    if (sc >= n_sc) return;  // whole groups leave; each group syncs only itself
+    select_group_body<QAM, G>(sc, nt, n_pe, sigma2, Rp, paths,
+                              group * (int)sel_group_bytes(n_pe), group, tid);
+}
+
+// Persistent variant over a batch of radio units of mixed sizes: every
+// group takes (unit, subcarrier) work items from a global counter.
+template <int G>
+__global__ void __launch_bounds__(kSelMaxWarps * 32)
+select_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ start,
+                    int n_items, int *__restrict__ counter, int group_bytes)
+{
+    __shared__ int s_w[kSelMaxWarps];
+    constexpr int T = 32 * G;
+    const int group = threadIdx.x / T, tid = threadIdx.x % T;
+    const int base = group * group_bytes;
+    const int total = start[n_items];
+    for (;;) {
+        if (tid == 0) s_w[group] = atomicAdd(counter, 1);
+        group_sync<G>(group);
+        const int w = s_w[group];
+        group_sync<G>(group);  // every thread has read the item before the next fetch
+        if (w >= total) break;
+        const int i = find_item(start, n_items, w);
+        const BatchItem &it = items[i];
+        const int sc = w - start[i];
+        switch (it.qam) {
+        case 4: select_group_body<4, G>(sc, it.nt, it.n_pe, it.sigma2, it.R, it.paths, base, group, tid); break;
+        case 16: select_group_body<16, G>(sc, it.nt, it.n_pe, it.sigma2, it.R, it.paths, base, group, tid); break;
+        default: select_group_body<64, G>(sc, it.nt, it.n_pe, it.sigma2, it.R, it.paths, base, group, tid); break;
+        }
+    }
 }
 
 template <int QAM, int G>
@@ -287,22 +331,47 @@ cudaError_t launch_group(int n_sc, int nt, int n_pe, float sigma2, const float2 
 
 template <int QAM>
 cudaError_t launch_tpl(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
-                       uint8_t *paths, cudaStream_t stream)
+                       uint8_t *paths, int warps, cudaStream_t stream)
 {
-    return n_pe >= 256 ? launch_group<QAM, 2>(n_sc, nt, n_pe, sigma2, R, paths, stream)
-                       : launch_group<QAM, 1>(n_sc, nt, n_pe, sigma2, R, paths, stream);
+    if (warps == 4) return launch_group<QAM, 4>(n_sc, nt, n_pe, sigma2, R, paths, stream);
+    if (warps == 2) return launch_group<QAM, 2>(n_sc, nt, n_pe, sigma2, R, paths, stream);
+    return launch_group<QAM, 1>(n_sc, nt, n_pe, sigma2, R, paths, stream);
+}
+
+template <int G>
+cudaError_t launch_select_batch_g(const BatchItem *items, const int *start, int n_items,
+                                  int *counter, int group_bytes, int grid, cudaStream_t stream)
+{
+    const int groups = kSelMaxWarps / G;
+    const size_t smem = (size_t)group_bytes * groups;
+    cudaError_t e = allow_dynamic_smem(select_batch_kernel<G>, smem);
+    if (e != cudaSuccess) return e;
+    select_batch_kernel<G><<<grid, kSelMaxWarps * 32, smem, stream>>>(items, start, n_items,
+                                                                     counter, group_bytes);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
+size_t select_group_bytes(int n_pe) { return sel_group_bytes(n_pe); }
+
+cudaError_t launch_select_batch(const BatchItem *items, const int *start, int n_items,
+                                int *counter, int group_bytes, int warps, int grid,
+                                cudaStream_t stream)
+{
+    if (warps == 4) return launch_select_batch_g<4>(items, start, n_items, counter, group_bytes, grid, stream);
+    if (warps == 2) return launch_select_batch_g<2>(items, start, n_items, counter, group_bytes, grid, stream);
+    return launch_select_batch_g<1>(items, start, n_items, counter, group_bytes, grid, stream);
+}
+
 cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,
-                                const float2 *R, uint8_t *paths, cudaStream_t stream)
+                                const float2 *R, uint8_t *paths, int warps, cudaStream_t stream)
 {
     if (n_sc == 0) return cudaSuccess;
     switch (qam) {
-    case 4: return launch_tpl<4>(n_sc, nt, n_pe, sigma2, R, paths, stream);
-    case 16: return launch_tpl<16>(n_sc, nt, n_pe, sigma2, R, paths, stream);
-    default: return launch_tpl<64>(n_sc, nt, n_pe, sigma2, R, paths, stream);
+    case 4: return launch_tpl<4>(n_sc, nt, n_pe, sigma2, R, paths, warps, stream);
+    case 16: return launch_tpl<16>(n_sc, nt, n_pe, sigma2, R, paths, warps, stream);
+    default: return launch_tpl<64>(n_sc, nt, n_pe, sigma2, R, paths, warps, stream);
     }
 }
 

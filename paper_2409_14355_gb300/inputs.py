@@ -119,3 +119,51 @@ def workload_slot(name: str, snr_index: int = 0, n_sc: int | None = None, extra_
     return make_slot(w["nr"], w["nt"], w["qam"], n_sc if n_sc is not None else w["n_sc"],
                      14, w["snrs"][snr_index], w["channel"], 0.3,
                      seed_for(w["config"], snr_index) + 7919 * extra_seed, noise)
+
+
+# Mixed batch of radio units (config 4): rx antennas in {4, 8, 16}, users
+# uniform in rx/2..rx, QAM in {4, 16, 64}, subcarriers in {312, 936, 3276},
+# N_pe in {16, 32, 64, 128, 256} (capped at QAM^users), all uniform; i.i.d.
+# or Kronecker (rho 0.3) channels; SNR per unit drawn around a level where
+# the QAM order is usable (QPSK 8-14 dB, 16-QAM 14-20 dB, 64-QAM 20-26 dB).
+MIXED_CONFIG = 4
+MIXED_RX = (4, 8, 16)
+MIXED_QAM = (4, 16, 64)
+MIXED_SC = (312, 936, 3276)
+MIXED_NPE = (16, 32, 64, 128, 256)
+MIXED_SNR_LO = {4: 8.0, 16: 14.0, 64: 20.0}
+
+
+@dataclass
+class UnitSpec:
+    nr: int
+    nt: int
+    qam: int
+    n_sc: int
+    n_pe: int
+    snr_db: float
+    channel: str
+    seed: int
+
+
+def mixed_units(n_units: int = 64, seed: int | None = None, sc_scale: float = 1.0,
+                config: int = MIXED_CONFIG) -> list[UnitSpec]:
+    """Sizes of a mixed batch.  sc_scale shrinks the subcarrier counts (for
+    tests) without changing the other draws."""
+    rng = np.random.Generator(np.random.PCG64(seed_for(config) if seed is None else seed))
+    out = []
+    for k in range(n_units):
+        nr = int(rng.choice(MIXED_RX))
+        nt = int(rng.integers(nr // 2, nr + 1))
+        qam = int(rng.choice(MIXED_QAM))
+        n_sc = max(1, int(round(int(rng.choice(MIXED_SC)) * sc_scale)))
+        n_pe = int(min(int(rng.choice(MIXED_NPE)), qam ** nt))
+        snr = float(MIXED_SNR_LO[qam] + 6.0 * rng.random())
+        channel = "iid" if rng.random() < 0.5 else "kronecker"
+        out.append(UnitSpec(nr, nt, qam, n_sc, n_pe, snr, channel,
+                            int(rng.integers(0, 2 ** 31 - 1))))
+    return out
+
+
+def unit_slot(u: UnitSpec, n_sym: int = 14, noise: bool = True) -> Slot:
+    return make_slot(u.nr, u.nt, u.qam, u.n_sc, n_sym, u.snr_db, u.channel, 0.3, u.seed, noise)

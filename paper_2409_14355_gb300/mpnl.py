@@ -37,7 +37,11 @@ ERR_TIMEOUT = -4
 EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_bytes",
             "mpnl_preprocess", "mpnl_preprocess_mmse", "mpnl_select_paths", "mpnl_detect",
             "mpnl_detect_mixed",
-            "mpnl_linear_mmse", "mpnl_check_status", "mpnl_probe_ffma")
+            "mpnl_linear_mmse", "mpnl_check_status", "mpnl_probe_ffma", "mpnl_set_tuning",
+            "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy")
+ITEM_MMSE_QR, ITEM_LINEAR_MMSE = 1, 2
+STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGES_ALL = 1, 2, 4, 8, 15
+RUN_GRAPH = 16
 PRECISIONS = ("fp32", "fp16")
 
 
@@ -55,6 +59,27 @@ class Dims(ctypes.Structure):
 _lib = None
 _lib_lock = threading.Lock()
 _ctxs: dict[int, ctypes.c_void_p] = {}
+
+
+class Tuning(ctypes.Structure):
+    """Launch-shape knobs (mpnl_tuning): [nt class][qam class][N_pe class],
+    0 = built-in choice.  Results never depend on them."""
+    _fields_ = [("detect_sym", ((ctypes.c_uint8 * 2) * 3) * 3),
+                ("select_warps", ((ctypes.c_uint8 * 2) * 3) * 3),
+                ("persistent_ctas_per_sm", ctypes.c_uint8)]
+
+
+class BatchItemC(ctypes.Structure):
+    """mpnl_batch_item."""
+    _fields_ = [("dims", Dims), ("sigma2", ctypes.c_float), ("flags", ctypes.c_int)] + [
+        (n, ctypes.c_void_p) for n in ("H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard",
+                                       "llr", "ped2", "mmse_hard", "mmse_llr")]
+
+
+def problem_class(nt: int, qam: int, n_pe: int) -> tuple[int, int, int]:
+    """Index of a problem in the Tuning tables."""
+    return (0 if nt <= 4 else (1 if nt <= 8 else 2), {4: 0, 16: 1, 64: 2}[qam],
+            1 if n_pe >= 256 else 0)
 
 
 def load_library(path: str = LIB_PATH):
@@ -92,6 +117,17 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_check_status.restype = I
         lib.mpnl_probe_ffma.argtypes = [P, I, I, P, ctypes.POINTER(ctypes.c_double), P]
         lib.mpnl_probe_ffma.restype = I
+        lib.mpnl_batch_create.argtypes = [P, ctypes.POINTER(BatchItemC), I,
+                                          ctypes.POINTER(ctypes.c_void_p)]
+        lib.mpnl_batch_create.restype = I
+        lib.mpnl_batch_run.argtypes = [P, P, I, P]
+        lib.mpnl_batch_run.restype = I
+        lib.mpnl_batch_destroy.argtypes = [P]
+        lib.mpnl_batch_destroy.restype = None
+        lib.mpnl_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+        lib.mpnl_set_tuning.restype = I
+        lib.mpnl_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
+        lib.mpnl_get_tuning.restype = I
         _lib = lib
         return lib
 
@@ -248,6 +284,22 @@ def check_status(device: int | None = None) -> None:
     _raise(load_library().mpnl_check_status(ctx, _stream(dev)), ctx)
 
 
+def set_tuning(tuning: Tuning | None, device: int | None = None) -> None:
+    """Install launch-shape knobs on the device's context (None: built-in)."""
+    dev = torch.cuda.current_device() if device is None else device
+    ctx = context(dev)
+    _raise(load_library().mpnl_set_tuning(ctx, None if tuning is None else ctypes.byref(tuning)),
+           ctx)
+
+
+def get_tuning(device: int | None = None) -> Tuning:
+    dev = torch.cuda.current_device() if device is None else device
+    ctx = context(dev)
+    t = Tuning()
+    _raise(load_library().mpnl_get_tuning(ctx, ctypes.byref(t)), ctx)
+    return t
+
+
 def probe_ffma(n_blocks: int, iters: int, out: torch.Tensor) -> float:
     """Enqueue the FP32 FMA throughput probe on the current stream (measurement
     helper, not part of the detector); returns the flops it performs."""
@@ -324,3 +376,53 @@ def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
         out = {k: v.to("cpu", non_blocking=True) for k, v in out.items()}
         torch.cuda.current_stream(device).synchronize()
     return out
+
+
+class Batch:
+    """A mixed-size batch of radio units' slots run by the persistent
+    launches (mpnl_batch_*).  Each unit is a SlotBuffers whose H and Y the
+    caller fills; ``run`` writes its R/perm/Z/paths state and its results.
+    Units are given as (buffers, sigma2, mmse_qr, mmse) tuples."""
+
+    def __init__(self, units, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.units = list(units)
+        items = (BatchItemC * len(self.units))()
+        for k, (buf, sigma2, mmse_qr, mmse) in enumerate(self.units):
+            n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
+            it = items[k]
+            it.dims = Dims(n_sc, n_sym, nr, nt, qam, n_pe)
+            it.sigma2 = float(sigma2)
+            it.flags = (ITEM_MMSE_QR if mmse_qr else 0) | (ITEM_LINEAR_MMSE if mmse else 0)
+            for name in ("H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard", "llr", "ped2"):
+                setattr(it, name, getattr(buf, name).data_ptr())
+            if mmse:
+                it.mmse_hard = buf.mmse_hard.data_ptr()
+                it.mmse_llr = buf.mmse_llr.data_ptr()
+        self._ctx = context(self.device.index)
+        h = ctypes.c_void_p()
+        _raise(load_library().mpnl_batch_create(self._ctx, items, len(self.units), ctypes.byref(h)),
+               self._ctx)
+        self._h = h
+
+    def run(self, stages: int = STAGES_ALL, graph: bool = False, stream=None) -> None:
+        """Enqueue the stages on `stream` (default: the current stream; a
+        graph needs a non-default stream)."""
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        flags = stages | (RUN_GRAPH if graph else 0)
+        _raise(load_library().mpnl_batch_run(self._ctx, self._h, flags,
+                                             ctypes.c_void_p(st.cuda_stream)), self._ctx)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            torch.cuda.synchronize(self.device)
+            load_library().mpnl_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

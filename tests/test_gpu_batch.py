@@ -1,0 +1,151 @@
+"""Mixed-size batches in persistent launches (mpnl_batch_*): every unit's
+results in the mix equal the per-call path on that unit alone, with and
+without a captured CUDA graph; launch-shape knobs leave results unchanged."""
+import numpy as np
+import pytest
+
+from paper_2409_14355_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OUTS = ("R", "inv_diag", "perm", "Z", "paths", "hard", "llr", "ped2")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    from paper_2409_14355_gb300 import mpnl
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    mpnl.load_library()
+    d = torch.device("cuda", 0)
+    torch.cuda.set_device(d)
+    return d
+
+
+def _mpnl():
+    from paper_2409_14355_gb300 import mpnl
+    return mpnl
+
+
+def _specs():
+    # a scaled-down mixed batch plus a unit with more users than antennas
+    specs = inputs.mixed_units(14, seed=20240914, sc_scale=0.05)
+    specs.append(inputs.UnitSpec(4, 6, 16, 37, 64, 18.0, "iid", 99))
+    return specs
+
+
+def _fill(dev, specs):
+    mpnl = _mpnl()
+    units, slots = [], []
+    for k, u in enumerate(specs):
+        sl = inputs.unit_slot(u)
+        buf = mpnl.SlotBuffers(u.n_sc, 14, u.nr, u.nt, u.qam, u.n_pe, dev, mmse=True)
+        buf.H.copy_(torch.from_numpy(sl.H))
+        buf.Y.copy_(torch.from_numpy(sl.Y))
+        mmse_qr = u.nt > u.nr or k % 5 == 3
+        units.append((buf, sl.sigma2, mmse_qr, k % 3 != 1))
+        slots.append(sl)
+    return units, slots
+
+
+def _alone(dev, unit):
+    mpnl = _mpnl()
+    buf, sigma2, mmse_qr, mmse = unit
+    n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
+    ref = mpnl.SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, dev, mmse=mmse)
+    mpnl.run_slot(ref, buf.H, buf.Y, sigma2, mmse=mmse, mmse_qr=mmse_qr)
+    return ref
+
+
+def _assert_same(unit, ref, k):
+    buf, _, _, mmse = unit
+    names = OUTS + (("mmse_hard", "mmse_llr") if mmse else ())
+    for name in names:
+        a, b = getattr(buf, name), getattr(ref, name)
+        assert torch.equal(a, b), (k, name, buf.dims)
+
+
+def test_batch_results_equal_each_unit_alone(dev):
+    mpnl = _mpnl()
+    units, _ = _fill(dev, _specs())
+    batch = mpnl.Batch(units, dev)
+    batch.run()
+    mpnl.check_status()
+    torch.cuda.synchronize()
+    for k, unit in enumerate(units):
+        _assert_same(unit, _alone(dev, unit), k)
+    batch.close()
+
+
+def test_batch_graph_replay_follows_new_inputs(dev):
+    mpnl = _mpnl()
+    specs = _specs()
+    units, _ = _fill(dev, specs)
+    batch = mpnl.Batch(units, dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        batch.run(graph=True, stream=side)
+    side.synchronize()
+    for k, unit in enumerate(units):
+        _assert_same(unit, _alone(dev, unit), k)
+    # new received symbols in the same buffers: the replayed graph reads them
+    for k, (buf, _, _, _) in enumerate(units):
+        sl = inputs.unit_slot(inputs.UnitSpec(**{**specs[k].__dict__, "seed": specs[k].seed + 1}))
+        buf.Y.copy_(torch.from_numpy(sl.Y))
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        batch.run(graph=True, stream=side)
+    side.synchronize()
+    mpnl.check_status()
+    for k, unit in enumerate(units):
+        _assert_same(unit, _alone(dev, unit), k)
+    batch.close()
+
+
+def test_batch_rejects_bad_items(dev):
+    mpnl = _mpnl()
+    units, _ = _fill(dev, _specs()[:3])
+    bad = list(units)
+    buf, s2, mq, mm = bad[1]
+    bad[1] = (buf, -1.0, mq, mm)
+    with pytest.raises(mpnl.MpnlError) as e:
+        mpnl.Batch(bad, dev)
+    assert "item 1" in str(e.value)
+    b = mpnl.Batch(units, dev)
+    with pytest.raises(mpnl.MpnlError):
+        b.run(graph=True, stream=torch.cuda.default_stream(dev))  # legacy stream cannot be captured
+    b.close()
+
+
+@pytest.mark.parametrize("name,n_pe,n_sc", [("16x16-64qam-3276sc", 256, 40),
+                                            ("8x8-16qam-936sc", 64, 61),
+                                            ("4x4-qpsk-64sc", 16, 64)])
+def test_launch_knobs_do_not_change_results(dev, name, n_pe, n_sc):
+    mpnl = _mpnl()
+    sl = inputs.workload_slot(name, 0, n_sc=n_sc)
+    H = torch.from_numpy(sl.H).to(dev)
+    Y = torch.from_numpy(sl.Y).to(dev)
+    out = []
+    for sym in (2, 1):
+        for warps in (1, 2, 4):
+            t = mpnl.Tuning()
+            a, b, c = mpnl.problem_class(sl.nt, sl.qam, n_pe)
+            t.detect_sym[a][b][c] = sym
+            t.select_warps[a][b][c] = warps
+            mpnl.set_tuning(t)
+            try:
+                buf = mpnl.SlotBuffers(n_sc, 14, sl.nr, sl.nt, sl.qam, n_pe, dev, mmse=False)
+                mpnl.run_slot(buf, H, Y, sl.sigma2, mmse=False)
+                torch.cuda.synchronize()
+                out.append(buf)
+            finally:
+                mpnl.set_tuning(None)
+    for buf in out[1:]:
+        for name_ in ("paths", "hard", "llr", "ped2"):
+            assert torch.equal(getattr(buf, name_), getattr(out[0], name_)), name_
+    with pytest.raises(mpnl.MpnlError):
+        t = mpnl.Tuning()
+        t.select_warps[0][0][0] = 3
+        mpnl.set_tuning(t)
