@@ -59,6 +59,9 @@ def parse():
                     help="walk residuals in FP32 (mpnl_detect) or FP16 (mpnl_detect_mixed)")
     ap.add_argument("--no-sweep", action="store_true",
                     help="skip the N_pe / precision sweep reported beside the main line")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-size persistent batch measured beside the main line")
+    ap.add_argument("--mixed-units", type=int, default=64)
     ap.add_argument("--n-sc", type=int, default=None,
                     help="override the subcarrier count (smaller profiling cases)")
     return ap.parse_args()
@@ -396,6 +399,13 @@ def run_mpnl(args):
                           "detect_tflops": fl / (dms / 1e3) / 1e12})
             del b2
 
+    # ---- mixed-size batch (64 radio units of random sizes) in persistent
+    # launches under a CUDA graph, knobs from the autotuner, beside the same
+    # units launched one by one
+    mixed = None
+    if not args.no_mixed:
+        mixed = run_mixed(args, dev, rank)
+
     # ---- measured FP32 FMA throughput (probe kernel), beside the derived peak
     probe_tflops = None
     props = torch.cuda.get_device_properties(dev)
@@ -456,6 +466,7 @@ def run_mpnl(args):
                          "peak_measured_ffma": probe_tflops,
                          "frac_of_measured_ffma": achieved_tflops / probe_tflops},
             "sweep": sweep,
+            "mixed_batch": mixed,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else
                    {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -468,6 +479,58 @@ def run_mpnl(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_mixed(args, dev, rank):
+    import torch
+
+    from paper_2409_14355_gb300 import autotune, mpnl
+
+    units = inputs.mixed_units(args.mixed_units, seed=inputs.seed_for(inputs.MIXED_CONFIG) + rank)
+    tuning, report = autotune.tune(units, dev.index)
+    mpnl.set_tuning(tuning, dev.index)
+    try:
+        bufs = []
+        for u in units:
+            sl = inputs.unit_slot(u)
+            b = mpnl.SlotBuffers(u.n_sc, 14, u.nr, u.nt, u.qam, u.n_pe, dev, mmse=True)
+            b.H.copy_(torch.from_numpy(sl.H))
+            b.Y.copy_(torch.from_numpy(sl.Y))
+            bufs.append((b, sl.sigma2, False, True))
+        dets = sum(u.n_sc for u in units) * 14
+        batch = mpnl.Batch(bufs, dev)
+        side = torch.cuda.Stream(dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        steps = max(10, args.steps // 10)
+
+        def timed(fn):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b_ = torch.cuda.Event(enable_timing=True)
+            a.record(side)
+            for _ in range(steps):
+                fn()
+            b_.record(side)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b_) / steps
+
+        with torch.cuda.stream(side):
+            ms_graph = timed(lambda: batch.run(graph=True, stream=side))
+            ms_seq = timed(lambda: [mpnl.run_slot(b, b.H, b.Y, s2, mmse=mm, mmse_qr=mq)
+                                    for b, s2, mq, mm in bufs])
+        mpnl.check_status(dev.index)
+        batch.close()
+    finally:
+        mpnl.set_tuning(None, dev.index)
+    return {"workload": f"{len(units)} radio units, rx in {{4,8,16}}, users rx/2..rx, QAM "
+                        f"{{4,16,64}}, sc {{312,936,3276}}, N_pe 16..256 (uniform, seeded)",
+            "detections_per_step": dets, "value": dets / (ms_graph / 1e3), "unit": UNIT,
+            "ms_per_step": ms_graph, "steps": steps, "launch": "persistent per stage, CUDA graph",
+            "per_unit_launches_ms": ms_seq,
+            "tuning": autotune.to_dict(tuning),
+            "tuning_batch_ms": report["batch_ms"], "tuning_choice": report["batch_choice"]}
 
 
 def main():

@@ -244,11 +244,14 @@ void mpnl_batch_destroy(mpnl_batch *batch);
  * (0: n_pe < 256, 1: n_pe >= 256).  An entry of 0 means the built-in choice.
  * The package's autotuner measures the candidates and sets them. */
 typedef struct {
-    uint8_t detect_sym[3][3][2];    /* symbols per lane in the walk kernel: 1 or 2 (built-in 2) */
+    uint8_t detect_sym[3][3][2];    /* symbols per lane in the walk kernel: 1 or 2
+                                       (built-in: 1 for nt > 8, else 2) */
     uint8_t select_warps[3][3][2];  /* warps per subcarrier in the selection: 1, 2 or 4
                                        (built-in: 2 for n_pe >= 256, else 1) */
     uint8_t persistent_ctas_per_sm; /* CTAs per SM of the batch (persistent) walk launch: 1 or 2
                                        (built-in 2) */
+    uint8_t persistent_select_warps; /* warps per subcarrier of the batch selection launch:
+                                        1, 2 or 4 (built-in 2) */
 } mpnl_tuning;
 
 /* Set the knobs of this context (NULL restores the built-in choices);

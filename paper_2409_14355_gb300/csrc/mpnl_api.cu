@@ -50,7 +50,8 @@ int pe_class(int n_pe) { return n_pe >= 256 ? 1 : 0; }
 int tuned_sym(const mpnl_ctx *ctx, const mpnl_dims *d)
 {
     const int v = ctx->tuning.detect_sym[nt_class(d->nt)][qam_class(d->qam)][pe_class(d->n_pe)];
-    return v ? v : 2;
+    if (v) return v;
+    return d->nt > 8 ? 1 : 2;  // measured: one symbol per lane is faster at nt 9..16
 }
 
 int tuned_select_warps(const mpnl_ctx *ctx, const mpnl_dims *d)
@@ -258,11 +259,8 @@ int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
         if (lin) mm = std::max(mm, mpnl::mmse_warp_bytes(d->n_sym, d->nr, d->nt));
         order[i] = i;
     }
-    int sel_warps = 2;  // the persistent selection uses one group shape for every unit
-    {
-        const int v = ctx->tuning.select_warps[2][2][1];
-        if (v) sel_warps = v;
-    }
+    // the persistent selection uses one group shape for every unit
+    const int sel_warps = ctx->tuning.persistent_select_warps ? ctx->tuning.persistent_select_warps : 2;
     int det_ctas = ctx->tuning.persistent_ctas_per_sm ? ctx->tuning.persistent_ctas_per_sm : 2;
     while (det_ctas > 1 && (size_t)det_ctas * det > (size_t)dev_smem) --det_ctas;
     if (det > (size_t)dev_smem || pre * 4 > (size_t)dev_smem || mm * 4 > (size_t)dev_smem ||
@@ -546,6 +544,11 @@ int mpnl_set_tuning(mpnl_ctx *ctx, const mpnl_tuning *t)
     if (t->persistent_ctas_per_sm > 2)
         return fail(ctx, MPNL_ERR_INVALID_ARG, "persistent_ctas_per_sm=%d not in {0,1,2}",
                     t->persistent_ctas_per_sm);
+    {
+        const int w = t->persistent_select_warps;
+        if (w != 0 && w != 1 && w != 2 && w != 4)
+            return fail(ctx, MPNL_ERR_INVALID_ARG, "persistent_select_warps=%d not in {0,1,2,4}", w);
+    }
     ctx->tuning = *t;
     return MPNL_OK;
 }

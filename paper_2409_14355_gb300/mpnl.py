@@ -66,7 +66,8 @@ class Tuning(ctypes.Structure):
     0 = built-in choice.  Results never depend on them."""
     _fields_ = [("detect_sym", ((ctypes.c_uint8 * 2) * 3) * 3),
                 ("select_warps", ((ctypes.c_uint8 * 2) * 3) * 3),
-                ("persistent_ctas_per_sm", ctypes.c_uint8)]
+                ("persistent_ctas_per_sm", ctypes.c_uint8),
+                ("persistent_select_warps", ctypes.c_uint8)]
 
 
 class BatchItemC(ctypes.Structure):

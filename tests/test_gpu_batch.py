@@ -149,3 +149,20 @@ def test_launch_knobs_do_not_change_results(dev, name, n_pe, n_sc):
         t = mpnl.Tuning()
         t.select_warps[0][0][0] = 3
         mpnl.set_tuning(t)
+
+
+def test_autotuner_picks_valid_knobs(dev):
+    from paper_2409_14355_gb300 import autotune
+    mpnl = _mpnl()
+    units = inputs.mixed_units(4, seed=7, sc_scale=0.03)
+    t, report = autotune.tune(units, dev.index, reps=2)
+    d = autotune.to_dict(t)
+    assert d["persistent_ctas_per_sm"] in (1, 2)
+    for u in units:
+        a, b, c = mpnl.problem_class(u.nt, u.qam, u.n_pe)
+        assert d["detect_sym"][a][b][c] in (1, 2)
+        assert d["select_warps"][a][b][c] in (1, 2, 4)
+    assert d["persistent_select_warps"] in (1, 2, 4)
+    assert report["classes"] and report["batch_ms"]
+    # the tuner leaves the built-in knobs installed
+    assert autotune.to_dict(mpnl.get_tuning()) == autotune.to_dict(mpnl.Tuning())
