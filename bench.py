@@ -62,6 +62,10 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-size persistent batch measured beside the main line")
     ap.add_argument("--mixed-units", type=int, default=64)
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving-loop latency measurement beside the main line")
+    ap.add_argument("--serving-rus", type=int, default=200)
+    ap.add_argument("--serving-seconds", type=float, default=1.0)
     ap.add_argument("--n-sc", type=int, default=None,
                     help="override the subcarrier count (smaller profiling cases)")
     return ap.parse_args()
@@ -406,6 +410,12 @@ def run_mpnl(args):
     if not args.no_mixed:
         mixed = run_mixed(args, dev, rank)
 
+    # ---- serving loop: Poisson slot requests from many radio units,
+    # continuous batching, p50/p99 and deadline misses at 50-100% load
+    serving_res = None
+    if not args.no_serving:
+        serving_res = run_serving(args, dev)
+
     # ---- measured FP32 FMA throughput (probe kernel), beside the derived peak
     probe_tflops = None
     props = torch.cuda.get_device_properties(dev)
@@ -467,6 +477,7 @@ def run_mpnl(args):
                          "frac_of_measured_ffma": achieved_tflops / probe_tflops},
             "sweep": sweep,
             "mixed_batch": mixed,
+            "serving": serving_res,
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else
                    {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
@@ -531,6 +542,46 @@ def run_mixed(args, dev, rank):
             "per_unit_launches_ms": ms_seq,
             "tuning": autotune.to_dict(tuning),
             "tuning_batch_ms": report["batch_ms"], "tuning_choice": report["batch_choice"]}
+
+
+def run_serving(args, dev):
+    import torch
+
+    from paper_2409_14355_gb300 import serving
+
+    units = serving.serving_units(args.serving_rus)
+    server = serving.Server(dev, mem_budget=4 << 30, max_units_per_round=64)
+    payloads = {}
+    for k, u in enumerate(units):
+        sl = inputs.unit_slot(u)
+        server.register(serving.RU(k, u.nr, u.nt, u.qam, u.n_sc, u.n_pe, sl.sigma2),
+                        torch.from_numpy(sl.H))
+        payloads[k] = {"slot": [torch.from_numpy(sl.Y).pin_memory()],
+                       "channel": [torch.from_numpy(sl.H).pin_memory()]}
+    dets = {k: u.n_sc * 14 for k, u in enumerate(units)}
+    mean_dets = float(np.mean(list(dets.values())))
+    # capacity: every RU's slot offered at once, twice over (rounds stay full)
+    sat = [(0.0, k, "slot") for _ in range(2) for k in range(len(units))]
+    reqs = serving.run_trace(server, sat, payloads)
+    span = max(q.done for q in reqs) - min(q.arrival for q in reqs)
+    capacity = sum(dets[q.ru] for q in reqs) / span
+    loads = {}
+    for rho in (0.5, 0.75, 1.0):
+        rate = rho * capacity / mean_dets
+        trace = serving.poisson_trace(units, rate, args.serving_seconds, seed=int(100 * rho))
+        server.round_sizes.clear()
+        reqs = serving.run_trace(server, trace, payloads)
+        st = serving.latency_stats(reqs, dets_of=lambda q: dets[q.ru])
+        st.update(offered_detections_per_s=rho * capacity, mean_round=float(
+            np.mean(server.round_sizes)) if server.round_sizes else 0.0)
+        loads[str(rho)] = st
+    server.close()
+    n_big = sum(1 for u in units if (u.nr, u.nt, u.qam, u.n_sc) == (16, 16, 64, 3276))
+    return {"workload": f"{len(units)} radio units ({n_big} of them 16x16 64-QAM 3276 sc), "
+                        f"sizes as the mixed batch, Poisson slot requests, channel update every "
+                        f"8th slot of a unit", "deadline_ms": 0.5,
+            "capacity_detections_per_s": capacity, "seconds_per_load": args.serving_seconds,
+            "resident_state_MB": server.state_bytes / 1e6, "loads": loads}
 
 
 def main():

@@ -116,6 +116,24 @@ int mpnl_preprocess_mmse(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, co
                          float sigma2, void *R, float *inv_diag, uint8_t *perm, void *Z, void *ws,
                          void *stream);
 
+/* Sorted QR keeping Q: the per-unit state a serving loop holds while the
+ * channel stays the same over several slots (§III-B: H constant over a
+ * slot; the channel changes slowly at vehicular speeds).  sigma2 = 0: plain
+ * sorted QR (nt <= nr); sigma2 > 0: MMSE-extended (as mpnl_preprocess_mmse).
+ *   H               in   c64 [n_sc][nr][nt]
+ *   Q               out  c64 [n_sc][nr][nt]  antenna rows of Q, column l
+ *                        belongs to level l (the sorted order)
+ *   R, inv_diag, perm out as mpnl_preprocess (dims.n_sym is not used) */
+int mpnl_factor(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, float sigma2, void *Q,
+                void *R, float *inv_diag, uint8_t *perm, void *ws, void *stream);
+
+/* z = Q^H y for every symbol, from a stored Q (mpnl_factor); for the
+ * MMSE-extended factor this is Q_a^H [y; 0].
+ *   Q  in   c64 [n_sc][nr][nt];  Y  in  c64 [n_sc][n_sym][nr]
+ *   Z  out  c64 [n_sc][n_sym][nt] */
+int mpnl_qhy(mpnl_ctx *ctx, const mpnl_dims *dims, const void *Q, const void *Y, void *Z,
+             void *ws, void *stream);
+
 /* Position-vector pre-selection (§II: found "before any transmission
  * begins" from the channel; §III-B: N_p).  Per level, gamma_l = R_ll^2 /
  * sigma2 gives the square-QAM symbol-error probability Pe_l (floored at
@@ -194,6 +212,10 @@ typedef struct {
     mpnl_dims dims;
     float sigma2;
     int flags;            /* MPNL_ITEM_MMSE_QR, MPNL_ITEM_LINEAR_MMSE */
+    int stages;           /* MPNL_STAGE_* bits this unit takes part in; 0 = the whole path
+                             (sorted QR + z, selection, walks, and MMSE with the flag) */
+    void *Q;              /* c64 [n_sc][nr][nt]: written by the QR stage if not NULL,
+                             read by the MPNL_STAGE_QHY stage */
     const void *H;        /* in  c64 [n_sc][nr][nt] */
     const void *Y;        /* in  c64 [n_sc][n_sym][nr] */
     void *R;              /* out c64 [n_sc][nt(nt+1)/2]  (unit state, as mpnl_preprocess) */
@@ -211,12 +233,17 @@ typedef struct {
 #define MPNL_ITEM_MMSE_QR 1      /* MMSE-extended QR (mpnl_preprocess_mmse); allows nt > nr */
 #define MPNL_ITEM_LINEAR_MMSE 2  /* also run the linear MMSE baseline */
 
+/* Stages run in the order QR, selection, Q^H y, walks, MMSE.  A unit whose
+ * stages include MPNL_STAGE_QHY gets z from its stored Q; otherwise, if its
+ * stages include the walks, its QR stage also forms z; else (a channel
+ * update: QR and selection only) the QR stage only factors. */
 #define MPNL_STAGE_PREPROCESS 1
 #define MPNL_STAGE_SELECT 2
 #define MPNL_STAGE_DETECT 4
 #define MPNL_STAGE_MMSE 8
-#define MPNL_STAGES_ALL 15
 #define MPNL_RUN_GRAPH 16  /* capture the stages into a CUDA graph once, then replay it */
+#define MPNL_STAGE_QHY 32
+#define MPNL_STAGES_ALL 47
 
 typedef struct mpnl_batch mpnl_batch;
 
@@ -229,6 +256,13 @@ typedef struct mpnl_batch mpnl_batch;
  * MPNL_ERR_CUDA. */
 int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
                       mpnl_batch **batch);
+
+/* Replace the batch's units by `n_items` new ones (n_items <= the count it
+ * was created with), validated and ordered as by mpnl_batch_create, reusing
+ * its device allocations; cached graphs are dropped.  The previous work of
+ * the batch must have completed. */
+int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *batch, const mpnl_batch_item *items,
+                     int n_items);
 
 /* Enqueue the stages in `stages` (MPNL_STAGE_* bits, in pipeline order) on
  * `stream`; with MPNL_RUN_GRAPH the stream must not be the legacy default

@@ -141,14 +141,20 @@ int begin(mpnl_ctx *ctx)
 
 }  // namespace
 
+// Stage slots of a batch, in execution order.
+enum BatchStage { kBPre, kBSel, kBQhy, kBDet, kBMmse, kBStages };
+static const int kStageBit[kBStages] = {MPNL_STAGE_PREPROCESS, MPNL_STAGE_SELECT, MPNL_STAGE_QHY,
+                                        MPNL_STAGE_DETECT, MPNL_STAGE_MMSE};
+
 struct mpnl_batch {
     int device;
+    int capacity;
     int n_items;
     mpnl::BatchItem *d_items;  // schedule order
-    int *d_start;              // n_items + 1 prefix sums of n_sc
+    int *d_start;              // kBStages x (capacity + 1) prefix sums of n_sc per stage
     int *d_counters;           // one per stage
-    bool any_mmse;
-    int pre_warp_bytes, sel_group_bytes, mmse_warp_bytes;
+    int stage_units[kBStages];
+    int pre_warp_bytes, sel_group_bytes, qhy_warp_bytes, mmse_warp_bytes;
     size_t det_smem;
     int sel_warps, det_ctas;
     int sms;
@@ -160,27 +166,181 @@ namespace {
 // Rough per-subcarrier cost of a unit's walks, for largest-first ordering.
 double unit_cost(const mpnl_dims &d) { return (double)d.n_pe * d.nt * (d.nt + 4) * d.n_sym; }
 
+int item_stages(const mpnl_batch_item &it)
+{
+    if (it.stages) return it.stages;
+    return MPNL_STAGE_PREPROCESS | MPNL_STAGE_SELECT | MPNL_STAGE_DETECT |
+           ((it.flags & MPNL_ITEM_LINEAR_MMSE) ? MPNL_STAGE_MMSE : 0);
+}
+
+// Validate the items, order them largest first, and write the descriptors
+// and per-stage prefix sums into the batch's device arrays.
+int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n_items)
+{
+    int dev_smem = 0;
+    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    std::vector<mpnl::BatchItem> host(n_items);
+    std::vector<int> order(n_items), stg(n_items);
+    size_t pre = 16, sel = 16, qhy = 16, mm = 16, det = 16;
+    for (int i = 0; i < n_items; ++i) {
+        const mpnl_batch_item &it = items[i];
+        const mpnl_dims *d = &it.dims;
+        const bool mqr = it.flags & MPNL_ITEM_MMSE_QR, lin = it.flags & MPNL_ITEM_LINEAR_MMSE;
+        const int st_bits = item_stages(it);
+        stg[i] = st_bits;
+        const bool pre_on = st_bits & MPNL_STAGE_PREPROCESS, qhy_on = st_bits & MPNL_STAGE_QHY;
+        // the QR stage also forms z when the walks follow and no Q^H y stage does
+        const bool carry_y = pre_on && (st_bits & MPNL_STAGE_DETECT) && !qhy_on;
+        int st = check_dims(ctx, d, true, mqr ? kNrAugmented : kNrTall);
+        if (st == MPNL_OK) st = check_sigma2(ctx, it.sigma2);
+        if (st == MPNL_OK && (it.flags & ~(MPNL_ITEM_MMSE_QR | MPNL_ITEM_LINEAR_MMSE)))
+            st = fail(ctx, MPNL_ERR_INVALID_ARG, "unknown flags 0x%x", it.flags);
+        if (st == MPNL_OK && (st_bits & ~(MPNL_STAGES_ALL)))
+            st = fail(ctx, MPNL_ERR_INVALID_ARG, "unknown stage bits 0x%x", st_bits);
+        if (st == MPNL_OK && (st_bits & MPNL_STAGE_MMSE) && !lin)
+            st = fail(ctx, MPNL_ERR_INVALID_ARG, "MMSE stage without MPNL_ITEM_LINEAR_MMSE");
+        if (st == MPNL_OK && d->n_sc > 0) {
+            struct Need {
+                const void *p;
+                const char *name;
+                size_t align;
+                bool need;
+            } need[] = {
+                {it.H, "H", 8, pre_on || (st_bits & MPNL_STAGE_MMSE)},
+                {it.Y, "Y", 8, carry_y || qhy_on || (st_bits & MPNL_STAGE_MMSE)},
+                {it.Q, "Q", 8, qhy_on},
+                {it.R, "R", 8, pre_on || (st_bits & (MPNL_STAGE_SELECT | MPNL_STAGE_DETECT))},
+                {it.inv_diag, "inv_diag", 4, pre_on || (st_bits & MPNL_STAGE_DETECT)},
+                {it.perm, "perm", 1, pre_on || (st_bits & MPNL_STAGE_DETECT)},
+                {it.Z, "Z", 8, carry_y || qhy_on || (st_bits & MPNL_STAGE_DETECT)},
+                {it.paths, "paths", 1, (st_bits & (MPNL_STAGE_SELECT | MPNL_STAGE_DETECT)) != 0},
+                {it.hard, "hard", 1, (st_bits & MPNL_STAGE_DETECT) != 0},
+                {it.mmse_hard, "mmse_hard", 1, (st_bits & MPNL_STAGE_MMSE) != 0},
+            };
+            for (const Need &n : need)
+                if (st == MPNL_OK && n.need) st = check_ptr(ctx, n.p, n.align, n.name, false);
+            if (st == MPNL_OK) st = check_ptr(ctx, it.Q, 8, "Q", true);
+            if (st == MPNL_OK) st = check_ptr(ctx, it.llr, 4, "llr", true);
+            if (st == MPNL_OK) st = check_ptr(ctx, it.ped2, 4, "ped2", true);
+            if (st == MPNL_OK) st = check_ptr(ctx, it.mmse_llr, 4, "mmse_llr", true);
+        }
+        if (st != MPNL_OK) {
+            char msg[sizeof ctx->err];
+            snprintf(msg, sizeof msg, "item %d: %s", i, ctx->err);
+            return fail(ctx, st, "%s", msg);
+        }
+        mpnl::BatchItem &h = host[i];
+        h.n_sc = d->n_sc;
+        h.n_sym = d->n_sym;
+        h.nr = d->nr;
+        h.nt = d->nt;
+        h.qam = d->qam;
+        h.n_pe = d->n_pe;
+        h.sigma2 = it.sigma2;
+        h.sigma = mqr ? sqrtf(it.sigma2) : 0.f;
+        h.sym = tuned_sym(ctx, d);
+        h.mmse = (st_bits & MPNL_STAGE_MMSE) ? 1 : 0;
+        h.factor_sym = carry_y ? d->n_sym : 0;
+        h.Q = (float2 *)it.Q;
+        h.H = (const float2 *)it.H;
+        h.Y = (const float2 *)it.Y;
+        h.R = (float2 *)it.R;
+        h.inv_diag = it.inv_diag;
+        h.perm = it.perm;
+        h.Z = (float2 *)it.Z;
+        h.paths = it.paths;
+        h.hard = it.hard;
+        h.llr = it.llr;
+        h.ped2 = it.ped2;
+        h.mmse_hard = lin ? it.mmse_hard : nullptr;
+        h.mmse_llr = lin ? it.mmse_llr : nullptr;
+        if (pre_on) {
+            const int rows = mqr ? d->nr + d->nt : d->nr;
+            pre = std::max(pre, mpnl::preprocess_warp_bytes(h.factor_sym, rows, d->nt));
+        }
+        if (st_bits & MPNL_STAGE_SELECT) sel = std::max(sel, mpnl::select_group_bytes(d->n_pe));
+        if (qhy_on) qhy = std::max(qhy, mpnl::qhy_warp_bytes(d->n_sym, d->nr, d->nt));
+        if (st_bits & MPNL_STAGE_DETECT)
+            det = std::max(det, mpnl::detect_smem_bytes(d->nt, d->qam, d->n_pe, d->n_sym));
+        if (st_bits & MPNL_STAGE_MMSE) mm = std::max(mm, mpnl::mmse_warp_bytes(d->n_sym, d->nr, d->nt));
+        order[i] = i;
+    }
+    // the persistent selection uses one group shape for every unit
+    const int sel_warps =
+        ctx->tuning.persistent_select_warps ? ctx->tuning.persistent_select_warps : 2;
+    int det_ctas = ctx->tuning.persistent_ctas_per_sm ? ctx->tuning.persistent_ctas_per_sm : 2;
+    while (det_ctas > 1 && (size_t)det_ctas * det > (size_t)dev_smem) --det_ctas;
+    if (det > (size_t)dev_smem || pre * 4 > (size_t)dev_smem || mm * 4 > (size_t)dev_smem ||
+        qhy * 4 > (size_t)dev_smem || sel * (4 / sel_warps) > (size_t)dev_smem)
+        return fail(ctx, MPNL_ERR_UNSUPPORTED, "a unit needs more shared memory than one SM has");
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return unit_cost(items[a].dims) > unit_cost(items[c].dims);
+    });
+    const int cap1 = b->capacity + 1;
+    std::vector<mpnl::BatchItem> sorted(n_items);
+    std::vector<int> start((size_t)kBStages * cap1, 0);
+    for (int k = 0; k < n_items; ++k) {
+        sorted[k] = host[order[k]];
+        const int bits = stg[order[k]];
+        for (int q = 0; q < kBStages; ++q)
+            start[q * cap1 + k + 1] = start[q * cap1 + k] + ((bits & kStageBit[q]) ? sorted[k].n_sc : 0);
+    }
+    for (int q = 0; q < kBStages; ++q) {
+        b->stage_units[q] = start[q * cap1 + n_items];
+        // entries past n_items repeat the total (the kernels read start[n_items])
+        for (int k = n_items + 1; k < cap1; ++k) start[q * cap1 + k] = start[q * cap1 + n_items];
+    }
+    cudaError_t e = cudaMemcpy(b->d_items, sorted.data(), sizeof(mpnl::BatchItem) * n_items,
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(b->d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(ctx, "batch descriptors", e);
+    b->n_items = n_items;
+    b->pre_warp_bytes = (int)pre;
+    b->sel_group_bytes = (int)sel;
+    b->qhy_warp_bytes = (int)qhy;
+    b->mmse_warp_bytes = (int)mm;
+    b->det_smem = det;
+    b->sel_warps = sel_warps;
+    b->det_ctas = det_ctas;
+    for (int k = 0; k <= MPNL_STAGES_ALL; ++k)
+        if (b->graph[k]) {
+            cudaGraphExecDestroy(b->graph[k]);
+            b->graph[k] = nullptr;
+        }
+    return MPNL_OK;
+}
+
 int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, 4 * sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(b->d_counters, 0, kBStages * sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(ctx, "batch counter reset", e);
-    if (stages & MPNL_STAGE_PREPROCESS) {
-        e = mpnl::launch_preprocess_batch(b->d_items, b->d_start, b->n_items, b->d_counters + 0,
+    const int cap1 = b->capacity + 1;
+    const int *start[kBStages];
+    for (int q = 0; q < kBStages; ++q) start[q] = b->d_start + q * cap1;
+    const int n = b->n_items;
+    if ((stages & MPNL_STAGE_PREPROCESS) && b->stage_units[kBPre]) {
+        e = mpnl::launch_preprocess_batch(b->d_items, start[kBPre], n, b->d_counters + kBPre,
                                           b->pre_warp_bytes, b->sms * 4, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch preprocess launch", e);
     }
-    if (stages & MPNL_STAGE_SELECT) {
-        e = mpnl::launch_select_batch(b->d_items, b->d_start, b->n_items, b->d_counters + 1,
+    if ((stages & MPNL_STAGE_SELECT) && b->stage_units[kBSel]) {
+        e = mpnl::launch_select_batch(b->d_items, start[kBSel], n, b->d_counters + kBSel,
                                       b->sel_group_bytes, b->sel_warps, b->sms * 4, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch select launch", e);
     }
-    if (stages & MPNL_STAGE_DETECT) {
-        e = mpnl::launch_detect_batch(b->d_items, b->d_start, b->n_items, b->d_counters + 2,
+    if ((stages & MPNL_STAGE_QHY) && b->stage_units[kBQhy]) {
+        e = mpnl::launch_qhy_batch(b->d_items, start[kBQhy], n, b->d_counters + kBQhy,
+                                   b->qhy_warp_bytes, b->sms * 4, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "batch qhy launch", e);
+    }
+    if ((stages & MPNL_STAGE_DETECT) && b->stage_units[kBDet]) {
+        e = mpnl::launch_detect_batch(b->d_items, start[kBDet], n, b->d_counters + kBDet,
                                       ctx->status, b->det_smem, b->sms * b->det_ctas, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch detect launch", e);
     }
-    if ((stages & MPNL_STAGE_MMSE) && b->any_mmse) {
-        e = mpnl::launch_mmse_batch(b->d_items, b->d_start, b->n_items, b->d_counters + 3,
+    if ((stages & MPNL_STAGE_MMSE) && b->stage_units[kBMmse]) {
+        e = mpnl::launch_mmse_batch(b->d_items, start[kBMmse], n, b->d_counters + kBMmse,
                                     b->mmse_warp_bytes, b->sms * 4, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch mmse launch", e);
     }
@@ -198,109 +358,39 @@ int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
     if (!out) return fail(ctx, MPNL_ERR_INVALID_ARG, "batch is NULL");
     *out = nullptr;
     if (n_items < 1 || !items) return fail(ctx, MPNL_ERR_INVALID_ARG, "need at least one item");
-    int dev_smem = 0, sms = 0;
-    cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device);
-    std::vector<mpnl::BatchItem> host(n_items);
-    std::vector<int> order(n_items);
-    size_t pre = 16, sel = 16, mm = 16, det = 16;
-    bool any_mmse = false;
-    for (int i = 0; i < n_items; ++i) {
-        const mpnl_batch_item &it = items[i];
-        const mpnl_dims *d = &it.dims;
-        const bool mqr = it.flags & MPNL_ITEM_MMSE_QR, lin = it.flags & MPNL_ITEM_LINEAR_MMSE;
-        int st = check_dims(ctx, d, true, mqr ? kNrAugmented : kNrTall);
-        if (st == MPNL_OK) st = check_sigma2(ctx, it.sigma2);
-        if (st == MPNL_OK && (it.flags & ~(MPNL_ITEM_MMSE_QR | MPNL_ITEM_LINEAR_MMSE)))
-            st = fail(ctx, MPNL_ERR_INVALID_ARG, "unknown flags 0x%x", it.flags);
-        if (st == MPNL_OK && d->n_sc > 0) {
-            const void *req[] = {it.H, it.Y, it.R, it.inv_diag, it.perm, it.Z, it.paths, it.hard};
-            const char *nm[] = {"H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard"};
-            const size_t al[] = {8, 8, 8, 4, 1, 8, 1, 1};
-            for (int k = 0; k < 8 && st == MPNL_OK; ++k) st = check_ptr(ctx, req[k], al[k], nm[k], false);
-            if (st == MPNL_OK) st = check_ptr(ctx, it.llr, 4, "llr", true);
-            if (st == MPNL_OK) st = check_ptr(ctx, it.ped2, 4, "ped2", true);
-            if (st == MPNL_OK && lin) st = check_ptr(ctx, it.mmse_hard, 1, "mmse_hard", false);
-            if (st == MPNL_OK && lin) st = check_ptr(ctx, it.mmse_llr, 4, "mmse_llr", true);
-        }
-        if (st != MPNL_OK) {
-            char msg[sizeof ctx->err];
-            snprintf(msg, sizeof msg, "item %d: %s", i, ctx->err);
-            return fail(ctx, st, "%s", msg);
-        }
-        mpnl::BatchItem &b = host[i];
-        b.n_sc = d->n_sc;
-        b.n_sym = d->n_sym;
-        b.nr = d->nr;
-        b.nt = d->nt;
-        b.qam = d->qam;
-        b.n_pe = d->n_pe;
-        b.sigma2 = it.sigma2;
-        b.sigma = mqr ? sqrtf(it.sigma2) : 0.f;
-        b.sym = tuned_sym(ctx, d);
-        b.mmse = lin ? 1 : 0;
-        b.H = (const float2 *)it.H;
-        b.Y = (const float2 *)it.Y;
-        b.R = (float2 *)it.R;
-        b.inv_diag = it.inv_diag;
-        b.perm = it.perm;
-        b.Z = (float2 *)it.Z;
-        b.paths = it.paths;
-        b.hard = it.hard;
-        b.llr = it.llr;
-        b.ped2 = it.ped2;
-        b.mmse_hard = lin ? it.mmse_hard : nullptr;
-        b.mmse_llr = lin ? it.mmse_llr : nullptr;
-        any_mmse = any_mmse || lin;
-        const int rows = mqr ? d->nr + d->nt : d->nr;
-        pre = std::max(pre, mpnl::preprocess_warp_bytes(d->n_sym, rows, d->nt));
-        sel = std::max(sel, mpnl::select_group_bytes(d->n_pe));
-        det = std::max(det, mpnl::detect_smem_bytes(d->nt, d->qam, d->n_pe, d->n_sym));
-        if (lin) mm = std::max(mm, mpnl::mmse_warp_bytes(d->n_sym, d->nr, d->nt));
-        order[i] = i;
-    }
-    // the persistent selection uses one group shape for every unit
-    const int sel_warps = ctx->tuning.persistent_select_warps ? ctx->tuning.persistent_select_warps : 2;
-    int det_ctas = ctx->tuning.persistent_ctas_per_sm ? ctx->tuning.persistent_ctas_per_sm : 2;
-    while (det_ctas > 1 && (size_t)det_ctas * det > (size_t)dev_smem) --det_ctas;
-    if (det > (size_t)dev_smem || pre * 4 > (size_t)dev_smem || mm * 4 > (size_t)dev_smem ||
-        sel * (4 / sel_warps) > (size_t)dev_smem)
-        return fail(ctx, MPNL_ERR_UNSUPPORTED, "a unit needs more shared memory than one SM has");
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-        return unit_cost(items[a].dims) > unit_cost(items[c].dims);
-    });
-    std::vector<mpnl::BatchItem> sorted(n_items);
-    std::vector<int> start(n_items + 1, 0);
-    for (int k = 0; k < n_items; ++k) {
-        sorted[k] = host[order[k]];
-        start[k + 1] = start[k] + sorted[k].n_sc;
-    }
     mpnl_batch *b = (mpnl_batch *)calloc(1, sizeof(mpnl_batch));
     if (!b) return fail(ctx, MPNL_ERR_CUDA, "out of host memory");
     b->device = ctx->device;
-    b->n_items = n_items;
-    b->any_mmse = any_mmse;
-    b->pre_warp_bytes = (int)pre;
-    b->sel_group_bytes = (int)sel;
-    b->mmse_warp_bytes = (int)mm;
-    b->det_smem = det;
-    b->sel_warps = sel_warps;
-    b->det_ctas = det_ctas;
+    b->capacity = n_items;
     b->sms = sms > 0 ? sms : 1;
     cudaError_t e = cudaMalloc(&b->d_items, sizeof(mpnl::BatchItem) * n_items);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_start, sizeof(int) * (n_items + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * 4);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_items, sorted.data(), sizeof(mpnl::BatchItem) * n_items,
-                       cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_start, start.data(), sizeof(int) * (n_items + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_start, sizeof(int) * kBStages * (n_items + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * kBStages);
     if (e != cudaSuccess) {
         mpnl_batch_destroy(b);
         return cuda_fail(ctx, "batch create", e);
     }
+    const int rc = fill_batch(ctx, b, items, n_items);
+    if (rc != MPNL_OK) {
+        mpnl_batch_destroy(b);
+        return rc;
+    }
     *out = b;
     return MPNL_OK;
+}
+
+int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n_items)
+{
+    MPNL_TRY(begin(ctx));
+    if (!b) return fail(ctx, MPNL_ERR_INVALID_ARG, "batch is NULL");
+    if (b->device != ctx->device)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "batch lives on device %d, context on %d", b->device,
+                    ctx->device);
+    if (n_items < 1 || n_items > b->capacity || !items)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "n_items=%d outside 1..%d", n_items, b->capacity);
+    return fill_batch(ctx, b, items, n_items);
 }
 
 int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *b, int stages, void *stream)
@@ -408,7 +498,8 @@ static int preprocess_impl(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, con
     MPNL_TRY(check_ptr(ctx, Z, 8, "Z", false));
     cudaError_t e = mpnl::launch_preprocess(d->n_sc, d->n_sym, d->nr, d->nt, sigma,
                                             (const float2 *)H, (const float2 *)Y, (float2 *)R,
-                                            inv_diag, perm, (float2 *)Z, (cudaStream_t)stream);
+                                            inv_diag, perm, (float2 *)Z, nullptr,
+                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(ctx, "preprocess launch", e);
     return MPNL_OK;
 }
@@ -431,6 +522,43 @@ int mpnl_preprocess_mmse(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const
     MPNL_TRY(check_dims(ctx, d, false, kNrAugmented));
     MPNL_TRY(check_sigma2(ctx, sigma2));
     return preprocess_impl(ctx, d, H, Y, sqrtf(sigma2), R, inv_diag, perm, Z, stream);
+}
+
+int mpnl_factor(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, float sigma2, void *Q, void *R,
+                float *inv_diag, uint8_t *perm, void *ws, void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    const bool mmse = sigma2 != 0.0f;
+    MPNL_TRY(check_dims(ctx, d, false, mmse ? kNrAugmented : kNrTall));
+    if (mmse) MPNL_TRY(check_sigma2(ctx, sigma2));
+    if (d->n_sc == 0) return MPNL_OK;
+    MPNL_TRY(check_ptr(ctx, H, 8, "H", false));
+    MPNL_TRY(check_ptr(ctx, Q, 8, "Q", false));
+    MPNL_TRY(check_ptr(ctx, R, 8, "R", false));
+    MPNL_TRY(check_ptr(ctx, inv_diag, 4, "inv_diag", false));
+    MPNL_TRY(check_ptr(ctx, perm, 1, "perm", false));
+    cudaError_t e = mpnl::launch_preprocess(d->n_sc, 0, d->nr, d->nt, mmse ? sqrtf(sigma2) : 0.f,
+                                            (const float2 *)H, nullptr, (float2 *)R, inv_diag, perm,
+                                            nullptr, (float2 *)Q, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "factor launch", e);
+    return MPNL_OK;
+}
+
+int mpnl_qhy(mpnl_ctx *ctx, const mpnl_dims *d, const void *Q, const void *Y, void *Z, void *ws,
+             void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_dims(ctx, d, false, kNrAny));
+    if (d->n_sc == 0) return MPNL_OK;
+    MPNL_TRY(check_ptr(ctx, Q, 8, "Q", false));
+    MPNL_TRY(check_ptr(ctx, Y, 8, "Y", false));
+    MPNL_TRY(check_ptr(ctx, Z, 8, "Z", false));
+    cudaError_t e = mpnl::launch_qhy(d->n_sc, d->n_sym, d->nr, d->nt, (const float2 *)Q,
+                                     (const float2 *)Y, (float2 *)Z, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "qhy launch", e);
+    return MPNL_OK;
 }
 
 int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, float sigma2,

@@ -25,9 +25,15 @@ struct DetArgs {
 };
 
 // sigma > 0: MMSE-extended factorisation of [H; sigma I] (mpnl_preprocess_mmse).
+// n_sym may be 0 (factor only; Y and Z unused); Q (nullable) receives the
+// antenna rows of Q, [n_sc][nr][nt].
 cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *H,
                               const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,
-                              float2 *Z, cudaStream_t stream);
+                              float2 *Z, float2 *Q, cudaStream_t stream);
+
+// z = Q^H y from a stored Q (mpnl_qhy).
+cudaError_t launch_qhy(int n_sc, int n_sym, int nr, int nt, const float2 *Q, const float2 *Y,
+                       float2 *Z, cudaStream_t stream);
 
 // warps: threads of one subcarrier's merges, 32 x (1, 2 or 4).
 cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,
@@ -54,13 +60,16 @@ cudaError_t launch_ffma_probe(int n_blocks, int iters, float *out, cudaStream_t 
 double ffma_probe_flops(int n_blocks, int iters);
 
 // One radio unit's slot in a batch (mpnl_batch_*), as the persistent kernels
-// read it from device memory.  The work items of a batch are its units'
-// subcarriers; start[] holds their prefix sums (n_items + 1 entries).
+// read it from device memory.  The work items of a stage are the
+// subcarriers of the units taking part in it; the stage's start[] holds
+// their prefix sums (n_items + 1 entries, zero-length for units outside).
 struct BatchItem {
     int n_sc, n_sym, nr, nt, qam, n_pe;
     float sigma2, sigma;  // sigma > 0: MMSE-extended QR (sigma = sqrt(sigma2))
     int sym;              // symbols per lane of the walk kernel
     int mmse;             // also run the linear MMSE baseline
+    int factor_sym;       // symbols the sorted-QR stage carries along (n_sym or 0)
+    float2 *Q;            // antenna rows of Q (nullable; required by the Q^H y stage)
     const float2 *H, *Y;
     float2 *R;
     float *inv_diag;
@@ -89,6 +98,9 @@ __device__ __forceinline__ int find_item(const int *start, int n_items, int w)
 // Persistent batch launchers: `counter` is a device int reset to 0 before
 // the launch; shared memory per worker is the maximum over the batch.
 size_t preprocess_warp_bytes(int n_sym, int nr, int nt);
+size_t qhy_warp_bytes(int n_sym, int nr, int nt);
+cudaError_t launch_qhy_batch(const BatchItem *items, const int *start, int n_items,
+                             int *counter, int warp_bytes, int grid, cudaStream_t stream);
 cudaError_t launch_preprocess_batch(const BatchItem *items, const int *start, int n_items,
                                     int *counter, int warp_bytes, int grid, cudaStream_t stream);
 size_t select_group_bytes(int n_pe);

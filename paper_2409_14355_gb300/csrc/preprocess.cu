@@ -64,7 +64,8 @@ __device__ __forceinline__ void sqrd_qhy_warp(int sc, int n_sym, int nr, int nt,
                                            float2 *__restrict__ Rp,
                                            float *__restrict__ inv_diag,
                                            uint8_t *__restrict__ perm_out,
-                                           float2 *__restrict__ Z, int base_off)
+                                           float2 *__restrict__ Z, float2 *__restrict__ Qout,
+                                           int base_off)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = smem_raw + base_off;
@@ -140,6 +141,8 @@ __device__ __forceinline__ void sqrd_qhy_warp(int sc, int n_sym, int nr, int nt,
             placed = true;
         }
         __syncwarp();
+        if (Qout != nullptr)  // column i of Q (antenna rows only), for z = Q^H y later
+            for (int r = lane; r < nr; r += 32) Qout[((size_t)sc * nr + r) * nt + i] = sQ[r];
 #pragma unroll
         for (int cs = 0; cs < CS; ++cs) {
             const int c = lane + 32 * cs;
@@ -197,19 +200,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32)
 sqrd_qhy_kernel(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *__restrict__ H,
                 const float2 *__restrict__ Y, float2 *__restrict__ Rp,
                 float *__restrict__ inv_diag, uint8_t *__restrict__ perm_out,
-                float2 *__restrict__ Z)
+                float2 *__restrict__ Z, float2 *__restrict__ Qout)
 {
     const int warp = threadIdx.x >> 5;
     const int sc = blockIdx.x * kWarpsPerCta + warp;
     if (sc >= n_sc) return;  // only __syncwarp inside: per-warp early exit is safe
     const WarpSmem L = warp_smem_layout(nr, nt, n_sym);
-    sqrd_qhy_warp<NR, CS>(sc, n_sym, nr, nt, sigma, H, Y, Rp, inv_diag, perm_out, Z,
+    sqrd_qhy_warp<NR, CS>(sc, n_sym, nr, nt, sigma, H, Y, Rp, inv_diag, perm_out, Z, Qout,
                           warp * L.bytes);
 }
 
 // Persistent variant over a batch of radio units of mixed sizes: every warp
 // takes (unit, subcarrier) work items from a global counter until the batch
-// is exhausted and runs the instance that fits the unit's sizes.
+// is exhausted and runs the instance that fits the unit's sizes.  `start`
+// holds this stage's prefix sums (units outside the stage have none).
 __global__ void __launch_bounds__(kWarpsPerCta * 32)
 sqrd_qhy_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ start,
                       int n_items, int *__restrict__ counter, int warp_bytes)
@@ -225,16 +229,17 @@ sqrd_qhy_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict
         const int i = find_item(start, n_items, w);
         const BatchItem &it = items[i];
         const int sc = w - start[i];
+        const int ns = it.factor_sym;  // 0: factor only (no symbols ride along)
         const int rows = it.sigma > 0.f ? it.nr + it.nt : it.nr;
-        const bool two = it.nt + it.n_sym > 32;
+        const bool two = it.nt + ns > 32;
 #define MPNL_PRE_W(NRV)                                                                          \
     do {                                                                                         \
         if (two)                                                                                 \
-            sqrd_qhy_warp<NRV, 2>(sc, it.n_sym, it.nr, it.nt, it.sigma, it.H, it.Y, it.R,        \
-                                  it.inv_diag, it.perm, it.Z, base);                             \
+            sqrd_qhy_warp<NRV, 2>(sc, ns, it.nr, it.nt, it.sigma, it.H, it.Y, it.R, it.inv_diag, \
+                                  it.perm, it.Z, it.Q, base);                                    \
         else                                                                                     \
-            sqrd_qhy_warp<NRV, 1>(sc, it.n_sym, it.nr, it.nt, it.sigma, it.H, it.Y, it.R,        \
-                                  it.inv_diag, it.perm, it.Z, base);                             \
+            sqrd_qhy_warp<NRV, 1>(sc, ns, it.nr, it.nt, it.sigma, it.H, it.Y, it.R, it.inv_diag, \
+                                  it.perm, it.Z, it.Q, base);                                    \
     } while (0)
         if (rows <= 4) MPNL_PRE_W(4);
         else if (rows <= 8) MPNL_PRE_W(8);
@@ -244,10 +249,69 @@ sqrd_qhy_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict
     }
 }
 
+// z = Q^H y for every symbol of one subcarrier, by one warp: Q (nr x nt)
+// and the symbols' y staged in shared memory with coalesced loads, then
+// lane k computes outputs (symbol, level) k, k + 32, ... as nr-term complex
+// dot products (FP32, explicit FMAs).
+__device__ __forceinline__ void qhy_warp(int sc, int n_sym, int nr, int nt,
+                                         const float2 *__restrict__ Q,
+                                         const float2 *__restrict__ Y, float2 *__restrict__ Z,
+                                         int base_off)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *sQ = reinterpret_cast<float2 *>(smem_raw + base_off);
+    float2 *sY = sQ + nr * nt;
+    const int lane = threadIdx.x & 31;
+    const float2 *gQ = Q + (size_t)sc * nr * nt;
+    const float2 *gY = Y + (size_t)sc * n_sym * nr;
+    for (int k = lane; k < nr * nt; k += 32) sQ[k] = gQ[k];
+    for (int k = lane; k < n_sym * nr; k += 32) sY[k] = gY[k];
+    __syncwarp();
+    float2 *gZ = Z + (size_t)sc * n_sym * nt;
+    for (int k = lane; k < n_sym * nt; k += 32) {
+        const int s = k / nt, i = k - s * nt;
+        float zx = 0.f, zy = 0.f;  // conj(q) . y
+        for (int r = 0; r < nr; ++r) {
+            const float2 q = sQ[r * nt + i], y = sY[s * nr + r];
+            zx = fmaf(q.x, y.x, fmaf(q.y, y.y, zx));
+            zy = fmaf(q.x, y.y, fmaf(-q.y, y.x, zy));
+        }
+        gZ[k] = make_float2(zx, zy);
+    }
+    __syncwarp();  // the region may be reused for the warp's next subcarrier
+}
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+qhy_kernel(int n_sc, int n_sym, int nr, int nt, const float2 *__restrict__ Q,
+           const float2 *__restrict__ Y, float2 *__restrict__ Z, int warp_bytes)
+{
+    const int warp = threadIdx.x >> 5;
+    const int sc = blockIdx.x * kWarpsPerCta + warp;
+    if (sc >= n_sc) return;
+    qhy_warp(sc, n_sym, nr, nt, Q, Y, Z, warp * warp_bytes);
+}
+
+__global__ void __launch_bounds__(kWarpsPerCta * 32)
+qhy_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ start,
+                 int n_items, int *__restrict__ counter, int warp_bytes)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int total = start[n_items];
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const int i = find_item(start, n_items, w);
+        const BatchItem &it = items[i];
+        qhy_warp(w - start[i], it.n_sym, it.nr, it.nt, it.Q, it.Y, it.Z, warp * warp_bytes);
+    }
+}
+
 template <int NR, int CS>
 cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *H,
                        const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm, float2 *Z,
-                       cudaStream_t stream)
+                       float2 *Q, cudaStream_t stream)
 {
     const WarpSmem L = warp_smem_layout(nr, nt, n_sym);
     const size_t smem = (size_t)L.bytes * kWarpsPerCta;
@@ -257,13 +321,43 @@ cudaError_t launch_tpl(int n_sc, int n_sym, int nr, int nt, float sigma, const f
     }
     const int grid = (n_sc + kWarpsPerCta - 1) / kWarpsPerCta;
     sqrd_qhy_kernel<NR, CS><<<grid, kWarpsPerCta * 32, smem, stream>>>(n_sc, n_sym, nr, nt, sigma,
-                                                                       H, Y, R, inv_diag, perm, Z);
+                                                                       H, Y, R, inv_diag, perm, Z,
+                                                                       Q);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 size_t preprocess_warp_bytes(int n_sym, int nr, int nt) { return warp_smem_layout(nr, nt, n_sym).bytes; }
+
+size_t qhy_warp_bytes(int n_sym, int nr, int nt)
+{
+    return (((size_t)nr * nt + (size_t)n_sym * nr) * 8 + 15) & ~(size_t)15;
+}
+
+cudaError_t launch_qhy(int n_sc, int n_sym, int nr, int nt, const float2 *Q, const float2 *Y,
+                       float2 *Z, cudaStream_t stream)
+{
+    if (n_sc == 0) return cudaSuccess;
+    const int wb = (int)qhy_warp_bytes(n_sym, nr, nt);
+    const size_t smem = (size_t)wb * kWarpsPerCta;
+    cudaError_t e = allow_dynamic_smem(qhy_kernel, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (n_sc + kWarpsPerCta - 1) / kWarpsPerCta;
+    qhy_kernel<<<grid, kWarpsPerCta * 32, smem, stream>>>(n_sc, n_sym, nr, nt, Q, Y, Z, wb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_qhy_batch(const BatchItem *items, const int *start, int n_items,
+                             int *counter, int warp_bytes, int grid, cudaStream_t stream)
+{
+    const size_t smem = (size_t)warp_bytes * kWarpsPerCta;
+    cudaError_t e = allow_dynamic_smem(qhy_batch_kernel, smem);
+    if (e != cudaSuccess) return e;
+    qhy_batch_kernel<<<grid, kWarpsPerCta * 32, smem, stream>>>(items, start, n_items, counter,
+                                                                warp_bytes);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_preprocess_batch(const BatchItem *items, const int *start, int n_items,
                                     int *counter, int warp_bytes, int grid, cudaStream_t stream)
@@ -278,14 +372,14 @@ cudaError_t launch_preprocess_batch(const BatchItem *items, const int *start, in
 
 cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, float sigma, const float2 *H,
                               const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,
-                              float2 *Z, cudaStream_t stream)
+                              float2 *Z, float2 *Q, cudaStream_t stream)
 {
     if (n_sc == 0) return cudaSuccess;
     const bool two = nt + n_sym > 32;
     const int rows = sigma > 0.f ? nr + nt : nr;
 #define MPNL_PRE(NRV)                                                                          \
-    return two ? launch_tpl<NRV, 2>(n_sc, n_sym, nr, nt, sigma, H, Y, R, inv_diag, perm, Z, stream) \
-               : launch_tpl<NRV, 1>(n_sc, n_sym, nr, nt, sigma, H, Y, R, inv_diag, perm, Z, stream)
+    return two ? launch_tpl<NRV, 2>(n_sc, n_sym, nr, nt, sigma, H, Y, R, inv_diag, perm, Z, Q, stream) \
+               : launch_tpl<NRV, 1>(n_sc, n_sym, nr, nt, sigma, H, Y, R, inv_diag, perm, Z, Q, stream)
     if (rows <= 4) MPNL_PRE(4);
     if (rows <= 8) MPNL_PRE(8);
     if (rows <= 16) MPNL_PRE(16);

@@ -38,9 +38,11 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_preprocess", "mpnl_preprocess_mmse", "mpnl_select_paths", "mpnl_detect",
             "mpnl_detect_mixed",
             "mpnl_linear_mmse", "mpnl_check_status", "mpnl_probe_ffma", "mpnl_set_tuning",
-            "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy")
+            "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy",
+            "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE = 1, 2
-STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGES_ALL = 1, 2, 4, 8, 15
+STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
+STAGES_ALL = 47
 RUN_GRAPH = 16
 PRECISIONS = ("fp32", "fp16")
 
@@ -72,7 +74,8 @@ class Tuning(ctypes.Structure):
 
 class BatchItemC(ctypes.Structure):
     """mpnl_batch_item."""
-    _fields_ = [("dims", Dims), ("sigma2", ctypes.c_float), ("flags", ctypes.c_int)] + [
+    _fields_ = [("dims", Dims), ("sigma2", ctypes.c_float), ("flags", ctypes.c_int),
+                ("stages", ctypes.c_int), ("Q", ctypes.c_void_p)] + [
         (n, ctypes.c_void_p) for n in ("H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard",
                                        "llr", "ped2", "mmse_hard", "mmse_llr")]
 
@@ -121,6 +124,12 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_batch_create.argtypes = [P, ctypes.POINTER(BatchItemC), I,
                                           ctypes.POINTER(ctypes.c_void_p)]
         lib.mpnl_batch_create.restype = I
+        lib.mpnl_batch_reset.argtypes = [P, P, ctypes.POINTER(BatchItemC), I]
+        lib.mpnl_batch_reset.restype = I
+        lib.mpnl_factor.argtypes = [P, D, P, F, P, P, P, P, P, P]
+        lib.mpnl_factor.restype = I
+        lib.mpnl_qhy.argtypes = [P, D, P, P, P, P, P]
+        lib.mpnl_qhy.restype = I
         lib.mpnl_batch_run.argtypes = [P, P, I, P]
         lib.mpnl_batch_run.restype = I
         lib.mpnl_batch_destroy.argtypes = [P]
@@ -209,6 +218,41 @@ def preprocess(H: torch.Tensor, Y: torch.Tensor, out=None, sigma2: float | None 
                                       _stream(dev))
     _raise(st, ctx)
     return R, inv_diag, perm, Z
+
+
+def factor(H: torch.Tensor, sigma2: float | None = None, out=None):
+    """Sorted QR keeping Q: returns (Q [n_sc][nr][nt], R, inv_diag, perm).
+    With sigma2 the MMSE-extended factor of [H; sqrt(sigma2) I]."""
+    dev = _dev_of(H)
+    n_sc, nr, nt = H.shape
+    _need(H, torch.complex64, (n_sc, nr, nt), "H")
+    if out is None:
+        out = (torch.empty((n_sc, nr, nt), dtype=torch.complex64, device=dev),
+               torch.empty((n_sc, nt * (nt + 1) // 2), dtype=torch.complex64, device=dev),
+               torch.empty((n_sc, nt), dtype=torch.float32, device=dev),
+               torch.empty((n_sc, nt), dtype=torch.uint8, device=dev))
+    Q, R, inv_diag, perm = out
+    ctx = context(dev.index)
+    d = Dims(n_sc, 1, nr, nt, 4, 1)
+    st = load_library().mpnl_factor(ctx, ctypes.byref(d), _ptr(H), float(sigma2 or 0.0), _ptr(Q),
+                                    _ptr(R), _ptr(inv_diag), _ptr(perm), None, _stream(dev))
+    _raise(st, ctx)
+    return Q, R, inv_diag, perm
+
+
+def qhy(Q: torch.Tensor, Y: torch.Tensor, out=None):
+    """z = Q^H y for every symbol (Q from factor)."""
+    dev = _dev_of(Q)
+    n_sc, nr, nt = Q.shape
+    n_sym = Y.shape[1]
+    _need(Q, torch.complex64, (n_sc, nr, nt), "Q")
+    _need(Y, torch.complex64, (n_sc, n_sym, nr), "Y")
+    Z = out if out is not None else torch.empty((n_sc, n_sym, nt), dtype=torch.complex64, device=dev)
+    ctx = context(dev.index)
+    d = Dims(n_sc, n_sym, nr, nt, 4, 1)
+    _raise(load_library().mpnl_qhy(ctx, ctypes.byref(d), _ptr(Q), _ptr(Y), _ptr(Z), None,
+                                   _stream(dev)), ctx)
+    return Z
 
 
 def select_paths(R: torch.Tensor, sigma2: float, qam: int, n_pe: int, nt: int, out=None):
@@ -379,33 +423,57 @@ def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
     return out
 
 
+def batch_item(dims, sigma2: float, flags: int = 0, stages: int = 0, **arrays) -> BatchItemC:
+    """One mpnl_batch_item from device tensors given by field name (H, Y, Q,
+    R, inv_diag, perm, Z, paths, hard, llr, ped2, mmse_hard, mmse_llr)."""
+    it = BatchItemC()
+    it.dims = Dims(*dims)
+    it.sigma2 = float(sigma2)
+    it.flags = flags
+    it.stages = stages
+    for name, t in arrays.items():
+        if t is not None:
+            setattr(it, name, t.data_ptr())
+    return it
+
+
 class Batch:
     """A mixed-size batch of radio units' slots run by the persistent
-    launches (mpnl_batch_*).  Each unit is a SlotBuffers whose H and Y the
-    caller fills; ``run`` writes its R/perm/Z/paths state and its results.
-    Units are given as (buffers, sigma2, mmse_qr, mmse) tuples."""
+    launches (mpnl_batch_*).  Units are SlotBuffers given as (buffers,
+    sigma2, mmse_qr, mmse) tuples, whose H and Y the caller fills; ``run``
+    writes their R/perm/Z/paths state and results.  Alternatively pass
+    ready-made BatchItemC items (``items=``) that reference tensors the
+    caller keeps alive."""
 
-    def __init__(self, units, device=None):
+    def __init__(self, units=(), device=None, items=None):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
         self.units = list(units)
-        items = (BatchItemC * len(self.units))()
-        for k, (buf, sigma2, mmse_qr, mmse) in enumerate(self.units):
-            n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
-            it = items[k]
-            it.dims = Dims(n_sc, n_sym, nr, nt, qam, n_pe)
-            it.sigma2 = float(sigma2)
-            it.flags = (ITEM_MMSE_QR if mmse_qr else 0) | (ITEM_LINEAR_MMSE if mmse else 0)
-            for name in ("H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard", "llr", "ped2"):
-                setattr(it, name, getattr(buf, name).data_ptr())
-            if mmse:
-                it.mmse_hard = buf.mmse_hard.data_ptr()
-                it.mmse_llr = buf.mmse_llr.data_ptr()
+        if items is None:
+            items = [self._unit_item(u) for u in self.units]
+        arr = (BatchItemC * len(items))(*items)
         self._ctx = context(self.device.index)
         h = ctypes.c_void_p()
-        _raise(load_library().mpnl_batch_create(self._ctx, items, len(self.units), ctypes.byref(h)),
+        _raise(load_library().mpnl_batch_create(self._ctx, arr, len(items), ctypes.byref(h)),
                self._ctx)
         self._h = h
+        self.capacity = len(items)
+
+    @staticmethod
+    def _unit_item(unit) -> BatchItemC:
+        buf, sigma2, mmse_qr, mmse = unit
+        flags = (ITEM_MMSE_QR if mmse_qr else 0) | (ITEM_LINEAR_MMSE if mmse else 0)
+        names = ("H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard", "llr", "ped2")
+        arrays = {n: getattr(buf, n) for n in names}
+        if mmse:
+            arrays.update(mmse_hard=buf.mmse_hard, mmse_llr=buf.mmse_llr)
+        return batch_item(buf.dims, sigma2, flags, 0, **arrays)
+
+    def reset(self, items) -> None:
+        """Replace the units (at most the creation count), reusing the
+        device allocations."""
+        arr = (BatchItemC * len(items))(*items)
+        _raise(load_library().mpnl_batch_reset(self._ctx, self._h, arr, len(items)), self._ctx)
 
     def run(self, stages: int = STAGES_ALL, graph: bool = False, stream=None) -> None:
         """Enqueue the stages on `stream` (default: the current stream; a
@@ -426,4 +494,3 @@ class Batch:
             self.close()
         except Exception:
             pass
-

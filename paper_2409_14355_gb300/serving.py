@@ -1,0 +1,382 @@
+"""Serving loop for slot-detection requests from many radio units (RUs).
+
+An O-RAN distributed unit serves many RUs (§I, §IV: one DU, many RUs, the
+compute allocated where the load is).  Each RU has its own antenna, user,
+QAM and subcarrier counts.  This module keeps every RU's channel state on
+the device -- the antenna rows of Q, R, 1/R_ll, the sorted order and the
+N_pe position vectors, all computed from the channel alone when the RU
+reports a new channel (§II: the candidate positions are found before the
+data arrives) -- and serves two kinds of requests:
+
+  channel  new H for an RU: sorted QR keeping Q, then the path selection;
+  slot     the received symbols Y of one slot: z = Q^H y, the N_pe walks,
+           hard decisions and max-log LLRs.
+
+Continuous batching: requests wait in arrival order; whenever one of the
+`max_inflight` round slots is free, the waiting requests that fit the
+device-memory budget (their input, scratch and output buffers) form a round,
+which runs as one mixed-size batch in the persistent launches (QR, selection,
+Q^H y, walks) on its own stream.  Requests arriving while rounds run join the
+next round, and up to `max_inflight` rounds overlap on the device.  A round
+copies its inputs from pinned host memory, runs, copies hard decisions and
+LLRs back, and records an event; a request's latency is the time from its
+arrival to the completion of its round, against the 0.5 ms slot deadline
+(§III-B).  An RU's channel update never shares the device with a round that
+still reads the RU's previous state: it waits for those rounds to finish,
+and the RU's later slots wait behind it (they may join its round: the
+stages run in order, QR and selection before Q^H y and the walks).
+
+Nothing here does arithmetic of the detector: all of it runs in the CUDA
+kernels behind the C ABI (mpnl.py).
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import inputs, mpnl
+
+DEADLINE_S = 0.5e-3
+
+
+@dataclass
+class RU:
+    """One radio unit and its device-resident channel state."""
+    ru_id: int
+    nr: int
+    nt: int
+    qam: int
+    n_sc: int
+    n_pe: int
+    sigma2: float
+    mmse_qr: bool = False
+    n_sym: int = 14
+    state: dict = field(default_factory=dict)   # Q, R, inv_diag, perm, paths (device)
+    busy_rounds: set = field(default_factory=set)
+    blocked: bool = False                       # a channel update is waiting
+
+    @property
+    def dims(self):
+        return (self.n_sc, self.n_sym, self.nr, self.nt, self.qam, self.n_pe)
+
+    @property
+    def cost(self) -> float:
+        """Relative work of one slot (the walks dominate)."""
+        return float(self.n_sc * self.n_sym * self.n_pe * self.nt * (self.nt + 4))
+
+    def state_bytes(self) -> int:
+        n_sc, nr, nt = self.n_sc, self.nr, self.nt
+        return n_sc * (nr * nt * 8 + nt * (nt + 1) // 2 * 8 + nt * 4 + nt + self.n_pe * nt)
+
+
+@dataclass
+class Request:
+    rid: int
+    ru: int
+    kind: str                 # "slot" or "channel"
+    arrival: float            # seconds since the start of the run
+    payload: torch.Tensor     # pinned host: Y [n_sc][n_sym][nr] or H [n_sc][nr][nt]
+    admitted: float = -1.0
+    done: float = -1.0
+    round_id: int = -1
+    hard: torch.Tensor | None = None   # pinned host results (slot requests)
+    llr: torch.Tensor | None = None
+
+
+def request_bytes(ru: RU, kind: str, llr: bool) -> int:
+    """Device bytes a request holds while it is in flight."""
+    n = ru.n_sc
+    if kind == "channel":
+        return n * ru.nr * ru.nt * 8
+    b = n * ru.n_sym * (ru.nr * 8 + ru.nt * 8 + ru.nt + 8)
+    if llr:
+        b += n * ru.n_sym * ru.nt * mpnl.BITS[ru.qam] * 4
+    return b
+
+
+class _Round:
+    def __init__(self, server, slot_index: int):
+        self.server = server
+        self.index = slot_index
+        self._stream = None
+        self.batch = None
+        self.requests: list[Request] = []
+        self.buffers: list = []
+        self.bytes = 0
+        self.event = None
+        self.round_id = -1
+
+    @property
+    def stream(self):
+        if self._stream is None:  # created on first use (the loop's logic needs no GPU)
+            self._stream = torch.cuda.Stream(self.server.device)
+        return self._stream
+
+    @property
+    def free(self) -> bool:
+        return self.event is None
+
+
+class Server:
+    """Continuous-batching serving loop over device-resident RU state."""
+
+    def __init__(self, device=None, mem_budget: int = 2 << 30, max_units_per_round: int = 64,
+                 max_inflight: int = 4, llr: bool = True, starve_s: float = 5e-3):
+        self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
+                       else torch.device(device))
+        self.mem_budget = int(mem_budget)
+        self.max_units = int(max_units_per_round)
+        self.llr = llr
+        self.starve_s = starve_s
+        self.rus: dict[int, RU] = {}
+        self.state_bytes = 0
+        self.in_use = 0
+        self.waiting: collections.deque[Request] = collections.deque()
+        self.rounds = [_Round(self, k) for k in range(max_inflight)]
+        self.completed: list[Request] = []
+        self.n_rounds = 0
+        self.t0 = time.perf_counter()
+        self.peak_in_use = 0
+        self.round_sizes: list[int] = []
+
+    # ---- RU registration (setup, synchronous)
+    def register(self, ru: RU, H: torch.Tensor) -> None:
+        """Allocate the RU's resident state and compute it from channel H."""
+        dev = self.device
+        n_sc, nr, nt = ru.n_sc, ru.nr, ru.nt
+        st = dict(Q=torch.empty((n_sc, nr, nt), dtype=torch.complex64, device=dev),
+                  R=torch.empty((n_sc, nt * (nt + 1) // 2), dtype=torch.complex64, device=dev),
+                  inv_diag=torch.empty((n_sc, nt), dtype=torch.float32, device=dev),
+                  perm=torch.empty((n_sc, nt), dtype=torch.uint8, device=dev),
+                  paths=torch.empty((n_sc, ru.n_pe, nt), dtype=torch.uint8, device=dev))
+        ru.state = st
+        Hd = H.to(dev)
+        mpnl.factor(Hd, ru.sigma2 if ru.mmse_qr else None,
+                    out=(st["Q"], st["R"], st["inv_diag"], st["perm"]))
+        mpnl.select_paths(st["R"], ru.sigma2, ru.qam, ru.n_pe, nt, out=st["paths"])
+        torch.cuda.synchronize(dev)
+        self.rus[ru.ru_id] = ru
+        self.state_bytes += ru.state_bytes()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0
+
+    def submit(self, req: Request) -> None:
+        self.waiting.append(req)
+
+    # ---- the loop
+    def poll(self) -> int:
+        """Retire finished rounds; returns how many finished."""
+        n = 0
+        for r in self.rounds:
+            if r.event is not None and r.event.query():
+                t = self.now()
+                for q in r.requests:
+                    q.done = t
+                    self.completed.append(q)
+                    self.rus[q.ru].busy_rounds.discard(r.round_id)
+                self.in_use -= r.bytes
+                r.requests, r.buffers, r.bytes, r.event = [], [], 0, None
+                n += 1
+        return n
+
+    def _form(self):
+        """Pick waiting requests for one round: smallest radio units first
+        (their slots can still meet the deadline), requests that waited
+        longer than `starve_s` before all others, within the memory budget
+        and the per-RU ordering rules."""
+        chosen, nbytes = [], 0
+        budget = self.mem_budget - self.in_use
+        blocked_rus = set()
+        keep = collections.deque()
+        now = self.now()
+        order = sorted(self.waiting, key=lambda q: (now - q.arrival <= self.starve_s,
+                                                    self.rus[q.ru].cost, q.arrival))
+        self.waiting = collections.deque(order)
+        while self.waiting and len(chosen) < self.max_units:
+            q = self.waiting.popleft()
+            ru = self.rus[q.ru]
+            need = request_bytes(ru, q.kind, self.llr)
+            ok = q.ru not in blocked_rus and nbytes + need <= budget
+            if ok and q.kind == "channel":
+                # the update rewrites the RU's state: no round in flight may
+                # still read it, and no earlier slot of the RU may share this
+                # round (its stages would see the new state)
+                ok = not ru.busy_rounds and not any(c.ru == q.ru for c in chosen)
+            if ok:
+                chosen.append(q)
+                nbytes += need
+            else:
+                keep.append(q)
+                blocked_rus.add(q.ru)  # the RU's later requests stay behind (per-RU order)
+        keep.extend(self.waiting)
+        self.waiting = collections.deque(sorted(keep, key=lambda q: q.arrival))
+        return chosen, nbytes
+
+    def _launch(self, r: _Round) -> bool:
+        reqs, nbytes = self._form()
+        if not reqs:
+            return False
+        dev = self.device
+        t_adm = self.now()
+        items, bufs = [], []
+        # channel updates first in the item list (the batch runs stages in
+        # order, so a slot of the same RU in this round sees the new state)
+        for q in sorted(reqs, key=lambda q: q.kind != "channel"):
+            ru = self.rus[q.ru]
+            st = ru.state
+            q.admitted = t_adm
+            if q.kind == "channel":
+                H = torch.empty((ru.n_sc, ru.nr, ru.nt), dtype=torch.complex64, device=dev)
+                H.copy_(q.payload, non_blocking=True)
+                flags = mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0
+                items.append(mpnl.batch_item(ru.dims, ru.sigma2, flags,
+                                             mpnl.STAGE_PREPROCESS | mpnl.STAGE_SELECT, H=H, **st))
+                bufs.append((q, H))
+            else:
+                n_sc, n_sym, nr, nt = ru.n_sc, ru.n_sym, ru.nr, ru.nt
+                Y = torch.empty((n_sc, n_sym, nr), dtype=torch.complex64, device=dev)
+                Y.copy_(q.payload, non_blocking=True)
+                Z = torch.empty((n_sc, n_sym, nt), dtype=torch.complex64, device=dev)
+                hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, device=dev)
+                llr = (torch.empty((n_sc, n_sym, nt, mpnl.BITS[ru.qam]), dtype=torch.float32,
+                                   device=dev) if self.llr else None)
+                items.append(mpnl.batch_item(ru.dims, ru.sigma2,
+                                             mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0,
+                                             mpnl.STAGE_QHY | mpnl.STAGE_DETECT, Y=Y, Z=Z,
+                                             hard=hard, llr=llr, Q=st["Q"], R=st["R"],
+                                             inv_diag=st["inv_diag"], perm=st["perm"],
+                                             paths=st["paths"]))
+                bufs.append((q, Y, Z, hard, llr))
+        with torch.cuda.stream(r.stream):
+            # inputs were queued on the current stream: order the round after them
+            r.stream.wait_stream(torch.cuda.current_stream(dev))
+            if r.batch is None:
+                # created once with room for a full round (padded with copies
+                # of this round's items, replaced right away)
+                pad = (items * (self.max_units // len(items) + 1))[:self.max_units]
+                r.batch = mpnl.Batch(items=pad, device=dev)
+            r.batch.reset(items)
+            r.batch.run(mpnl.STAGE_PREPROCESS | mpnl.STAGE_SELECT | mpnl.STAGE_QHY |
+                        mpnl.STAGE_DETECT, stream=r.stream)
+            for b in bufs:
+                q = b[0]
+                if q.kind == "slot":
+                    _, Y, Z, hard, llr = b
+                    q.hard = torch.empty(hard.shape, dtype=hard.dtype, pin_memory=True)
+                    q.hard.copy_(hard, non_blocking=True)
+                    if llr is not None:
+                        q.llr = torch.empty(llr.shape, dtype=llr.dtype, pin_memory=True)
+                        q.llr.copy_(llr, non_blocking=True)
+                for t in b[1:]:
+                    if t is not None:
+                        t.record_stream(r.stream)
+            r.event = torch.cuda.Event()
+            r.event.record(r.stream)
+        self.n_rounds += 1
+        r.round_id = self.n_rounds
+        for q in reqs:
+            q.round_id = r.round_id
+            self.rus[q.ru].busy_rounds.add(r.round_id)
+        r.requests, r.buffers, r.bytes = reqs, bufs, nbytes
+        self.in_use += nbytes
+        self.peak_in_use = max(self.peak_in_use, self.in_use)
+        self.round_sizes.append(len(reqs))
+        return True
+
+    def step(self) -> None:
+        self.poll()
+        for r in self.rounds:
+            if not self.waiting:
+                break
+            if r.free:
+                self._launch(r)
+
+    def drain(self, timeout_s: float = 60.0) -> None:
+        t_end = time.perf_counter() + timeout_s
+        while (self.waiting or any(not r.free for r in self.rounds)) and time.perf_counter() < t_end:
+            self.step()
+
+    def close(self) -> None:
+        torch.cuda.synchronize(self.device)
+        for r in self.rounds:
+            if r.batch is not None:
+                r.batch.close()
+                r.batch = None
+
+
+# ---------------------------------------------------------------------------
+# workload: RUs, payloads and Poisson arrivals
+# ---------------------------------------------------------------------------
+def serving_units(n_rus: int = 200, big_fraction: float = 0.2, seed: int | None = None,
+                  sc_scale: float = 1.0) -> list[inputs.UnitSpec]:
+    """RU sizes as in the mixed batch; a fraction of them 16x16 64-QAM with
+    3276 subcarriers (N_pe drawn as in the mixed batch)."""
+    units = inputs.mixed_units(n_rus, seed=seed, sc_scale=sc_scale, config=5)
+    rng = np.random.Generator(np.random.PCG64(inputs.seed_for(5, 1) if seed is None else seed + 1))
+    big = rng.choice(n_rus, size=int(round(big_fraction * n_rus)), replace=False)
+    for k in big:
+        u = units[k]
+        units[k] = inputs.UnitSpec(16, 16, 64, max(1, int(round(3276 * sc_scale))),
+                                   u.n_pe, 20.0 + 6.0 * rng.random(), u.channel, u.seed)
+    return units
+
+
+def poisson_trace(units, rate_per_s: float, duration_s: float, coherence_slots: int = 8,
+                  seed: int = 0):
+    """Arrival times and RUs of slot requests (Poisson, RU chosen uniformly);
+    every `coherence_slots`-th slot of an RU is preceded by a channel update
+    arriving with it."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = rng.poisson(rate_per_s * duration_s)
+    times = np.sort(rng.uniform(0.0, duration_s, size=n))
+    rus = rng.integers(0, len(units), size=n)
+    count = np.zeros(len(units), dtype=np.int64)
+    out = []
+    for t, k in zip(times, rus):
+        if count[k] % coherence_slots == coherence_slots - 1:
+            out.append((float(t), int(k), "channel"))
+        out.append((float(t), int(k), "slot"))
+        count[k] += 1
+    return out
+
+
+def run_trace(server: Server, trace, payloads, t_limit_s: float = 120.0):
+    """Replay `trace` in real time: requests are submitted at their arrival
+    times (relative to the start) and the loop runs until all complete.
+    payloads[ru][kind] -> list of pinned host tensors, used cyclically."""
+    use = collections.defaultdict(int)
+    reqs = []
+    server.t0 = time.perf_counter()
+    i = 0
+    t_end = time.perf_counter() + t_limit_s
+    while (i < len(trace) or server.waiting or any(not r.free for r in server.rounds)) \
+            and time.perf_counter() < t_end:
+        now = server.now()
+        while i < len(trace) and trace[i][0] <= now:
+            t, k, kind = trace[i]
+            pl = payloads[k][kind]
+            q = Request(len(reqs), k, kind, t, pl[use[(k, kind)] % len(pl)])
+            use[(k, kind)] += 1
+            reqs.append(q)
+            server.submit(q)
+            i += 1
+        server.step()
+    return reqs
+
+
+def latency_stats(reqs, deadline_s: float = DEADLINE_S, dets_of=None) -> dict:
+    slots = [q for q in reqs if q.kind == "slot" and q.done >= 0]
+    lat = np.array([q.done - q.arrival for q in slots]) if slots else np.zeros(0)
+    out = {"requests": len(reqs), "slots_done": len(slots),
+           "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+           "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+           "miss_rate": float(np.mean(lat > deadline_s)) if len(lat) else None}
+    if dets_of is not None and slots:
+        span = max(q.done for q in slots) - min(q.arrival for q in slots)
+        out["detections_per_s"] = sum(dets_of(q) for q in slots) / max(span, 1e-9)
+    return out

@@ -1,0 +1,124 @@
+"""Serving loop: every slot request's results in the continuous-batching mix
+equal the per-call path (factor, selection, Q^H y, walks) on that RU alone
+with the channel that applied to it; z from a stored Q matches the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_14355_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def dev():
+    from paper_2409_14355_gb300 import mpnl
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    mpnl.load_library()
+    d = torch.device("cuda", 0)
+    torch.cuda.set_device(d)
+    return d
+
+
+@pytest.mark.parametrize("nr,nt,qam,n_sc,mmse_qr", [(8, 8, 16, 37, False), (16, 16, 64, 9, False),
+                                                     (7, 12, 4, 21, True), (4, 2, 64, 33, False)])
+def test_factor_and_stored_q_match_oracle(dev, nr, nt, qam, n_sc, mmse_qr):
+    from paper_2409_14355_gb300 import mpnl
+    from tests import _parity as P
+    sl = inputs.make_slot(nr, nt, qam, n_sc, 14, 18.0, "iid", 0.3, 500 + nr + nt)
+    H = torch.from_numpy(sl.H).to(dev)
+    Y = torch.from_numpy(sl.Y).to(dev)
+    Q, R, inv_diag, perm = mpnl.factor(H, sl.sigma2 if mmse_qr else None)
+    Z = mpnl.qhy(Q, Y)
+    torch.cuda.synchronize()
+    H64 = sl.H.astype(np.complex128)
+    Y64 = sl.Y.astype(np.complex128)
+    if mmse_qr:
+        Rr, pr, Zr, gap = P.oracle_front_mmse(H64, Y64, sl.sigma2)
+        Ha = np.concatenate([H64, np.broadcast_to(np.sqrt(sl.sigma2) * np.eye(nt),
+                                                  (n_sc, nt, nt))], axis=1)
+    else:
+        Rr, pr, Zr, gap = P.oracle_front(H64, Y64)
+        Ha = H64
+    kappa = np.linalg.cond(Ha)
+    ok = np.all(gap > 1e-4, axis=1)
+    assert ok.mean() > 0.8
+    pg = perm.cpu().numpy()
+    np.testing.assert_array_equal(pg[ok], pr[ok])
+    Rg = P.unpack_upper(R.cpu().numpy().astype(np.complex128), nt)
+    Zg = Z.cpu().numpy().astype(np.complex128)
+    Qg = Q.cpu().numpy().astype(np.complex128)
+    for c in np.flatnonzero(ok):
+        assert np.max(np.abs(Rg[c] - Rr[c])) <= 100 * U32 * kappa[c] * np.linalg.norm(Ha[c])
+        ynorm = np.max(np.linalg.norm(Y64[c], axis=-1))
+        assert np.max(np.abs(Zg[c] - Zr[c])) <= 100 * U32 * kappa[c] * ynorm
+        # the stored antenna rows of Q reproduce H P = Q R on those rows
+        Hp = H64[c][:, pg[c]]
+        assert np.max(np.abs(Qg[c] @ Rg[c] - Hp)) <= 100 * U32 * kappa[c] * np.linalg.norm(Ha[c])
+
+
+def _alone(dev, ru, H, Y):
+    from paper_2409_14355_gb300 import mpnl
+    Q, R, inv_diag, perm = mpnl.factor(H.to(dev), ru.sigma2 if ru.mmse_qr else None)
+    paths = mpnl.select_paths(R, ru.sigma2, ru.qam, ru.n_pe, ru.nt)
+    Z = mpnl.qhy(Q, Y.to(dev))
+    hard, llr, _ = mpnl.detect(R, inv_diag, perm, paths, Z, ru.sigma2, ru.qam)
+    return hard.cpu(), llr.cpu()
+
+
+def test_serving_results_equal_each_request_alone(dev):
+    from paper_2409_14355_gb300 import mpnl, serving
+    specs = inputs.mixed_units(6, seed=31, sc_scale=0.02)
+    specs[1] = inputs.UnitSpec(4, 6, 16, 29, 64, 18.0, "iid", 77)   # more users than antennas
+    server = serving.Server(dev, mem_budget=64 << 20, max_units_per_round=8, max_inflight=2)
+    payloads, first_H = {}, {}
+    for k, u in enumerate(specs):
+        sl = inputs.unit_slot(u)
+        ru = serving.RU(k, u.nr, u.nt, u.qam, u.n_sc, u.n_pe, sl.sigma2, mmse_qr=u.nt > u.nr)
+        server.register(ru, torch.from_numpy(sl.H))
+        first_H[k] = torch.from_numpy(sl.H)
+        alt = [inputs.unit_slot(inputs.UnitSpec(**{**u.__dict__, "seed": u.seed + j}))
+               for j in (1, 2)]
+        payloads[k] = {"slot": [torch.from_numpy(a.Y).pin_memory() for a in [sl] + alt],
+                       "channel": [torch.from_numpy(a.H).pin_memory() for a in alt]}
+    trace = serving.poisson_trace(specs, rate_per_s=40000.0, duration_s=0.002,
+                                  coherence_slots=3, seed=3)
+    assert any(kind == "channel" for _, _, kind in trace)
+    reqs = serving.run_trace(server, trace, payloads)
+    server.close()
+    mpnl.check_status()
+    assert all(q.done >= 0 for q in reqs)
+    assert max(server.round_sizes) > 1  # requests were batched together
+    current = dict(first_H)
+    n_cmp = 0
+    for q in reqs:  # per-RU order is submission order
+        if q.kind == "channel":
+            current[q.ru] = q.payload
+            continue
+        ru = server.rus[q.ru]
+        hard, llr = _alone(dev, ru, current[q.ru], q.payload)
+        assert torch.equal(q.hard, hard), (q.rid, q.ru)
+        assert torch.equal(q.llr, llr), (q.rid, q.ru)
+        n_cmp += 1
+    assert n_cmp > 20
+
+
+def test_memory_budget_limits_rounds(dev):
+    from paper_2409_14355_gb300 import serving
+    specs = inputs.mixed_units(3, seed=8, sc_scale=0.05)
+    server = serving.Server(dev, mem_budget=1, max_units_per_round=8, max_inflight=1)
+    payloads = {}
+    for k, u in enumerate(specs):
+        sl = inputs.unit_slot(u)
+        server.register(serving.RU(k, u.nr, u.nt, u.qam, u.n_sc, u.n_pe, sl.sigma2),
+                        torch.from_numpy(sl.H))
+        payloads[k] = {"slot": [torch.from_numpy(sl.Y).pin_memory()], "channel": []}
+    # a budget smaller than any request admits nothing: the loop gives up at its limit
+    trace = [(0.0, 0, "slot")]
+    reqs = serving.run_trace(server, trace, payloads, t_limit_s=0.2)
+    assert reqs[0].done < 0 and server.n_rounds == 0
+    server.close()

@@ -1,0 +1,83 @@
+"""Host logic of the serving loop (no GPU): arrivals, request sizes and the
+admission rules (memory budget, per-RU order, channel updates)."""
+import numpy as np
+import torch
+
+from paper_2409_14355_gb300 import inputs, serving
+
+
+def _server(budget=1 << 30, units=4):
+    s = serving.Server(device="cpu", mem_budget=budget, max_units_per_round=8)
+    for k in range(units):
+        s.rus[k] = serving.RU(k, 4, 4, 16, 12 + k, 16, 0.1)
+    return s
+
+
+def _req(rid, ru, kind):
+    return serving.Request(rid, ru, kind, rid * 1e-6, torch.zeros(1))
+
+
+def test_poisson_trace_is_sorted_with_periodic_channel_updates():
+    units = inputs.mixed_units(5, seed=2, sc_scale=0.01)
+    tr = serving.poisson_trace(units, 5000.0, 0.1, coherence_slots=4, seed=1)
+    times = [t for t, _, _ in tr]
+    assert times == sorted(times)
+    per = {}
+    for t, k, kind in tr:
+        per.setdefault(k, []).append(kind)
+    for kinds in per.values():
+        slots = 0
+        for a, kind in enumerate(kinds):
+            if kind == "channel":
+                assert slots % 4 == 3 and kinds[a + 1] == "slot"
+            else:
+                slots += 1
+    n_slots = sum(1 for _, _, k in tr if k == "slot")
+    assert abs(n_slots - 500) < 5 * np.sqrt(500)
+
+
+def test_request_bytes_counts_inputs_scratch_and_outputs():
+    ru = serving.RU(0, 8, 4, 64, 10, 16, 0.1)
+    slot = serving.request_bytes(ru, "slot", llr=True)
+    assert slot == 10 * 14 * (8 * 8 + 4 * 8 + 4 + 8) + 10 * 14 * 4 * 6 * 4
+    assert serving.request_bytes(ru, "slot", llr=False) == slot - 10 * 14 * 4 * 6 * 4
+    assert serving.request_bytes(ru, "channel", llr=True) == 10 * 8 * 4 * 8
+
+
+def test_admission_keeps_per_ru_order_and_budget():
+    s = _server()
+    reqs = [_req(0, 3, "slot"), _req(1, 0, "slot"), _req(2, 3, "slot"), _req(3, 1, "slot")]
+    for q in reqs:
+        s.submit(q)
+    chosen, nbytes = s._form()
+    # smallest RUs first; RU 3's two slots stay in arrival order
+    assert [q.rid for q in chosen] == [1, 3, 0, 2]
+    assert nbytes == sum(serving.request_bytes(s.rus[q.ru], q.kind, True) for q in chosen)
+    # a budget for one request admits one, the rest wait in arrival order
+    s = _server(budget=serving.request_bytes(serving.RU(0, 4, 4, 16, 13, 16, 0.1), "slot", True))
+    for q in reqs:
+        s.submit(q)
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [1]
+    assert [q.rid for q in s.waiting] == [0, 2, 3]
+
+
+def test_channel_update_waits_for_rounds_reading_the_state():
+    s = _server()
+    s.rus[2].busy_rounds.add(7)
+    for q in (_req(0, 2, "channel"), _req(1, 2, "slot"), _req(2, 0, "slot")):
+        s.submit(q)
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [2]          # RU 2 is held behind its update
+    s.rus[2].busy_rounds.clear()
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [0, 1]       # update, then its slot, same round
+
+
+def test_update_never_shares_a_round_with_an_earlier_slot_of_its_ru():
+    s = _server()
+    for q in (_req(0, 1, "slot"), _req(1, 1, "channel"), _req(2, 1, "slot")):
+        s.submit(q)
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [0]
+    assert [q.rid for q in s.waiting] == [1, 2]
