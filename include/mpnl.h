@@ -134,6 +134,21 @@ int mpnl_factor(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, float sigma
 int mpnl_qhy(mpnl_ctx *ctx, const mpnl_dims *dims, const void *Q, const void *Y, void *Z,
              void *ws, void *stream);
 
+/* FP64 re-factorisation of ill-conditioned channels.  Run after
+ * mpnl_preprocess / mpnl_preprocess_mmse (sigma2 > 0 selects the latter's
+ * augmented matrix, 0 the plain one) or mpnl_factor (Y and Z NULL, Q not
+ * NULL): for every subcarrier whose FP32 R has max R_ll / min R_ll >
+ * cond_threshold (a lower bound on the condition number; NaN or zero
+ * diagonals count as above), the sorted QR, z and Q are recomputed in FP64
+ * from H and Y and overwrite R, inv_diag, perm, Z and Q (rounded to FP32);
+ * the other subcarriers are left untouched.  The FP16 walk path is stated
+ * for cond_threshold = 1e3.
+ *   n_refined  device int (nullable): incremented once per subcarrier redone
+ * Errors: as mpnl_preprocess; cond_threshold must be >= 1. */
+int mpnl_refine_qr(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const void *Y,
+                   float sigma2, float cond_threshold, void *R, float *inv_diag, uint8_t *perm,
+                   void *Z, void *Q, int *n_refined, void *ws, void *stream);
+
 /* Position-vector pre-selection (§II: found "before any transmission
  * begins" from the channel; §III-B: N_p).  Per level, gamma_l = R_ll^2 /
  * sigma2 gives the square-QAM symbol-error probability Pe_l (floored at

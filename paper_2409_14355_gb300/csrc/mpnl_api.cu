@@ -545,6 +545,36 @@ int mpnl_factor(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, float sigma2, 
     return MPNL_OK;
 }
 
+int mpnl_refine_qr(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const void *Y, float sigma2,
+                   float cond_threshold, void *R, float *inv_diag, uint8_t *perm, void *Z,
+                   void *Q, int *n_refined, void *ws, void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    const bool mmse = sigma2 != 0.0f;
+    MPNL_TRY(check_dims(ctx, d, false, mmse ? kNrAugmented : kNrTall));
+    if (mmse) MPNL_TRY(check_sigma2(ctx, sigma2));
+    if (!(cond_threshold >= 1.0f))
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "cond_threshold=%g must be >= 1", (double)cond_threshold);
+    if (d->n_sc == 0) return MPNL_OK;
+    const bool with_z = Z != nullptr || Y != nullptr;
+    MPNL_TRY(check_ptr(ctx, H, 8, "H", false));
+    MPNL_TRY(check_ptr(ctx, Y, 8, "Y", !with_z));
+    MPNL_TRY(check_ptr(ctx, Z, 8, "Z", !with_z));
+    MPNL_TRY(check_ptr(ctx, R, 8, "R", false));
+    MPNL_TRY(check_ptr(ctx, inv_diag, 4, "inv_diag", false));
+    MPNL_TRY(check_ptr(ctx, perm, 1, "perm", false));
+    MPNL_TRY(check_ptr(ctx, Q, 8, "Q", true));
+    MPNL_TRY(check_ptr(ctx, n_refined, 4, "n_refined", true));
+    cudaError_t e = mpnl::launch_refine(d->n_sc, with_z ? d->n_sym : 0, d->nr, d->nt,
+                                        mmse ? sqrtf(sigma2) : 0.f, cond_threshold,
+                                        (const float2 *)H, (const float2 *)Y, (float2 *)R, inv_diag,
+                                        perm, (float2 *)Z, (float2 *)Q, n_refined,
+                                        (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "refine launch", e);
+    return MPNL_OK;
+}
+
 int mpnl_qhy(mpnl_ctx *ctx, const mpnl_dims *d, const void *Q, const void *Y, void *Z, void *ws,
              void *stream)
 {

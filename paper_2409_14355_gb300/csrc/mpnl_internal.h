@@ -31,6 +31,14 @@ cudaError_t launch_preprocess(int n_sc, int n_sym, int nr, int nt, float sigma, 
                               const float2 *Y, float2 *R, float *inv_diag, uint8_t *perm,
                               float2 *Z, float2 *Q, cudaStream_t stream);
 
+// FP64 re-factorisation where max R_ll / min R_ll > threshold (mpnl_refine_qr);
+// Y/Z and Q nullable (n_sym 0 / no Q); n_refined (nullable) counts the
+// subcarriers redone.
+cudaError_t launch_refine(int n_sc, int n_sym, int nr, int nt, float sigma, float threshold,
+                          const float2 *H, const float2 *Y, float2 *R, float *inv_diag,
+                          uint8_t *perm, float2 *Z, float2 *Q, int *n_refined,
+                          cudaStream_t stream);
+
 // z = Q^H y from a stored Q (mpnl_qhy).
 cudaError_t launch_qhy(int n_sc, int n_sym, int nr, int nt, const float2 *Q, const float2 *Y,
                        float2 *Z, cudaStream_t stream);

@@ -39,7 +39,7 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_detect_mixed",
             "mpnl_linear_mmse", "mpnl_check_status", "mpnl_probe_ffma", "mpnl_set_tuning",
             "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy",
-            "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy")
+            "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE = 1, 2
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
@@ -128,6 +128,8 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_batch_reset.restype = I
         lib.mpnl_factor.argtypes = [P, D, P, F, P, P, P, P, P, P]
         lib.mpnl_factor.restype = I
+        lib.mpnl_refine_qr.argtypes = [P, D, P, P, F, F, P, P, P, P, P, P, P, P]
+        lib.mpnl_refine_qr.restype = I
         lib.mpnl_qhy.argtypes = [P, D, P, P, P, P, P]
         lib.mpnl_qhy.restype = I
         lib.mpnl_batch_run.argtypes = [P, P, I, P]
@@ -238,6 +240,22 @@ def factor(H: torch.Tensor, sigma2: float | None = None, out=None):
                                     _ptr(R), _ptr(inv_diag), _ptr(perm), None, _stream(dev))
     _raise(st, ctx)
     return Q, R, inv_diag, perm
+
+
+def refine_qr(H, Y, R, inv_diag, perm, Z=None, Q=None, sigma2: float | None = None,
+              cond_threshold: float = 1e3, count: torch.Tensor | None = None) -> None:
+    """FP64 re-factorisation, in place, of the subcarriers whose FP32 R has
+    max R_ll / min R_ll above cond_threshold.  `count` (device int32 [1])
+    receives the number redone."""
+    dev = _dev_of(H)
+    n_sc, nr, nt = H.shape
+    n_sym = Y.shape[1] if Y is not None else 1
+    ctx = context(dev.index)
+    d = Dims(n_sc, n_sym, nr, nt, 4, 1)
+    _raise(load_library().mpnl_refine_qr(ctx, ctypes.byref(d), _ptr(H), _ptr(Y),
+                                         float(sigma2 or 0.0), float(cond_threshold), _ptr(R),
+                                         _ptr(inv_diag), _ptr(perm), _ptr(Z), _ptr(Q),
+                                         _ptr(count), None, _stream(dev)), ctx)
 
 
 def qhy(Q: torch.Tensor, Y: torch.Tensor, out=None):
@@ -379,13 +397,17 @@ class SlotBuffers:
 
 
 def run_slot(buf: SlotBuffers, H, Y, sigma2: float, mmse: bool = True,
-             precision: str = "fp32", mmse_qr: bool = False) -> None:
+             precision: str = "fp32", mmse_qr: bool = False,
+             refine_threshold: float | None = None) -> None:
     """The whole path on device tensors H, Y (enqueued on the current stream):
     preprocess -> select_paths -> detect (hard, LLR, PED pair) [-> MMSE].
     mmse_qr selects the MMSE-extended pre-processing (needed when nt > nr)."""
     n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
     preprocess(H, Y, out=(buf.R, buf.inv_diag, buf.perm, buf.Z),
                sigma2=sigma2 if mmse_qr else None)
+    if refine_threshold is not None:
+        refine_qr(H, Y, buf.R, buf.inv_diag, buf.perm, Z=buf.Z,
+                  sigma2=sigma2 if mmse_qr else None, cond_threshold=refine_threshold)
     select_paths(buf.R, sigma2, qam, n_pe, nt, out=buf.paths)
     detect(buf.R, buf.inv_diag, buf.perm, buf.paths, buf.Z, sigma2, qam,
            out=(buf.hard, buf.llr, buf.ped2), precision=precision)
