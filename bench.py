@@ -439,7 +439,7 @@ def run_mpnl(args):
     flop_per_det = n_pe * (4 * nt * nt + 4 * nt)
     achieved_tflops = flop_per_det * dets_per_step / (det_avg / 1e3) / 1e12
     det_src = [os.path.join(ROOT, "paper_2409_14355_gb300", "csrc", f)
-               for f in ("detect.cu", "mpnl_common.cuh")]
+               for f in ("detect_impl.cuh", "detect_f32.cu", "mpnl_common.cuh")]
     traffic = load_traffic(det_src)
 
     line = None
