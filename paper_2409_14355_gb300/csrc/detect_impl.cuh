@@ -148,7 +148,58 @@ __device__ __forceinline__ float2 label_point(int lab)
     return make_float2(axis_pos<QAM>(ire), axis_pos<QAM>(iim));
 }
 
-// p-th closest point (p >= 3) by (squared distance, label): the 2-D order is
+// The third closest point (p = 3), the same answer as the enumeration below
+// by the same arithmetic, in closed form: after the nearest point (row 0, column 0
+// of the staircase) the second pop is the better of (0, 1) and (1, 0); if it
+// was (1, 0) the third is the best of (0, 1), (1, 1) and (2, 0), else the
+// better of (0, 2) and (1, 0) -- candidates taken in row order, the first
+// valid one first, a later one replacing it on a smaller distance or an
+// equal distance with a smaller label.  p = 3 is most of the ranks >= 3 a
+// table holds, and this skips the enumeration loop.
+template <int QAM>
+__device__ __forceinline__ float third_point(float bx, float by, int ire, int iim, int &oi,
+                                             int &oj)
+{
+    constexpr int L = Qam<QAM>::L;
+    const AxisOrder<QAM> ore(bx, ire), oim(by, iim);
+    auto dist = [&](int ia, int ic) {
+        const float dx = bx - axis_pos<QAM>(ia), dy = by - axis_pos<QAM>(ic);
+        return dx * dx + dy * dy;
+    };
+    int bi, bj;
+    float bd;
+    bool have = false;
+    auto offer = [&](int ia, int ic) {
+        const float v = dist(ia, ic);
+        bool take = !have || v < bd;
+        if (!take && v == bd) take = grid_label<QAM>(ia, ic) < grid_label<QAM>(bi, bj);
+        if (take) {
+            bi = ia;
+            bj = ic;
+            bd = v;
+        }
+        have = true;
+    };
+    const int x1 = ore.idx(1), y1 = oim.idx(1);
+    offer(ire, y1);  // row 0, column 1
+    offer(x1, iim);  // row 1, column 0
+    const bool row1 = bi == x1 && bj == iim && !(x1 == ire && iim == y1);
+    have = false;
+    if (row1) {
+        offer(ire, y1);                       // row 0, column 1
+        offer(x1, y1);                        // row 1, column 1
+        if (L > 2) offer(ore.idx(2), iim);    // row 2, column 0
+    } else {
+        if (L > 2) offer(ire, oim.idx(2));    // row 0, column 2
+        offer(x1, iim);                       // row 1, column 0
+    }
+    oi = bi;
+    oj = bj;
+    return bd;
+}
+
+// p-th closest point (p >= 3) by (squared distance, label), out of line (p = 3
+// in closed form, above).  The 2-D order is
 // enumerated over the "staircase" of (row a, column c) pairs of the two axis
 // orders: popping (a, c) exposes (a, c + 1), popping (a, 0) also exposes
 // (a + 1, 0); every pair's predecessor sorts no later, so p pops reach the
@@ -158,6 +209,7 @@ template <int QAM>
 __device__ __noinline__ float kth_point_slow(float bx, float by, int p, int ire, int iim,
                                              int &oi, int &oj)
 {
+    if (p == 3) return third_point<QAM>(bx, by, ire, iim, oi, oj);
     constexpr int L = Qam<QAM>::L;
     const AxisOrder<QAM> ore(bx, ire), oim(by, iim);
     unsigned cols = 0;
