@@ -251,44 +251,62 @@ __device__ __noinline__ float kth_point_slow(float bx, float by, int p, int ire,
 
 // The first detected level sees the same b = z_{nt-1} / R for every row, so
 // its ordered neighbour list is built once per symbol by one warp: lane j
-// holds points j and j + 32; a point's rank is the number of points before it
-// in (distance, label) order.  Entry r: (x, y, distance, label).
+// holds points j and j + 32, and a bitonic sort of their (distance, label)
+// keys over the warp orders them.  Entry r: (x, y, distance, label).
 template <int QAM>
 __device__ __forceinline__ void top_list(float bx, float by, int kmax, float4 *list)
 {
+    // keys (distance bits, label, grid index): as unsigned 64-bit integers
+    // they order by (distance, label); a bitonic sort over the warp puts the
+    // e-th closest point at element e = lane + 32 k
     constexpr int M = QAM;
     constexpr int PER = (M + 31) / 32;
+    constexpr int E = 32 * PER;
     const int lane = threadIdx.x & 31;
-    float dq[PER], xq[PER], yq[PER];
-    int lq[PER];
+    unsigned long long key[PER];
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
         const int q = lane + 32 * k;  // q = grid index: iy * L + ix
         const int ix = q % Qam<QAM>::L, iy = q / Qam<QAM>::L;
-        xq[k] = axis_pos<QAM>(ix);
-        yq[k] = axis_pos<QAM>(iy);
-        const float dx = bx - xq[k], dy = by - yq[k];
-        dq[k] = q < M ? dx * dx + dy * dy : INFINITY;
-        lq[k] = q < M ? grid_label<QAM>(ix, iy) : 0x7fffffff;
+        const float dx = bx - axis_pos<QAM>(ix), dy = by - axis_pos<QAM>(iy);
+        const float dq = dx * dx + dy * dy;
+        key[k] = q < M ? (((unsigned long long)__float_as_uint(dq) << 32) |
+                          ((unsigned)grid_label<QAM>(ix, iy) << 8) | (unsigned)q)
+                       : ~0ull;
     }
-    int rank[PER];
 #pragma unroll
-    for (int k = 0; k < PER; ++k) rank[k] = 0;
-    for (int j = 0; j < 32; ++j) {
+    for (int size = 2; size <= E; size <<= 1) {
 #pragma unroll
-        for (int kk = 0; kk < PER; ++kk) {
-            const float dj = __shfl_sync(0xffffffffu, dq[kk], j);
-            const int lj = __shfl_sync(0xffffffffu, lq[kk], j);
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
 #pragma unroll
-            for (int k = 0; k < PER; ++k)
-                rank[k] += (dj < dq[k] || (dj == dq[k] && lj < lq[k])) ? 1 : 0;
+            for (int k = 0; k < PER; ++k) {
+                const int e = lane + 32 * k;
+                const bool up = (e & size) == 0;
+                if (stride >= 32) {  // partner in the same lane (PER == 2, stride 32)
+                    if (k == 0) {
+                        const unsigned long long a = key[0], c = key[1];
+                        const bool swap = (a > c) == up;
+                        key[0] = swap ? c : a;
+                        key[1] = swap ? a : c;
+                    }
+                } else {
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, key[k], stride);
+                    const bool lower = (e & stride) == 0;
+                    const bool keep_min = lower == up;
+                    key[k] = keep_min ? (o < key[k] ? o : key[k]) : (o > key[k] ? o : key[k]);
+                }
+            }
         }
     }
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-        const int q = lane + 32 * k;
-        if (q < M && rank[k] < kmax)
-            list[rank[k]] = make_float4(xq[k], yq[k], dq[k], __int_as_float(lq[k]));
+        const int e = lane + 32 * k;
+        if (e < kmax && e < M) {
+            const int q = (int)(key[k] & 0xffu);
+            const float dq = __uint_as_float((unsigned)(key[k] >> 32));
+            list[e] = make_float4(axis_pos<QAM>(q % Qam<QAM>::L), axis_pos<QAM>(q / Qam<QAM>::L), dq,
+                                  __int_as_float((int)((key[k] >> 8) & 0xffu)));
+        }
     }
 }
 
@@ -776,11 +794,14 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
             __syncthreads();
         }
     }
+    // symbol slots the walks visit (SYM per warp item; with SYM = 2 and an
+    // odd n_sym the last slot walks the zero vector of row n_sym)
+    const int nsl = SYM * ((n_sym + SYM - 1) / SYM);
     // ordered neighbours of b = z_{nt-1} / R_{nt-1,nt-1}, one warp per symbol
     {
         const int kmx = s_kmax;
         const float iv = sInvd[nt - 1];
-        for (int s = warp; s <= n_sym; s += kWarps) {
+        for (int s = warp; s < nsl; s += kWarps) {
             const float2 z = sZ[s * NT + nt - 1];
             top_list<QAM>(z.x * iv, z.y * iv, kmx, sTop + s * kTopList);
         }
@@ -802,7 +823,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
         const int l = nt - 2;
         const float iv = sInvd[l];
         const float2 r = sRr[(nt - 1) * NT];  // R_{nt-2, nt-1}
-        for (int it = tid; it < (n_sym + 1) * kmx; it += kThreads) {  // one thread per list
+        for (int it = tid; it < nsl * kmx; it += kThreads) {  // one thread per list
             const int s = it / kmx, a = 1 + it - s * kmx;
             const int len = s_k1[a];
             if (len == 0) continue;
