@@ -297,8 +297,8 @@ typedef struct {
                                        (built-in: 1 for nt > 8, else 2) */
     uint8_t select_warps[3][3][2];  /* warps per subcarrier in the selection: 1, 2 or 4
                                        (built-in: 2 for n_pe >= 256, else 1) */
-    uint8_t persistent_ctas_per_sm; /* CTAs per SM of the batch (persistent) walk launch: 1 or 2
-                                       (built-in 2) */
+    uint8_t persistent_ctas_per_sm; /* CTAs per SM of the batch (persistent) walk launch: 1, 2
+                                       or 3 (built-in 3; fewer when shared memory is short) */
     uint8_t persistent_select_warps; /* warps per subcarrier of the batch selection launch:
                                         1, 2 or 4 (built-in 2) */
 } mpnl_tuning;

@@ -25,7 +25,7 @@ from . import inputs, mpnl
 
 SYM_CHOICES = (1, 2)
 SELECT_WARP_CHOICES = (1, 2, 4)
-CTA_CHOICES = (1, 2)
+CTA_CHOICES = (2, 3)
 
 
 def _time_ms(fn, reps: int = 5, warmup: int = 2) -> float:

@@ -29,7 +29,7 @@ __device__ __forceinline__ void detect_item_qam(const DetArgs &a, int qam, int s
     }
 }
 
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
 detect_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ start,
                     int n_items, int *__restrict__ counter, unsigned *__restrict__ status)
 {

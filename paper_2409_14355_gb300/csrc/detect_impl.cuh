@@ -43,6 +43,9 @@ namespace mpnl {
 namespace {
 
 constexpr int kThreads = 256;
+// Three CTAs per SM (about 80 registers a thread): measured faster than two
+// with more registers; the shared memory of the bench shape (73 KB) fits.
+constexpr int kCtasPerSm = 3;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTopList = 64;  // entries of the first-level neighbour list
 constexpr int kList2 = 128;   // per symbol: entries of all second-level lists together
@@ -1078,7 +1081,7 @@ __device__ __noinline__ void detect_sc(const DetArgs args, int sc)
 }
 
 template <int NT, int QAM, bool F16, int SYM>
-__global__ void __launch_bounds__(kThreads, 2) detect_walk_kernel(DetArgs args)
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) detect_walk_kernel(DetArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     detect_body<NT, QAM, F16, SYM>(args, blockIdx.x, smem);

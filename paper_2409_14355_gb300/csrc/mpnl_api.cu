@@ -268,7 +268,7 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
     // the persistent selection uses one group shape for every unit
     const int sel_warps =
         ctx->tuning.persistent_select_warps ? ctx->tuning.persistent_select_warps : 2;
-    int det_ctas = ctx->tuning.persistent_ctas_per_sm ? ctx->tuning.persistent_ctas_per_sm : 2;
+    int det_ctas = ctx->tuning.persistent_ctas_per_sm ? ctx->tuning.persistent_ctas_per_sm : 3;
     while (det_ctas > 1 && (size_t)det_ctas * det > (size_t)dev_smem) --det_ctas;
     if (det > (size_t)dev_smem || pre * 4 > (size_t)dev_smem || mm * 4 > (size_t)dev_smem ||
         qhy * 4 > (size_t)dev_smem || sel * (4 / sel_warps) > (size_t)dev_smem)
@@ -699,8 +699,8 @@ int mpnl_set_tuning(mpnl_ctx *ctx, const mpnl_tuning *t)
                 if (w != 0 && w != 1 && w != 2 && w != 4)
                     return fail(ctx, MPNL_ERR_INVALID_ARG, "select_warps=%d not in {0,1,2,4}", w);
             }
-    if (t->persistent_ctas_per_sm > 2)
-        return fail(ctx, MPNL_ERR_INVALID_ARG, "persistent_ctas_per_sm=%d not in {0,1,2}",
+    if (t->persistent_ctas_per_sm > 3)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "persistent_ctas_per_sm=%d not in {0,1,2,3}",
                     t->persistent_ctas_per_sm);
     {
         const int w = t->persistent_select_warps;

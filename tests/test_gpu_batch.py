@@ -157,7 +157,7 @@ def test_autotuner_picks_valid_knobs(dev):
     units = inputs.mixed_units(4, seed=7, sc_scale=0.03)
     t, report = autotune.tune(units, dev.index, reps=2)
     d = autotune.to_dict(t)
-    assert d["persistent_ctas_per_sm"] in (1, 2)
+    assert d["persistent_ctas_per_sm"] in (2, 3)
     for u in units:
         a, b, c = mpnl.problem_class(u.nt, u.qam, u.n_pe)
         assert d["detect_sym"][a][b][c] in (1, 2)
