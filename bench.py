@@ -610,10 +610,13 @@ def run_serving(args, dev):
         rate = rho * capacity / mean_dets
         trace = serving.poisson_trace(units, rate, args.serving_seconds, seed=int(100 * rho))
         server.round_sizes.clear()
+        server.host_launch_s = 0.0
         reqs = serving.run_trace(server, trace, payloads)
         st = serving.latency_stats(reqs, dets_of=lambda q: dets[q.ru])
         st.update(offered_detections_per_s=rho * capacity, mean_round=float(
-            np.mean(server.round_sizes)) if server.round_sizes else 0.0)
+            np.mean(server.round_sizes)) if server.round_sizes else 0.0,
+            rounds=len(server.round_sizes),
+            host_ms_per_round=1e3 * server.host_launch_s / max(1, len(server.round_sizes)))
         loads[str(rho)] = st
     server.close()
     n_big = sum(1 for u in units if (u.nr, u.nt, u.qam, u.n_sc) == (16, 16, 64, 3276))

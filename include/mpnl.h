@@ -274,10 +274,17 @@ int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
 
 /* Replace the batch's units by `n_items` new ones (n_items <= the count it
  * was created with), validated and ordered as by mpnl_batch_create, reusing
- * its device allocations; cached graphs are dropped.  The previous work of
- * the batch must have completed. */
+ * its allocations; cached graphs are dropped.  The new descriptors go to
+ * the device with the next mpnl_batch_run, asynchronously on its stream (a
+ * reset waits only until the previous upload has been read).  The previous
+ * runs' kernels may still be in flight only if they have finished reading
+ * nothing the new items change -- in practice: reset after the previous run
+ * of this batch completed.  flags: MPNL_RESET_TRUSTED_POINTERS skips the
+ * per-pointer CUDA attribute queries (null and alignment are still checked;
+ * for callers that draw every buffer from their own device pools). */
+#define MPNL_RESET_TRUSTED_POINTERS 1
 int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *batch, const mpnl_batch_item *items,
-                     int n_items);
+                     int n_items, int flags);
 
 /* Enqueue the stages in `stages` (MPNL_STAGE_* bits, in pipeline order) on
  * `stream`; with MPNL_RUN_GRAPH the stream must not be the legacy default

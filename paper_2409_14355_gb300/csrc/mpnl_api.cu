@@ -150,6 +150,10 @@ struct mpnl_batch {
     int device;
     int capacity;
     int n_items;
+    mpnl::BatchItem *h_items;  // pinned staging of the descriptors (schedule order)
+    int *h_start;              // pinned staging of the prefix sums
+    bool dirty;                // staging newer than the device copy
+    cudaEvent_t copied;        // the last upload has been read
     mpnl::BatchItem *d_items;  // schedule order
     int *d_start;              // kBStages x (capacity + 1) prefix sums of n_sc per stage
     int *d_counters;           // one per stage
@@ -175,7 +179,8 @@ int item_stages(const mpnl_batch_item &it)
 
 // Validate the items, order them largest first, and write the descriptors
 // and per-stage prefix sums into the batch's device arrays.
-int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n_items)
+int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n_items,
+               bool check_pointers = true)
 {
     int dev_smem = 0;
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
@@ -218,11 +223,17 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
                 {it.mmse_hard, "mmse_hard", 1, (st_bits & MPNL_STAGE_MMSE) != 0},
             };
             for (const Need &n : need)
-                if (st == MPNL_OK && n.need) st = check_ptr(ctx, n.p, n.align, n.name, false);
-            if (st == MPNL_OK) st = check_ptr(ctx, it.Q, 8, "Q", true);
-            if (st == MPNL_OK) st = check_ptr(ctx, it.llr, 4, "llr", true);
-            if (st == MPNL_OK) st = check_ptr(ctx, it.ped2, 4, "ped2", true);
-            if (st == MPNL_OK) st = check_ptr(ctx, it.mmse_llr, 4, "mmse_llr", true);
+                if (st == MPNL_OK && n.need) {
+                    if (check_pointers) st = check_ptr(ctx, n.p, n.align, n.name, false);
+                    else if (!n.p || (uintptr_t)n.p % n.align)
+                        st = fail(ctx, MPNL_ERR_INVALID_ARG, "%s is NULL or misaligned", n.name);
+                }
+            if (check_pointers) {
+                if (st == MPNL_OK) st = check_ptr(ctx, it.Q, 8, "Q", true);
+                if (st == MPNL_OK) st = check_ptr(ctx, it.llr, 4, "llr", true);
+                if (st == MPNL_OK) st = check_ptr(ctx, it.ped2, 4, "ped2", true);
+                if (st == MPNL_OK) st = check_ptr(ctx, it.mmse_llr, 4, "mmse_llr", true);
+            }
         }
         if (st != MPNL_OK) {
             char msg[sizeof ctx->err];
@@ -276,9 +287,13 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         return unit_cost(items[a].dims) > unit_cost(items[c].dims);
     });
+    // the previous upload must have been read before the staging is rewritten
+    cudaError_t ce = cudaEventSynchronize(b->copied);
+    if (ce != cudaSuccess) return cuda_fail(ctx, "batch staging", ce);
     const int cap1 = b->capacity + 1;
-    std::vector<mpnl::BatchItem> sorted(n_items);
-    std::vector<int> start((size_t)kBStages * cap1, 0);
+    mpnl::BatchItem *sorted = b->h_items;
+    int *start = b->h_start;
+    for (int k = 0; k < kBStages * cap1; ++k) start[k] = 0;
     for (int k = 0; k < n_items; ++k) {
         sorted[k] = host[order[k]];
         const int bits = stg[order[k]];
@@ -290,11 +305,7 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
         // entries past n_items repeat the total (the kernels read start[n_items])
         for (int k = n_items + 1; k < cap1; ++k) start[q * cap1 + k] = start[q * cap1 + n_items];
     }
-    cudaError_t e = cudaMemcpy(b->d_items, sorted.data(), sizeof(mpnl::BatchItem) * n_items,
-                               cudaMemcpyHostToDevice);
-    if (e == cudaSuccess)
-        e = cudaMemcpy(b->d_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return cuda_fail(ctx, "batch descriptors", e);
+    b->dirty = true;  // uploaded by the next run, on its stream
     b->n_items = n_items;
     b->pre_warp_bytes = (int)pre;
     b->sel_group_bytes = (int)sel;
@@ -308,6 +319,21 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
             cudaGraphExecDestroy(b->graph[k]);
             b->graph[k] = nullptr;
         }
+    return MPNL_OK;
+}
+
+int upload_batch(mpnl_ctx *ctx, mpnl_batch *b, cudaStream_t st)
+{
+    if (!b->dirty) return MPNL_OK;
+    const int cap1 = b->capacity + 1;
+    cudaError_t e = cudaMemcpyAsync(b->d_items, b->h_items, sizeof(mpnl::BatchItem) * b->n_items,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_start, b->h_start, sizeof(int) * kBStages * cap1,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->copied, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, "batch descriptors", e);
+    b->dirty = false;
     return MPNL_OK;
 }
 
@@ -368,6 +394,9 @@ int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
     cudaError_t e = cudaMalloc(&b->d_items, sizeof(mpnl::BatchItem) * n_items);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_start, sizeof(int) * kBStages * (n_items + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * kBStages);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_items, sizeof(mpnl::BatchItem) * n_items);
+    if (e == cudaSuccess) e = cudaMallocHost(&b->h_start, sizeof(int) * kBStages * (n_items + 1));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         mpnl_batch_destroy(b);
         return cuda_fail(ctx, "batch create", e);
@@ -381,7 +410,8 @@ int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
     return MPNL_OK;
 }
 
-int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n_items)
+int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n_items,
+                     int flags)
 {
     MPNL_TRY(begin(ctx));
     if (!b) return fail(ctx, MPNL_ERR_INVALID_ARG, "batch is NULL");
@@ -390,7 +420,9 @@ int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items,
                     ctx->device);
     if (n_items < 1 || n_items > b->capacity || !items)
         return fail(ctx, MPNL_ERR_INVALID_ARG, "n_items=%d outside 1..%d", n_items, b->capacity);
-    return fill_batch(ctx, b, items, n_items);
+    if (flags & ~MPNL_RESET_TRUSTED_POINTERS)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "unknown reset flags 0x%x", flags);
+    return fill_batch(ctx, b, items, n_items, !(flags & MPNL_RESET_TRUSTED_POINTERS));
 }
 
 int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *b, int stages, void *stream)
@@ -404,6 +436,7 @@ int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *b, int stages, void *stream)
         return fail(ctx, MPNL_ERR_INVALID_ARG, "unknown stage bits 0x%x", stages);
     const int mask = stages & MPNL_STAGES_ALL;
     cudaStream_t st = (cudaStream_t)stream;
+    MPNL_TRY(upload_batch(ctx, b, st));
     if (!(stages & MPNL_RUN_GRAPH)) return enqueue_batch(ctx, b, mask, st);
     if (!st) return fail(ctx, MPNL_ERR_INVALID_ARG, "graph capture needs a non-default stream");
     if (!b->graph[mask]) {
@@ -440,6 +473,12 @@ void mpnl_batch_destroy(mpnl_batch *b)
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_start) cudaFree(b->d_start);
     if (b->d_counters) cudaFree(b->d_counters);
+    if (b->h_items) cudaFreeHost(b->h_items);
+    if (b->h_start) cudaFreeHost(b->h_start);
+    if (b->copied) {
+        cudaEventSynchronize(b->copied);
+        cudaEventDestroy(b->copied);
+    }
     free(b);
     if (prev >= 0) cudaSetDevice(prev);
 }

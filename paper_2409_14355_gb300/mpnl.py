@@ -44,6 +44,7 @@ ITEM_MMSE_QR, ITEM_LINEAR_MMSE = 1, 2
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
 RUN_GRAPH = 16
+RESET_TRUSTED_POINTERS = 1
 PRECISIONS = ("fp32", "fp16")
 
 
@@ -124,7 +125,7 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_batch_create.argtypes = [P, ctypes.POINTER(BatchItemC), I,
                                           ctypes.POINTER(ctypes.c_void_p)]
         lib.mpnl_batch_create.restype = I
-        lib.mpnl_batch_reset.argtypes = [P, P, ctypes.POINTER(BatchItemC), I]
+        lib.mpnl_batch_reset.argtypes = [P, P, ctypes.POINTER(BatchItemC), I, I]
         lib.mpnl_batch_reset.restype = I
         lib.mpnl_factor.argtypes = [P, D, P, F, P, P, P, P, P, P]
         lib.mpnl_factor.restype = I
@@ -491,11 +492,13 @@ class Batch:
             arrays.update(mmse_hard=buf.mmse_hard, mmse_llr=buf.mmse_llr)
         return batch_item(buf.dims, sigma2, flags, 0, **arrays)
 
-    def reset(self, items) -> None:
+    def reset(self, items, trusted_pointers: bool = False) -> None:
         """Replace the units (at most the creation count), reusing the
-        device allocations."""
-        arr = (BatchItemC * len(items))(*items)
-        _raise(load_library().mpnl_batch_reset(self._ctx, self._h, arr, len(items)), self._ctx)
+        allocations; `items` is a sequence of BatchItemC or a ctypes array."""
+        arr = items if isinstance(items, ctypes.Array) else (BatchItemC * len(items))(*items)
+        _raise(load_library().mpnl_batch_reset(self._ctx, self._h, arr, len(items),
+                                               RESET_TRUSTED_POINTERS if trusted_pointers else 0),
+               self._ctx)
 
     def run(self, stages: int = STAGES_ALL, graph: bool = False, stream=None) -> None:
         """Enqueue the stages on `stream` (default: the current stream; a

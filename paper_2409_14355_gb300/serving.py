@@ -57,7 +57,8 @@ class RU:
     n_sym: int = 14
     state: dict = field(default_factory=dict)   # Q, R, inv_diag, perm, paths (device)
     busy_rounds: set = field(default_factory=set)
-    blocked: bool = False                       # a channel update is waiting
+    pool: list = field(default_factory=list)    # free per-slot buffer sets
+    H_dev: torch.Tensor | None = None           # device staging of a channel update
 
     @property
     def dims(self):
@@ -73,6 +74,24 @@ class RU:
         return n_sc * (nr * nt * 8 + nt * (nt + 1) // 2 * 8 + nt * 4 + nt + self.n_pe * nt)
 
 
+class SlotBuffers:
+    """Device and pinned host buffers of one in-flight slot request of an RU
+    (allocated at registration, reused)."""
+
+    def __init__(self, ru: "RU", device, llr: bool):
+        n_sc, n_sym, nr, nt = ru.n_sc, ru.n_sym, ru.nr, ru.nt
+        kw = dict(device=device)
+        self.Y = torch.empty((n_sc, n_sym, nr), dtype=torch.complex64, **kw)
+        self.Z = torch.empty((n_sc, n_sym, nt), dtype=torch.complex64, **kw)
+        self.hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, **kw)
+        self.llr = (torch.empty((n_sc, n_sym, nt, mpnl.BITS[ru.qam]), dtype=torch.float32, **kw)
+                    if llr else None)
+        pin = device.type == "cuda"
+        self.hard_host = torch.empty(self.hard.shape, dtype=torch.uint8, pin_memory=pin)
+        self.llr_host = (torch.empty(self.llr.shape, dtype=torch.float32, pin_memory=pin)
+                         if llr else None)
+
+
 @dataclass
 class Request:
     rid: int
@@ -83,8 +102,9 @@ class Request:
     admitted: float = -1.0
     done: float = -1.0
     round_id: int = -1
-    hard: torch.Tensor | None = None   # pinned host results (slot requests)
+    hard: torch.Tensor | None = None   # host results (slot requests)
     llr: torch.Tensor | None = None
+    bufs: SlotBuffers | None = None
 
 
 def request_bytes(ru: RU, kind: str, llr: bool) -> int:
@@ -125,13 +145,17 @@ class Server:
     """Continuous-batching serving loop over device-resident RU state."""
 
     def __init__(self, device=None, mem_budget: int = 2 << 30, max_units_per_round: int = 64,
-                 max_inflight: int = 4, llr: bool = True, starve_s: float = 5e-3):
+                 max_inflight: int = 4, llr: bool = True, starve_s: float = 5e-3,
+                 slots_per_ru: int = 2, keep_results: bool = False):
         self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
                        else torch.device(device))
         self.mem_budget = int(mem_budget)
         self.max_units = int(max_units_per_round)
         self.llr = llr
         self.starve_s = starve_s
+        self.slots_per_ru = slots_per_ru
+        self.keep_results = keep_results  # copy each result out (else a view valid
+        # until the RU's pool buffer is reused)
         self.rus: dict[int, RU] = {}
         self.state_bytes = 0
         self.in_use = 0
@@ -142,6 +166,7 @@ class Server:
         self.t0 = time.perf_counter()
         self.peak_in_use = 0
         self.round_sizes: list[int] = []
+        self.host_launch_s = 0.0  # host time spent forming and enqueueing rounds
 
     # ---- RU registration (setup, synchronous)
     def register(self, ru: RU, H: torch.Tensor) -> None:
@@ -154,6 +179,8 @@ class Server:
                   perm=torch.empty((n_sc, nt), dtype=torch.uint8, device=dev),
                   paths=torch.empty((n_sc, ru.n_pe, nt), dtype=torch.uint8, device=dev))
         ru.state = st
+        ru.pool = [SlotBuffers(ru, dev, self.llr) for _ in range(self.slots_per_ru)]
+        ru.H_dev = torch.empty((n_sc, nr, nt), dtype=torch.complex64, device=dev)
         Hd = H.to(dev)
         mpnl.factor(Hd, ru.sigma2 if ru.mmse_qr else None,
                     out=(st["Q"], st["R"], st["inv_diag"], st["perm"]))
@@ -178,7 +205,16 @@ class Server:
                 for q in r.requests:
                     q.done = t
                     self.completed.append(q)
-                    self.rus[q.ru].busy_rounds.discard(r.round_id)
+                    ru = self.rus[q.ru]
+                    ru.busy_rounds.discard(r.round_id)
+                    if q.bufs is not None:
+                        if self.keep_results:
+                            q.hard = q.bufs.hard_host.clone()
+                            q.llr = q.bufs.llr_host.clone() if q.bufs.llr_host is not None else None
+                        else:
+                            q.hard, q.llr = q.bufs.hard_host, q.bufs.llr_host
+                        ru.pool.append(q.bufs)
+                        q.bufs = None
                 self.in_use -= r.bytes
                 r.requests, r.buffers, r.bytes, r.event = [], [], 0, None
                 n += 1
@@ -202,6 +238,9 @@ class Server:
             ru = self.rus[q.ru]
             need = request_bytes(ru, q.kind, self.llr)
             ok = q.ru not in blocked_rus and nbytes + need <= budget
+            if ok and q.kind == "slot":
+                # a free buffer set of the RU (its earlier slots in this round hold theirs)
+                ok = len(ru.pool) > sum(1 for c in chosen if c.ru == q.ru and c.kind == "slot")
             if ok and q.kind == "channel":
                 # the update rewrites the RU's state: no round in flight may
                 # still read it, and no earlier slot of the RU may share this
@@ -218,71 +257,74 @@ class Server:
         return chosen, nbytes
 
     def _launch(self, r: _Round) -> bool:
+        t_host = time.perf_counter()
+        try:
+            return self._launch_round(r)
+        finally:
+            self.host_launch_s += time.perf_counter() - t_host
+
+    def _launch_round(self, r: _Round) -> bool:
         reqs, nbytes = self._form()
         if not reqs:
             return False
         dev = self.device
         t_adm = self.now()
-        items, bufs = [], []
-        # channel updates first in the item list (the batch runs stages in
-        # order, so a slot of the same RU in this round sees the new state)
-        for q in sorted(reqs, key=lambda q: q.kind != "channel"):
-            ru = self.rus[q.ru]
-            st = ru.state
-            q.admitted = t_adm
-            if q.kind == "channel":
-                H = torch.empty((ru.n_sc, ru.nr, ru.nt), dtype=torch.complex64, device=dev)
-                H.copy_(q.payload, non_blocking=True)
-                flags = mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0
-                items.append(mpnl.batch_item(ru.dims, ru.sigma2, flags,
-                                             mpnl.STAGE_PREPROCESS | mpnl.STAGE_SELECT, H=H, **st))
-                bufs.append((q, H))
-            else:
-                n_sc, n_sym, nr, nt = ru.n_sc, ru.n_sym, ru.nr, ru.nt
-                Y = torch.empty((n_sc, n_sym, nr), dtype=torch.complex64, device=dev)
-                Y.copy_(q.payload, non_blocking=True)
-                Z = torch.empty((n_sc, n_sym, nt), dtype=torch.complex64, device=dev)
-                hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, device=dev)
-                llr = (torch.empty((n_sc, n_sym, nt, mpnl.BITS[ru.qam]), dtype=torch.float32,
-                                   device=dev) if self.llr else None)
-                items.append(mpnl.batch_item(ru.dims, ru.sigma2,
-                                             mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0,
-                                             mpnl.STAGE_QHY | mpnl.STAGE_DETECT, Y=Y, Z=Z,
-                                             hard=hard, llr=llr, Q=st["Q"], R=st["R"],
-                                             inv_diag=st["inv_diag"], perm=st["perm"],
-                                             paths=st["paths"]))
-                bufs.append((q, Y, Z, hard, llr))
-        with torch.cuda.stream(r.stream):
-            # inputs were queued on the current stream: order the round after them
-            r.stream.wait_stream(torch.cuda.current_stream(dev))
+        if r.batch is None:
+            r.items = (mpnl.BatchItemC * self.max_units)()
+        items = r.items
+        st = r.stream
+        n = 0
+        with torch.cuda.stream(st):
+            # channel updates first in the item list (the batch runs stages in
+            # order, so a slot of the same RU in this round sees the new state)
+            for q in sorted(reqs, key=lambda q: q.kind != "channel"):
+                ru = self.rus[q.ru]
+                s_ = ru.state
+                q.admitted = t_adm
+                it = items[n]
+                n += 1
+                it.dims = mpnl.Dims(*ru.dims)
+                it.sigma2 = ru.sigma2
+                it.flags = mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0
+                it.Q, it.R = s_["Q"].data_ptr(), s_["R"].data_ptr()
+                it.inv_diag, it.perm = s_["inv_diag"].data_ptr(), s_["perm"].data_ptr()
+                it.paths = s_["paths"].data_ptr()
+                if q.kind == "channel":
+                    ru.H_dev.copy_(q.payload, non_blocking=True)
+                    it.stages = mpnl.STAGE_PREPROCESS | mpnl.STAGE_SELECT
+                    it.H = ru.H_dev.data_ptr()
+                    it.Y = it.Z = it.hard = it.llr = it.ped2 = None
+                else:
+                    b = ru.pool.pop()
+                    q.bufs = b
+                    b.Y.copy_(q.payload, non_blocking=True)
+                    it.stages = mpnl.STAGE_QHY | mpnl.STAGE_DETECT
+                    it.H = it.ped2 = None
+                    it.Y, it.Z, it.hard = b.Y.data_ptr(), b.Z.data_ptr(), b.hard.data_ptr()
+                    it.llr = b.llr.data_ptr() if b.llr is not None else None
+                it.mmse_hard = it.mmse_llr = None
             if r.batch is None:
                 # created once with room for a full round (padded with copies
-                # of this round's items, replaced right away)
-                pad = (items * (self.max_units // len(items) + 1))[:self.max_units]
-                r.batch = mpnl.Batch(items=pad, device=dev)
-            r.batch.reset(items)
+                # of this round's first item, replaced right away)
+                for k in range(n, self.max_units):
+                    items[k] = items[0]
+                r.batch = mpnl.Batch(items=list(items), device=dev)
+            r.batch.reset((mpnl.BatchItemC * n).from_buffer(items), trusted_pointers=True)
             r.batch.run(mpnl.STAGE_PREPROCESS | mpnl.STAGE_SELECT | mpnl.STAGE_QHY |
-                        mpnl.STAGE_DETECT, stream=r.stream)
-            for b in bufs:
-                q = b[0]
-                if q.kind == "slot":
-                    _, Y, Z, hard, llr = b
-                    q.hard = torch.empty(hard.shape, dtype=hard.dtype, pin_memory=True)
-                    q.hard.copy_(hard, non_blocking=True)
-                    if llr is not None:
-                        q.llr = torch.empty(llr.shape, dtype=llr.dtype, pin_memory=True)
-                        q.llr.copy_(llr, non_blocking=True)
-                for t in b[1:]:
-                    if t is not None:
-                        t.record_stream(r.stream)
+                        mpnl.STAGE_DETECT, stream=st)
+            for q in reqs:
+                if q.bufs is not None:
+                    q.bufs.hard_host.copy_(q.bufs.hard, non_blocking=True)
+                    if q.bufs.llr is not None:
+                        q.bufs.llr_host.copy_(q.bufs.llr, non_blocking=True)
             r.event = torch.cuda.Event()
-            r.event.record(r.stream)
+            r.event.record(st)
         self.n_rounds += 1
         r.round_id = self.n_rounds
         for q in reqs:
             q.round_id = r.round_id
             self.rus[q.ru].busy_rounds.add(r.round_id)
-        r.requests, r.buffers, r.bytes = reqs, bufs, nbytes
+        r.requests, r.bytes = reqs, nbytes
         self.in_use += nbytes
         self.peak_in_use = max(self.peak_in_use, self.in_use)
         self.round_sizes.append(len(reqs))

@@ -74,7 +74,8 @@ def test_serving_results_equal_each_request_alone(dev):
     from paper_2409_14355_gb300 import mpnl, serving
     specs = inputs.mixed_units(6, seed=31, sc_scale=0.02)
     specs[1] = inputs.UnitSpec(4, 6, 16, 29, 64, 18.0, "iid", 77)   # more users than antennas
-    server = serving.Server(dev, mem_budget=64 << 20, max_units_per_round=8, max_inflight=2)
+    server = serving.Server(dev, mem_budget=64 << 20, max_units_per_round=8, max_inflight=2,
+                            keep_results=True)
     payloads, first_H = {}, {}
     for k, u in enumerate(specs):
         sl = inputs.unit_slot(u)

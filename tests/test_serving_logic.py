@@ -10,6 +10,7 @@ def _server(budget=1 << 30, units=4):
     s = serving.Server(device="cpu", mem_budget=budget, max_units_per_round=8)
     for k in range(units):
         s.rus[k] = serving.RU(k, 4, 4, 16, 12 + k, 16, 0.1)
+        s.rus[k].pool = [object(), object()]  # two free buffer sets
     return s
 
 
@@ -72,6 +73,15 @@ def test_channel_update_waits_for_rounds_reading_the_state():
     s.rus[2].busy_rounds.clear()
     chosen, _ = s._form()
     assert [q.rid for q in chosen] == [0, 1]       # update, then its slot, same round
+
+
+def test_slots_wait_for_a_free_buffer_set_of_their_ru():
+    s = _server()
+    for q in (_req(0, 1, "slot"), _req(1, 1, "slot"), _req(2, 1, "slot"), _req(3, 2, "slot")):
+        s.submit(q)
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [0, 1, 3]    # RU 1 (smaller) has two buffer sets
+    assert [q.rid for q in s.waiting] == [2]
 
 
 def test_update_never_shares_a_round_with_an_earlier_slot_of_its_ru():
