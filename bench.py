@@ -612,7 +612,8 @@ def run_serving(args, dev):
         server.round_sizes.clear()
         server.host_launch_s = 0.0
         reqs = serving.run_trace(server, trace, payloads)
-        st = serving.latency_stats(reqs, dets_of=lambda q: dets[q.ru])
+        st = serving.latency_stats(reqs, dets_of=lambda q: dets[q.ru],
+                                   big_of=lambda q: server.rus[q.ru].cost >= server.big_cost)
         st.update(offered_detections_per_s=rho * capacity, mean_round=float(
             np.mean(server.round_sizes)) if server.round_sizes else 0.0,
             rounds=len(server.round_sizes),
@@ -622,7 +623,8 @@ def run_serving(args, dev):
     n_big = sum(1 for u in units if (u.nr, u.nt, u.qam, u.n_sc) == (16, 16, 64, 3276))
     return {"workload": f"{len(units)} radio units ({n_big} of them 16x16 64-QAM 3276 sc), "
                         f"sizes as the mixed batch, Poisson slot requests, channel update every "
-                        f"8th slot of a unit", "deadline_ms": 0.5,
+                        f"8th slot of a unit; large units: walk work >= a 16x16 936-sc N_pe 64 "
+                        f"slot", "deadline_ms": 0.5,
             "capacity_detections_per_s": capacity, "seconds_per_load": args.serving_seconds,
             "resident_state_MB": server.state_bytes / 1e6, "loads": loads}
 

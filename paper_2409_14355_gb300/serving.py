@@ -146,7 +146,8 @@ class Server:
 
     def __init__(self, device=None, mem_budget: int = 2 << 30, max_units_per_round: int = 64,
                  max_inflight: int = 4, llr: bool = True, starve_s: float = 5e-3,
-                 slots_per_ru: int = 2, keep_results: bool = False):
+                 slots_per_ru: int = 2, keep_results: bool = False,
+                 big_cost: float = 936 * 14 * 64 * 16 * 20):
         self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
                        else torch.device(device))
         self.mem_budget = int(mem_budget)
@@ -154,6 +155,7 @@ class Server:
         self.llr = llr
         self.starve_s = starve_s
         self.slots_per_ru = slots_per_ru
+        self.big_cost = big_cost  # units at least this costly form rounds of their own
         self.keep_results = keep_results  # copy each result out (else a view valid
         # until the RU's pool buffer is reused)
         self.rus: dict[int, RU] = {}
@@ -233,11 +235,17 @@ class Server:
         order = sorted(self.waiting, key=lambda q: (now - q.arrival <= self.starve_s,
                                                     self.rus[q.ru].cost, q.arrival))
         self.waiting = collections.deque(order)
+        size_class = None
         while self.waiting and len(chosen) < self.max_units:
             q = self.waiting.popleft()
             ru = self.rus[q.ru]
             need = request_bytes(ru, q.kind, self.llr)
             ok = q.ru not in blocked_rus and nbytes + need <= budget
+            # small and large units in separate rounds: a small unit's slot does
+            # not wait for a large unit's walks in the same round
+            big = ru.cost >= self.big_cost
+            if ok and size_class is not None and big != size_class:
+                ok = False
             if ok and q.kind == "slot":
                 # a free buffer set of the RU (its earlier slots in this round hold theirs)
                 ok = len(ru.pool) > sum(1 for c in chosen if c.ru == q.ru and c.kind == "slot")
@@ -249,6 +257,7 @@ class Server:
             if ok:
                 chosen.append(q)
                 nbytes += need
+                size_class = big
             else:
                 keep.append(q)
                 blocked_rus.add(q.ru)  # the RU's later requests stay behind (per-RU order)
@@ -411,14 +420,22 @@ def run_trace(server: Server, trace, payloads, t_limit_s: float = 120.0):
     return reqs
 
 
-def latency_stats(reqs, deadline_s: float = DEADLINE_S, dets_of=None) -> dict:
+def latency_stats(reqs, deadline_s: float = DEADLINE_S, dets_of=None, big_of=None) -> dict:
+    """p50/p99 latency and deadline-miss rate of the completed slot requests;
+    with big_of (request -> bool) also per size class."""
+    def stats(slots):
+        lat = np.array([q.done - q.arrival for q in slots]) if slots else np.zeros(0)
+        return {"slots_done": len(slots),
+                "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+                "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+                "miss_rate": float(np.mean(lat > deadline_s)) if len(lat) else None}
+
     slots = [q for q in reqs if q.kind == "slot" and q.done >= 0]
-    lat = np.array([q.done - q.arrival for q in slots]) if slots else np.zeros(0)
-    out = {"requests": len(reqs), "slots_done": len(slots),
-           "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
-           "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
-           "miss_rate": float(np.mean(lat > deadline_s)) if len(lat) else None}
+    out = {"requests": len(reqs), **stats(slots)}
     if dets_of is not None and slots:
         span = max(q.done for q in slots) - min(q.arrival for q in slots)
         out["detections_per_s"] = sum(dets_of(q) for q in slots) / max(span, 1e-9)
+    if big_of is not None:
+        out["large_units"] = stats([q for q in slots if big_of(q)])
+        out["small_units"] = stats([q for q in slots if not big_of(q)])
     return out

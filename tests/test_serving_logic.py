@@ -91,3 +91,15 @@ def test_update_never_shares_a_round_with_an_earlier_slot_of_its_ru():
     chosen, _ = s._form()
     assert [q.rid for q in chosen] == [0]
     assert [q.rid for q in s.waiting] == [1, 2]
+
+
+def test_small_and_large_units_form_separate_rounds():
+    s = _server()
+    s.rus[3] = serving.RU(3, 16, 16, 64, 3276, 256, 0.1)
+    s.rus[3].pool = [object(), object()]
+    for q in (_req(0, 3, "slot"), _req(1, 0, "slot"), _req(2, 1, "slot")):
+        s.submit(q)
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [1, 2]       # the small units' round
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [0]          # then the large unit's
