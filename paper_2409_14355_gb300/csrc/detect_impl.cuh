@@ -425,8 +425,8 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     o = a16(o + (n_sym + 1) * NT * 8);
     s.off_tab = o;
     o = a16(o + chunks * 32 * NT);
-    s.off_order = o;
-    o = a16(o + np2 * 4);
+    s.off_order = o;  // row buckets, then the rows in walk order
+    o = a16(o + (np2 + chunks * 32) * 4);
     s.off_m = o;
     o = a16(o + n_sym * NT * B * 2 * 4);
     s.off_best = o;
@@ -741,13 +741,17 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     if (tid == 0) s_kmax = 1;
     for (int k = tid; k <= QAM; k += kThreads) s_k1[k] = 0;
     __syncthreads();
-    // table, clamped; the sort key of a row: how far it deviates from rank 1
-    // below the two list-served levels (largest rank, then rank sum), then
-    // the row.  Also: the largest first-level rank, and per first-level rank
-    // the largest second-level rank (the lengths of the second-level lists).
+    // table, clamped; the order of the rows: by how far they deviate from
+    // rank 1 below the two list-served levels (largest rank, then rank sum,
+    // each clipped at 15: a counting sort into 256 buckets, padding rows
+    // last), so that lanes taking the slower ranking paths share warps.
+    // Also: the largest first-level rank, and per first-level rank the
+    // largest second-level rank (the lengths of the second-level lists).
+    __shared__ int s_hist[256], s_wsum[kWarps];
+    s_hist[tid] = 0;
+    __syncthreads();
     int kmax = 1;
     for (int r = tid; r < np2; r += kThreads) {
-        unsigned key = 0xffffffffu;
         if (r < nrows) {
             int mx = 1, sum = 0, top = 1, second = 1;
             for (int l = 0; l < NT; ++l) {
@@ -770,33 +774,39 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
                 }
                 sTab[r * NT + l] = (uint8_t)v;
             }
-            if (r < n_pe && nt >= 2) atomicMax(&s_k1[top], second);
-            key = r < n_pe ? ((unsigned)min(mx, 255) << 24) | ((unsigned)min(sum, 4095) << 12) |
-                                 (unsigned)r
-                           : (0xfffu << 20) | (unsigned)r;
+            if (r < n_pe) {
+                if (nt >= 2) atomicMax(&s_k1[top], second);
+                sOrder[r] = (unsigned)(min(mx - 1, 15) * 16 + min(sum, 15));  // bucket
+                atomicAdd(&s_hist[sOrder[r]], 1);
+            }
         }
-        sOrder[r] = key;
     }
     atomicMax(&s_kmax, kmax);
     for (int k = tid; k < n_sym * NT * B * 2; k += kThreads) sM[k] = kInfBits;
     for (int k = tid; k < n_sym; k += kThreads) sBest[k] = ~0ull;
     __syncthreads();
-    // bitonic sort of the row keys
-    for (int k = 2; k <= np2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < np2; i += kThreads) {
-                const int ixj = i ^ j;
-                if (ixj > i) {
-                    const unsigned a = sOrder[i], b = sOrder[ixj];
-                    if ((a > b) == ((i & k) == 0)) {
-                        sOrder[i] = b;
-                        sOrder[ixj] = a;
-                    }
-                }
-            }
-            __syncthreads();
+    {  // exclusive scan of the 256 bucket counts, one per thread
+        const int v = s_hist[tid];
+        int inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
         }
+        if (lane == 31) s_wsum[warp] = inc;
+        __syncthreads();
+        int base = 0;
+        for (int w = 0; w < warp; ++w) base += s_wsum[w];
+        s_hist[tid] = base + inc - v;  // now the bucket's next free position
     }
+    __syncthreads();
+    // scatter: real rows by bucket (order inside a bucket does not matter:
+    // every result is a minimum or a per-row value), padding rows after them
+    for (int r = tid; r < nrows; r += kThreads) {
+        const int pos = r < n_pe ? atomicAdd(&s_hist[sOrder[r]], 1) : r;
+        sOrder[np2 + pos] = (unsigned)r;
+    }
+    __syncthreads();
     // symbol slots the walks visit (SYM per warp item; with SYM = 2 and an
     // odd n_sym the last slot walks the zero vector of row n_sym)
     const int nsl = SYM * ((n_sym + SYM - 1) / SYM);
@@ -845,7 +855,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     const int l_list = use2 ? nt - 2 : nt - 1;  // levels >= l_list are list-served
     for (int item = warp; item < chunks * groups; item += kWarps) {
         const int chunk = item / groups, s0 = SYM * (item - chunk * groups);
-        const int row = (int)(sOrder[chunk * 32 + lane] & 0xfffu);
+        const int row = (int)sOrder[np2 + chunk * 32 + lane];
         const bool active = row < n_pe;
         const uint8_t *trow = sTab + row * NT;
         // shift register: when level l is decided, e[k][i] = e_{l-i} of
