@@ -146,10 +146,12 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # CPU oracle timing (baseline only)
 # --------------------------------------------------------------------------
-def time_oracle(sl, qam, n_pe, seconds: float, max_sc: int | None = None, n_threads: int = 0):
+def time_oracle(sl, qam, n_pe, seconds: float, max_sc: int | None = None, n_threads: int = 0,
+                keep: list | None = None):
     """Run the oracle on growing prefixes of the slot's subcarriers until one
     run takes >= `seconds` (or the cap is reached).  Returns (dets/s, threads,
-    subcarriers, elapsed).  n_threads 0 = all host cores."""
+    subcarriers, elapsed); the last run's outputs go to `keep` if given.
+    n_threads 0 = all host cores."""
     import oracle
 
     n = 4
@@ -161,6 +163,8 @@ def time_oracle(sl, qam, n_pe, seconds: float, max_sc: int | None = None, n_thre
                                  n_threads=n_threads)
         dt = time.perf_counter() - t0
         if dt >= seconds or n >= cap:
+            if keep is not None:
+                keep.append(out)
             return n * sl.n_sym / dt, out["threads"], n, dt
         grow = max(2.0, min(8.0, 1.2 * seconds / max(dt, 1e-3)))
         n = int(n * grow) + 1
@@ -485,13 +489,16 @@ def run_mpnl(args):
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             sl0 = inputs.workload_slot(args.workload, args.snr_index, extra_seed=1)
-            v, thr, n_used, dt = time_oracle(sl0, qam, n_pe, args.cpu_seconds)
+            kept = []
+            v, thr, n_used, dt = time_oracle(sl0, qam, n_pe, args.cpu_seconds, keep=kept)
+            accuracy = accuracy_vs_oracle(sl0, kept[0], n_used, qam, n_pe, dev)
             v1, _, n1, dt1 = time_oracle(sl0, qam, n_pe, args.cpu_seconds / 3, n_threads=1)
             cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{n_used} of {n_sc} subcarriers x 14 symbols of one slot "
                              f"(whole path incl. MMSE), FP64, {dt:.1f} s",
                    "one_core": {"value": v1, "cores": 1,
-                                "sample": f"{n1} subcarriers x 14 symbols, {dt1:.1f} s"}}
+                                "sample": f"{n1} subcarriers x 14 symbols, {dt1:.1f} s"},
+                   "accuracy": accuracy}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / K, "higher_is_better": True,
@@ -530,6 +537,36 @@ def run_mpnl(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def accuracy_vs_oracle(sl, ref, n_used, qam, n_pe, dev):
+    """Decision-mismatch rate and BER of the GPU path (FP32 and FP16
+    residuals) against the FP64 oracle on the subcarriers the oracle ran."""
+    import torch
+
+    from paper_2409_14355_gb300 import mpnl
+
+    B = BITS[qam]
+    labels = sl.labels[:n_used]
+
+    def ber(hard):
+        e = 0
+        for b in range(B):
+            e += np.sum(((hard >> (B - 1 - b)) & 1) != ((labels >> (B - 1 - b)) & 1))
+        return float(e / (labels.size * B))
+
+    out = {"subcarriers": int(n_used), "ber_oracle": ber(ref["hard"]),
+           "ber_oracle_mmse": ber(ref["mmse_hard"])}
+    H = torch.from_numpy(sl.H).to(dev)
+    Y = torch.from_numpy(sl.Y).to(dev)
+    for prec in ("fp32", "fp16"):
+        g = mpnl.detect_slot(H, Y, sl.sigma2, qam, n_pe, mmse=True, precision=prec)
+        hard = g["hard"].cpu().numpy()[:n_used]
+        out[prec] = {"decision_mismatch": float(np.mean(np.any(hard != ref["hard"], axis=-1))),
+                     "ber": ber(hard), "ber_delta": ber(hard) - out["ber_oracle"]}
+        if prec == "fp32":
+            out["ber_mmse_gpu"] = ber(g["mmse_hard"].cpu().numpy()[:n_used])
+    return out
 
 
 def run_mixed(args, dev, rank):

@@ -226,7 +226,7 @@ int mpnl_check_status(mpnl_ctx *ctx, void *stream);
 typedef struct {
     mpnl_dims dims;
     float sigma2;
-    int flags;            /* MPNL_ITEM_MMSE_QR, MPNL_ITEM_LINEAR_MMSE */
+    int flags;            /* MPNL_ITEM_MMSE_QR, MPNL_ITEM_LINEAR_MMSE, MPNL_ITEM_FP16 */
     int stages;           /* MPNL_STAGE_* bits this unit takes part in; 0 = the whole path
                              (sorted QR + z, selection, walks, and MMSE with the flag) */
     void *Q;              /* c64 [n_sc][nr][nt]: written by the QR stage if not NULL,
@@ -247,6 +247,7 @@ typedef struct {
 
 #define MPNL_ITEM_MMSE_QR 1      /* MMSE-extended QR (mpnl_preprocess_mmse); allows nt > nr */
 #define MPNL_ITEM_LINEAR_MMSE 2  /* also run the linear MMSE baseline */
+#define MPNL_ITEM_FP16 4         /* walks with FP16 residuals, as mpnl_detect_mixed */
 
 /* Stages run in the order QR, selection, Q^H y, walks, MMSE.  A unit whose
  * stages include MPNL_STAGE_QHY gets z from its stored Q; otherwise, if its

@@ -404,8 +404,18 @@ __host__ __device__ inline int pow2_at_least(int n)
 
 struct DetSmem {
     int off_rc, off_r2, off_invd, off_perm, off_z, off_tab, off_order, off_m, off_best, off_wmin,
-        off_second, off_blab, off_top, off_l2, off_lut, off_rh, off_key2, off_blab2, bytes;
+        off_second, off_blab, off_top, off_l2, off_lut, off_rh, off_key2, off_blab2, off_scr,
+        bytes;
 };
+
+// Small per-CTA counters of one subcarrier, kept in the dynamic shared
+// memory rather than as function-scope __shared__ arrays: every instance of
+// the walk body would otherwise add its own static copy to a kernel that
+// calls several instances (the persistent batch kernel), cutting its
+// residency.  Ints: k1[65], off1[65], use2, kmax, hist[256], wsum[warps].
+constexpr int kScrK1 = 0, kScrOff1 = 65, kScrUse2 = 130, kScrKmax = 131, kScrHist = 132,
+              kScrWsum = 388, kScrInts = 388 + kWarps;
+static_assert(kThreads == 256, "the row sort gives each thread one of the 256 buckets");
 
 __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym, int WORDS)
 {
@@ -450,6 +460,8 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     o = a16(o + n_sym * chunks * 8);
     s.off_blab2 = o;
     o = a16(o + n_sym * chunks * WORDS * 4);
+    s.off_scr = o;
+    o = a16(o + kScrInts * 4);
     s.bytes = o;
     return s;
 }
@@ -692,13 +704,14 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     uint32_t *sBlab = reinterpret_cast<uint32_t *>(smem + S.off_blab);
     float4 *sTop = reinterpret_cast<float4 *>(smem + S.off_top);
     float4 *sL2 = reinterpret_cast<float4 *>(smem + S.off_l2);
-    __shared__ int s_k1[QAM + 1], s_off1[QAM + 1];
-    __shared__ int s_use2;
+    int *sScr = reinterpret_cast<int *>(smem + S.off_scr);
+    int *s_k1 = sScr + kScrK1, *s_off1 = sScr + kScrOff1;  // QAM + 1 entries each
+    int &s_use2 = sScr[kScrUse2];
     uint8_t *sLut = smem + S.off_lut;
     uint2 *sRh = reinterpret_cast<uint2 *>(smem + S.off_rh);  // sRr as {(-Re,-Re), (Im,-Im)} half2
     unsigned long long *sKey2 = reinterpret_cast<unsigned long long *>(smem + S.off_key2);
     uint32_t *sBlab2 = reinterpret_cast<uint32_t *>(smem + S.off_blab2);
-    __shared__ int s_kmax;
+    int &s_kmax = sScr[kScrKmax];
 
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -747,7 +760,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     // last), so that lanes taking the slower ranking paths share warps.
     // Also: the largest first-level rank, and per first-level rank the
     // largest second-level rank (the lengths of the second-level lists).
-    __shared__ int s_hist[256], s_wsum[kWarps];
+    int *s_hist = sScr + kScrHist, *s_wsum = sScr + kScrWsum;  // 256 buckets, kWarps sums
     s_hist[tid] = 0;
     __syncthreads();
     int kmax = 1;

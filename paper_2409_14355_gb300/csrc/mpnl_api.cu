@@ -198,7 +198,8 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
         const bool carry_y = pre_on && (st_bits & MPNL_STAGE_DETECT) && !qhy_on;
         int st = check_dims(ctx, d, true, mqr ? kNrAugmented : kNrTall);
         if (st == MPNL_OK) st = check_sigma2(ctx, it.sigma2);
-        if (st == MPNL_OK && (it.flags & ~(MPNL_ITEM_MMSE_QR | MPNL_ITEM_LINEAR_MMSE)))
+        if (st == MPNL_OK &&
+            (it.flags & ~(MPNL_ITEM_MMSE_QR | MPNL_ITEM_LINEAR_MMSE | MPNL_ITEM_FP16)))
             st = fail(ctx, MPNL_ERR_INVALID_ARG, "unknown flags 0x%x", it.flags);
         if (st == MPNL_OK && (st_bits & ~(MPNL_STAGES_ALL)))
             st = fail(ctx, MPNL_ERR_INVALID_ARG, "unknown stage bits 0x%x", st_bits);
@@ -251,6 +252,7 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
         h.sigma = mqr ? sqrtf(it.sigma2) : 0.f;
         h.sym = tuned_sym(ctx, d);
         h.mmse = (st_bits & MPNL_STAGE_MMSE) ? 1 : 0;
+        h.f16 = (it.flags & MPNL_ITEM_FP16) ? 1 : 0;
         h.factor_sym = carry_y ? d->n_sym : 0;
         h.Q = (float2 *)it.Q;
         h.H = (const float2 *)it.H;

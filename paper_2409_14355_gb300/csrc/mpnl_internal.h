@@ -76,6 +76,7 @@ struct BatchItem {
     float sigma2, sigma;  // sigma > 0: MMSE-extended QR (sigma = sqrt(sigma2))
     int sym;              // symbols per lane of the walk kernel
     int mmse;             // also run the linear MMSE baseline
+    int f16;              // walks with FP16 residuals (mpnl_detect_mixed's arithmetic)
     int factor_sym;       // symbols the sorted-QR stage carries along (n_sym or 0)
     float2 *Q;            // antenna rows of Q (nullable; required by the Q^H y stage)
     const float2 *H, *Y;

@@ -55,6 +55,7 @@ class RU:
     sigma2: float
     mmse_qr: bool = False
     n_sym: int = 14
+    precision: str = "fp32"   # walk arithmetic: "fp32" or "fp16" residuals
     state: dict = field(default_factory=dict)   # Q, R, inv_diag, perm, paths (device)
     busy_rounds: set = field(default_factory=set)
     pool: list = field(default_factory=list)    # free per-slot buffer sets
@@ -294,7 +295,8 @@ class Server:
                 n += 1
                 it.dims = mpnl.Dims(*ru.dims)
                 it.sigma2 = ru.sigma2
-                it.flags = mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0
+                it.flags = (mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0) \
+                    | (mpnl.ITEM_FP16 if ru.precision == "fp16" else 0)
                 it.Q, it.R = s_["Q"].data_ptr(), s_["R"].data_ptr()
                 it.inv_diag, it.perm = s_["inv_diag"].data_ptr(), s_["perm"].data_ptr()
                 it.paths = s_["paths"].data_ptr()

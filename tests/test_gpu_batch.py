@@ -44,22 +44,23 @@ def _fill(dev, specs):
         buf.H.copy_(torch.from_numpy(sl.H))
         buf.Y.copy_(torch.from_numpy(sl.Y))
         mmse_qr = u.nt > u.nr or k % 5 == 3
-        units.append((buf, sl.sigma2, mmse_qr, k % 3 != 1))
+        precision = "fp16" if k % 4 == 2 else "fp32"
+        units.append((buf, sl.sigma2, mmse_qr, k % 3 != 1, precision))
         slots.append(sl)
     return units, slots
 
 
 def _alone(dev, unit):
     mpnl = _mpnl()
-    buf, sigma2, mmse_qr, mmse = unit
+    buf, sigma2, mmse_qr, mmse, precision = unit
     n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
     ref = mpnl.SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, dev, mmse=mmse)
-    mpnl.run_slot(ref, buf.H, buf.Y, sigma2, mmse=mmse, mmse_qr=mmse_qr)
+    mpnl.run_slot(ref, buf.H, buf.Y, sigma2, mmse=mmse, mmse_qr=mmse_qr, precision=precision)
     return ref
 
 
 def _assert_same(unit, ref, k):
-    buf, _, _, mmse = unit
+    buf, _, _, mmse, _ = unit
     names = OUTS + (("mmse_hard", "mmse_llr") if mmse else ())
     for name in names:
         a, b = getattr(buf, name), getattr(ref, name)
@@ -91,7 +92,7 @@ def test_batch_graph_replay_follows_new_inputs(dev):
     for k, unit in enumerate(units):
         _assert_same(unit, _alone(dev, unit), k)
     # new received symbols in the same buffers: the replayed graph reads them
-    for k, (buf, _, _, _) in enumerate(units):
+    for k, (buf, _, _, _, _) in enumerate(units):
         sl = inputs.unit_slot(inputs.UnitSpec(**{**specs[k].__dict__, "seed": specs[k].seed + 1}))
         buf.Y.copy_(torch.from_numpy(sl.Y))
     torch.cuda.synchronize()
@@ -108,8 +109,8 @@ def test_batch_rejects_bad_items(dev):
     mpnl = _mpnl()
     units, _ = _fill(dev, _specs()[:3])
     bad = list(units)
-    buf, s2, mq, mm = bad[1]
-    bad[1] = (buf, -1.0, mq, mm)
+    buf, s2, mq, mm, prec = bad[1]
+    bad[1] = (buf, -1.0, mq, mm, prec)
     with pytest.raises(mpnl.MpnlError) as e:
         mpnl.Batch(bad, dev)
     assert "item 1" in str(e.value)

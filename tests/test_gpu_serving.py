@@ -66,7 +66,8 @@ def _alone(dev, ru, H, Y):
     Q, R, inv_diag, perm = mpnl.factor(H.to(dev), ru.sigma2 if ru.mmse_qr else None)
     paths = mpnl.select_paths(R, ru.sigma2, ru.qam, ru.n_pe, ru.nt)
     Z = mpnl.qhy(Q, Y.to(dev))
-    hard, llr, _ = mpnl.detect(R, inv_diag, perm, paths, Z, ru.sigma2, ru.qam)
+    hard, llr, _ = mpnl.detect(R, inv_diag, perm, paths, Z, ru.sigma2, ru.qam,
+                               precision=ru.precision)
     return hard.cpu(), llr.cpu()
 
 
@@ -79,7 +80,8 @@ def test_serving_results_equal_each_request_alone(dev):
     payloads, first_H = {}, {}
     for k, u in enumerate(specs):
         sl = inputs.unit_slot(u)
-        ru = serving.RU(k, u.nr, u.nt, u.qam, u.n_sc, u.n_pe, sl.sigma2, mmse_qr=u.nt > u.nr)
+        ru = serving.RU(k, u.nr, u.nt, u.qam, u.n_sc, u.n_pe, sl.sigma2, mmse_qr=u.nt > u.nr,
+                        precision="fp16" if k % 3 == 2 else "fp32")
         server.register(ru, torch.from_numpy(sl.H))
         first_H[k] = torch.from_numpy(sl.H)
         alt = [inputs.unit_slot(inputs.UnitSpec(**{**u.__dict__, "seed": u.seed + j}))
