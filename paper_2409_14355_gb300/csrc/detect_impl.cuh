@@ -754,10 +754,15 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     if (tid == 0) s_kmax = 1;
     for (int k = tid; k <= QAM; k += kThreads) s_k1[k] = 0;
     __syncthreads();
-    // table, clamped; the order of the rows: by how far they deviate from
-    // rank 1 below the two list-served levels (largest rank, then rank sum,
-    // each clipped at 15: a counting sort into 256 buckets, padding rows
-    // last), so that lanes taking the slower ranking paths share warps.
+    // table, clamped; the order of the rows (a counting sort into 256
+    // buckets, padding rows last): a warp pays for a ranking path at a level
+    // if any of its lanes takes it there, so rows are grouped by the levels
+    // at which they leave rank 1 below the two list-served levels -- rows
+    // with a rank >= 4 first, by that rank, largest first (their enumeration
+    // loop runs rank-many steps); then those whose largest rank is 3, by
+    // the highest level holding it; then rows with a single rank 2, by its
+    // level; with two, by (lower, upper) level; with more, by the lowest;
+    // rows that stay at rank 1 last.
     // Also: the largest first-level rank, and per first-level rank the
     // largest second-level rank (the lengths of the second-level lists).
     int *s_hist = sScr + kScrHist, *s_wsum = sScr + kScrWsum;  // 256 buckets, kWarps sums
@@ -766,7 +771,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     int kmax = 1;
     for (int r = tid; r < np2; r += kThreads) {
         if (r < nrows) {
-            int mx = 1, sum = 0, top = 1, second = 1;
+            int mx = 1, ndev = 0, d1 = 0, d2 = 0, hi3 = 0, top = 1, second = 1;
             for (int l = 0; l < NT; ++l) {
                 int v = 1;  // padding rows and levels: rank 1
                 if (r < n_pe && l < nt) {
@@ -780,16 +785,29 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
                         top = v;
                     } else if (l == nt - 2) {
                         second = v;
-                    } else {
+                    } else if (v > 1) {  // levels visited bottom-up
+                        if (ndev == 0) d1 = l;
+                        else if (ndev == 1) d2 = l;
+                        ++ndev;
+                        if (v > 2) hi3 = l;
                         mx = max(mx, v);
-                        sum += v - 1;
                     }
                 }
                 sTab[r * NT + l] = (uint8_t)v;
             }
             if (r < n_pe) {
                 if (nt >= 2) atomicMax(&s_k1[top], second);
-                sOrder[r] = (unsigned)(min(mx - 1, 15) * 16 + min(sum, 15));  // bucket
+                d1 = min(d1, 13);  // levels below nt - 2 <= 14
+                d2 = min(d2, 13);
+                const int h3 = min(hi3, 13);
+                int bucket;
+                if (mx >= 4) bucket = 7 - min(mx - 4, 7);               // 0 .. 7
+                else if (mx == 3) bucket = 8 + h3;                      // 8 .. 21
+                else if (ndev == 0) bucket = 240;
+                else if (ndev == 1) bucket = 22 + d1;                   // 22 .. 35
+                else if (ndev == 2) bucket = 36 + d1 * 14 + d2;         // 36 .. 217
+                else bucket = 218 + d1;                                 // 218 .. 230
+                sOrder[r] = (unsigned)bucket;
                 atomicAdd(&s_hist[sOrder[r]], 1);
             }
         }
