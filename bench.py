@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--n-pe", type=int, default=256)
     ap.add_argument("--snr-index", type=int, default=2)
     ap.add_argument("--ring", type=int, default=16, help="distinct slots cycled through (> L2)")
-    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--inflight", type=int, default=2,
                     help="slots in flight on their own streams (MMSE on a side stream each)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -396,18 +396,30 @@ def run_mpnl(args):
         H, Y, _ = ring[i]
         hs.append((H.cpu().pin_memory(), Y.cpu().pin_memory()))
     if args.e2e_steps > 0:
-        for i in range(2):
-            mpnl.detect_slot(hs[i % len(hs)][0], hs[i % len(hs)][1], sigma2, qam, n_pe,
-                             mmse=True, buffers=buf, precision=args.precision)
+        # the streaming host API: every slot's H and Y copied in from pinned
+        # host memory and its results (decisions, LLRs, PED pairs, MMSE
+        # outputs) copied back into pinned host memory, `inflight` slots in
+        # flight; each result is waited for in order
+        pipe = mpnl.SlotPipeline(n_sc, n_sym, nr, nt, qam, n_pe, dev, depth=nf, mmse=True,
+                                 precision=args.precision)
+
+        def run_e2e(n):
+            tickets = []
+            for i in range(n):
+                Hh, Yh = hs[i % len(hs)]
+                tickets.append(pipe.submit(Hh, Yh, sigma2))
+                if len(tickets) >= nf:
+                    pipe.result(tickets.pop(0))
+            for t in tickets:
+                pipe.result(t)
+
+        run_e2e(max(3, nf))
+        pipe.check_status()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(args.e2e_steps):
-            Hh, Yh = hs[i % len(hs)]
-            out = mpnl.detect_slot(Hh, Yh, sigma2, qam, n_pe, mmse=True, buffers=buf,
-                                   precision=args.precision)
+        run_e2e(args.e2e_steps)
         e2e_dt = time.perf_counter() - t0
-        h2d = hs[0][0].numel() * 8 + hs[0][1].numel() * 8
-        d2h = sum(v.numel() * v.element_size() for v in out.values())
+        h2d, d2h = pipe.h2d_bytes, pipe.d2h_bytes
         e2e_value, _ = whole_job_rate(args.e2e_steps * n_sc * n_sym, e2e_dt, dev)
 
     dets_per_step = n_sc * n_sym

@@ -446,6 +446,92 @@ def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
     return out
 
 
+class SlotPipeline:
+    """End-to-end detection of a stream of slots held in host memory, with
+    `depth` slots in flight.  A slot's host-to-device copies, the path and
+    the device-to-host copies of its results run on the slot's own stream
+    (the MMSE baseline, which needs only H and Y, on a side stream), so the
+    copies of one slot overlap the kernels of another.  Inputs should be
+    pinned host tensors (pageable ones are copied synchronously).  Results
+    land in pinned host buffers owned by the pipeline: ``result(ticket)``
+    waits for that slot and returns views that stay valid until the same
+    buffers are reused, `depth` submissions later."""
+
+    def __init__(self, n_sc, n_sym, nr, nt, qam, n_pe, device=None, depth: int = 2,
+                 mmse: bool = True, precision: str = "fp32", mmse_qr: bool = False):
+        if depth < 1:
+            raise ValueError("depth must be >= 1")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.dims = (n_sc, n_sym, nr, nt, qam, n_pe)
+        self.mmse, self.precision, self.mmse_qr = mmse, precision, mmse_qr
+        self._lanes = []
+        for _ in range(depth):
+            buf = SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, self.device, mmse)
+            names = ("hard", "llr", "ped2") + (("mmse_hard", "mmse_llr") if mmse else ())
+            host = {k: torch.empty(getattr(buf, k).shape, dtype=getattr(buf, k).dtype,
+                                   pin_memory=True) for k in names}
+            self._lanes.append(dict(buf=buf, host=host, ticket=-1,
+                                    stream=torch.cuda.Stream(self.device),
+                                    side=torch.cuda.Stream(self.device),
+                                    done=torch.cuda.Event()))
+        self._next = 0
+
+    @property
+    def h2d_bytes(self) -> int:
+        b = self._lanes[0]["buf"]
+        return b.H.numel() * b.H.element_size() + b.Y.numel() * b.Y.element_size()
+
+    @property
+    def d2h_bytes(self) -> int:
+        return sum(v.numel() * v.element_size() for v in self._lanes[0]["host"].values())
+
+    def submit(self, H, Y, sigma2: float) -> int:
+        """Enqueue one slot (host H [n_sc][nr][nt], Y [n_sc][n_sym][nr],
+        complex64); returns its ticket.  Waits first for the slot that last
+        used the same buffers."""
+        lane = self._lanes[self._next % len(self._lanes)]
+        ticket = self._next
+        self._next += 1
+        if lane["ticket"] >= 0:
+            lane["done"].synchronize()
+        lane["ticket"] = ticket
+        buf, st, side, host = lane["buf"], lane["stream"], lane["side"], lane["host"]
+        qam = self.dims[4]
+        with torch.cuda.stream(st):
+            buf.H.copy_(H, non_blocking=True)
+            buf.Y.copy_(Y, non_blocking=True)
+        if self.mmse:
+            side.wait_stream(st)
+            with torch.cuda.stream(side):
+                linear_mmse(buf.H, buf.Y, sigma2, qam, out=(buf.mmse_hard, buf.mmse_llr))
+                host["mmse_hard"].copy_(buf.mmse_hard, non_blocking=True)
+                host["mmse_llr"].copy_(buf.mmse_llr, non_blocking=True)
+        with torch.cuda.stream(st):
+            run_slot(buf, buf.H, buf.Y, sigma2, mmse=False, precision=self.precision,
+                     mmse_qr=self.mmse_qr)
+            for k in ("hard", "llr", "ped2"):
+                host[k].copy_(getattr(buf, k), non_blocking=True)
+            if self.mmse:
+                st.wait_stream(side)
+            lane["done"].record(st)
+        return ticket
+
+    def result(self, ticket: int) -> dict:
+        """Wait for a submitted slot and return its host results."""
+        lane = self._lanes[ticket % len(self._lanes)]
+        if lane["ticket"] != ticket:
+            raise ValueError(f"ticket {ticket} is no longer held (buffers reused)")
+        lane["done"].synchronize()
+        return lane["host"]
+
+    def check_status(self) -> None:
+        """Raise on device-side errors recorded by the slots' launches."""
+        for lane in self._lanes:
+            lane["done"].synchronize()
+        check_status(self.device.index)
+
+
 def batch_item(dims, sigma2: float, flags: int = 0, stages: int = 0, **arrays) -> BatchItemC:
     """One mpnl_batch_item from device tensors given by field name (H, Y, Q,
     R, inv_diag, perm, Z, paths, hard, llr, ped2, mmse_hard, mmse_llr)."""
