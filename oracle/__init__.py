@@ -12,8 +12,10 @@ only compiles it with gcc and marshals numpy arrays.
 Parity pins (checked by ``tests/test_oracle_*.py`` against things other than
 the oracle itself): exhaustive ML on 4x4 QPSK, N_pe = 1 == sorted-QR SIC,
 N_pe = M^Nt == ML, QR and path-table invariants, brute-force top-N selection,
-noise-free recovery, MMSE vs a direct linear solve, closed-form SISO LLRs and
-the closed-form MRC bit-error rate.  Parity unpinned: how well the selection
+noise-free recovery, MMSE vs a direct linear solve, closed-form SISO LLRs,
+the closed-form MRC bit-error rate, and for the table-driven rank model the
+closed-form rank probabilities of QPSK and 16QAM, brute-force top-N selection
+and agreement with the geometric model on a table built from it.  Parity unpinned: how well the selection
 heuristic (the per-level error model) matches the paper's own MPNL BER; the
 paper prints no numbers for it.
 """
@@ -70,8 +72,13 @@ def _load():
             lib.orc_mmse.argtypes = [I, I, I, I, P, P, D, P, P, P, P]
             lib.orc_detect_slot.argtypes = [I, I, I, I, I, I, D, P, P, P, P, P, P, P, P, P,
                                             P, P, P, P, P, I, D, P, I]
+            LL = ctypes.c_longlong
+            lib.orc_rank_counts_mc.argtypes = [I, I, P, LL, ctypes.c_ulonglong, P]
+            lib.orc_rank_costs.argtypes = [I, I, P, LL, P]
+            lib.orc_select_paths_lut.argtypes = [I, I, P, D, I, P, P, I, P, P, P]
             for f in ("orc_constellation", "orc_sqrd", "orc_sqrd_mmse", "orc_qhy", "orc_select_paths",
-                      "orc_detect", "orc_mmse", "orc_detect_slot"):
+                      "orc_detect", "orc_mmse", "orc_detect_slot", "orc_rank_counts_mc",
+                      "orc_rank_costs", "orc_select_paths_lut"):
                 getattr(lib, f).restype = I
             _lib = lib
     return _lib
@@ -145,6 +152,44 @@ def select_paths(rdiag, sigma2: float, qam: int, n_pe: int):
     _check(_load().orc_select_paths(nt, qam, _p(rdiag), float(sigma2), n_pe, _p(paths),
                                     _p(score), _p(pe)), "select_paths")
     return paths, score, pe
+
+
+def rank_counts_mc(qam: int, gamma, n_trials: int, seed: int) -> np.ndarray:
+    """Monte-Carlo rank histogram per SNR (linear) -> int64[n_bins][qam]:
+    counts[b][k-1] = trials whose transmitted point ranked k-th."""
+    gamma = np.ascontiguousarray(np.asarray(gamma, np.float64))
+    counts = np.zeros((gamma.shape[0], qam), np.int64)
+    _check(_load().orc_rank_counts_mc(qam, gamma.shape[0], _p(gamma), int(n_trials),
+                                      ctypes.c_ulonglong(seed), _p(counts)), "rank_counts_mc")
+    return counts
+
+
+def rank_costs(counts, n_trials: int) -> np.ndarray:
+    """Rank costs c(k) = log P(1) - log P(k) (floored, nondecreasing) -> float64[n_bins][qam]."""
+    counts = np.ascontiguousarray(np.asarray(counts, np.int64))
+    n_bins, qam = counts.shape
+    cost = np.zeros((n_bins, qam), np.float64)
+    _check(_load().orc_rank_costs(qam, n_bins, _p(counts), int(n_trials), _p(cost)), "rank_costs")
+    return cost
+
+
+def select_paths_lut(rdiag, sigma2: float, qam: int, n_pe: int, edges, cost):
+    """Best-first table under the table-driven rank model: per level the bin
+    of gamma = R_ll^2 / sigma2 (float32) among the ascending `edges`, costs
+    from `cost` (float32 [n_bins][qam]) -> (paths, score, bins)."""
+    rdiag = np.ascontiguousarray(np.asarray(rdiag, np.float64))
+    edges = np.ascontiguousarray(np.asarray(edges, np.float32))
+    cost = np.ascontiguousarray(np.asarray(cost, np.float32))
+    nt = rdiag.shape[0]
+    n_bins = cost.shape[0]
+    assert edges.shape[0] == n_bins - 1 and cost.shape[1] == qam
+    paths = np.zeros((n_pe, nt), np.uint8)
+    score = np.zeros(n_pe, np.float64)
+    bins = np.zeros(nt, np.int32)
+    _check(_load().orc_select_paths_lut(nt, qam, _p(rdiag), float(sigma2), n_bins, _p(edges),
+                                        _p(cost), n_pe, _p(paths), _p(score), _p(bins)),
+           "select_paths_lut")
+    return paths, score, bins
 
 
 def detect(R, Z, perm, paths, sigma2: float, qam: int, want_all: bool = False,

@@ -54,6 +54,7 @@ typedef double complex cplx;
 /* Reading: the per-level symbol-error probability is floored at this value so
  * that no level is ever treated as error-free (keeps every log finite). */
 #define ORC_PE_FLOOR 1e-12
+#define ORC_PI 3.14159265358979323846
 
 static int bits_of(int qam)
 {
@@ -286,17 +287,13 @@ static int cand_before(const orc_cand *a, const orc_cand *b, int nt)
     return 0;
 }
 
-static int select_paths(int nt, int qam, const double *rdiag, double sigma2, int n_pe,
-                        unsigned char *paths, double *score_out, double *pe_out)
+/* Best-first enumeration over per-level log-probabilities logp[l][k] (rank
+ * k = 1..M at level l), nonincreasing in k so that a child never precedes
+ * its parent.  Shared by the geometric model and the table-driven model. */
+static int select_best_first(int nt, int qam, double logp[ORC_MAX_NT][ORC_MAX_M + 1], int n_pe,
+                             unsigned char *paths, double *score_out)
 {
     int M = qam;
-    double logp[ORC_MAX_NT][ORC_MAX_M + 1];
-    for (int l = 0; l < nt; l++) {
-        double pe = level_pe(rdiag[l], sigma2, M);
-        if (pe_out) pe_out[l] = pe;
-        for (int k = 1; k <= M; k++)
-            logp[l][k] = log(1.0 - pe) + (double)(k - 1) * log(pe);
-    }
     size_t cap = 1 + (size_t)n_pe * (size_t)nt;
     orc_cand *front = (orc_cand *)malloc(cap * sizeof(orc_cand));
     if (!front) return -2;
@@ -341,6 +338,20 @@ static int select_paths(int nt, int qam, const double *rdiag, double sigma2, int
     return 0;
 }
 
+static int select_paths(int nt, int qam, const double *rdiag, double sigma2, int n_pe,
+                        unsigned char *paths, double *score_out, double *pe_out)
+{
+    int M = qam;
+    double logp[ORC_MAX_NT][ORC_MAX_M + 1];
+    for (int l = 0; l < nt; l++) {
+        double pe = level_pe(rdiag[l], sigma2, M);
+        if (pe_out) pe_out[l] = pe;
+        for (int k = 1; k <= M; k++)
+            logp[l][k] = log(1.0 - pe) + (double)(k - 1) * log(pe);
+    }
+    return select_best_first(nt, qam, logp, n_pe, paths, score_out);
+}
+
 static double ipow(double b, int e)
 {
     double r = 1.0;
@@ -355,6 +366,135 @@ int orc_select_paths(int nt, int qam, const double *rdiag, double sigma2, int n_
     if ((double)n_pe > ipow((double)qam, nt)) return -1;
     if (!(sigma2 > 0.0)) return -1;
     return select_paths(nt, qam, rdiag, sigma2, n_pe, paths, score, pe);
+}
+
+/* ---------------------------------------------------------------------------
+ * Table-driven rank model (Reading: the paper gives no model; this is the
+ * alternative to the geometric model above in which the probability of each
+ * rank is estimated once, offline, per SNR, and looked up per level).
+ *
+ * Estimation by Monte-Carlo, per SNR gamma_b (b = 0..n_bins-1): n_trials
+ * draws of a uniformly chosen constellation label s and of complex Gaussian
+ * noise n of total variance 1/gamma_b -- the law of b_l = s + n_l / R_ll in
+ * step 4 when gamma = R_ll^2 / sigma2 and E_s = 1 -- and the rank of s among
+ * all M points ordered by (|b - q|^2, label) is counted: counts[b][k-1].
+ *
+ * Random numbers: SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a
+ * counter-based generator.  Draw number n gives
+ *   z = seed + n * 0x9E3779B97F4A7C15;
+ *   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9;
+ *   z = (z ^ (z >> 27)) * 0x94D049BB133111EB;
+ *   out = z ^ (z >> 31)
+ * with n = 1 + (b << 40) + (t << 2) + i for draw i (0..2) of trial t (t < 2^38).
+ * Draw 0: the label, its top B bits.  Draws 1, 2: u = ((out >> 11) + 0.5)
+ * 2^-53, in (0, 1).  Noise by Box-Muller: r = sqrt(-2 ln u1 / (2 gamma)),
+ * n = r (cos 2 pi u2, sin 2 pi u2).
+ *
+ * Costs (Reading): P(k) = max(counts[k-1], 1/2) / n_trials (half a count for
+ * a rank never seen, so every log is finite), c(k) = log P(1) - log P(k),
+ * then made nondecreasing in k by a running maximum (so the top-N set stays
+ * downward-closed); c(1) = 0.  Selection then maximises -sum_l c_l(p_l),
+ * which orders vectors as sum_l log P_l(p_l) does wherever P is
+ * nonincreasing.
+ *
+ * Lookup: the bin of a level is the number of edges e (ascending, n_bins - 1
+ * of them) with gamma >= e, where gamma = R_ll^2 / sigma2 is formed in
+ * float (R_ll and sigma2 rounded to float first): a float decides the bin, in
+ * the precision the GPU path uses.
+ * ------------------------------------------------------------------------- */
+static uint64_t splitmix64_at(uint64_t seed, uint64_t n)
+{
+    uint64_t z = seed + n * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static double unit_open(uint64_t x)
+{
+    return ((double)(x >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+}
+
+int orc_rank_counts_mc(int qam, int n_bins, const double *gamma, long long n_trials,
+                       unsigned long long seed, long long *counts)
+{
+    int M = qam, B = bits_of(qam);
+    if (!B || n_bins < 1 || n_trials < 1 || n_trials >= (1ll << 38)) return -1;
+    cplx pts[ORC_MAX_M];
+    for (int q = 0; q < M; q++) pts[q] = qam_point(qam, q);
+    for (int b = 0; b < n_bins; b++) {
+        if (!(gamma[b] > 0.0)) return -1;
+        long long *cnt = counts + (size_t)b * M;
+        for (int k = 0; k < M; k++) cnt[k] = 0;
+        double sd = sqrt(1.0 / (2.0 * gamma[b]));
+        for (long long t = 0; t < n_trials; t++) {
+            uint64_t base = 1ull + ((uint64_t)b << 40) + ((uint64_t)t << 2);
+            int s = (int)(splitmix64_at(seed, base) >> (64 - B));
+            double u1 = unit_open(splitmix64_at(seed, base + 1));
+            double u2 = unit_open(splitmix64_at(seed, base + 2));
+            double r = sqrt(-2.0 * log(u1)) * sd;
+            double th = 2.0 * ORC_PI * u2;
+            cplx y = pts[s] + r * cos(th) + I * (r * sin(th));
+            cplx df = y - pts[s];
+            double ds = creal(df) * creal(df) + cimag(df) * cimag(df);
+            int rank = 1;
+            for (int q = 0; q < M; q++) {
+                if (q == s) continue;
+                cplx e = y - pts[q];
+                double dq = creal(e) * creal(e) + cimag(e) * cimag(e);
+                if (dq < ds || (dq == ds && q < s)) rank++;
+            }
+            cnt[rank - 1]++;
+        }
+    }
+    return 0;
+}
+
+int orc_rank_costs(int qam, int n_bins, const long long *counts, long long n_trials, double *cost)
+{
+    int M = qam;
+    if (!bits_of(qam) || n_bins < 1 || n_trials < 1) return -1;
+    for (int b = 0; b < n_bins; b++) {
+        const long long *cnt = counts + (size_t)b * M;
+        double *c = cost + (size_t)b * M;
+        double lp1 = log((cnt[0] > 0 ? (double)cnt[0] : 0.5) / (double)n_trials);
+        c[0] = 0.0;
+        for (int k = 1; k < M; k++) {
+            double lp = log((cnt[k] > 0 ? (double)cnt[k] : 0.5) / (double)n_trials);
+            double v = lp1 - lp;
+            c[k] = v > c[k - 1] ? v : c[k - 1];
+        }
+    }
+    return 0;
+}
+
+static int lut_bin(double rll, double sigma2, int n_bins, const float *edges)
+{
+    float rf = (float)rll, s2 = (float)sigma2;
+    float sq = rf * rf;
+    float g = sq / s2;
+    int b = 0;
+    for (int e = 0; e < n_bins - 1; e++)
+        if (g >= edges[e]) b = e + 1;
+    return b;
+}
+
+int orc_select_paths_lut(int nt, int qam, const double *rdiag, double sigma2, int n_bins,
+                         const float *edges, const float *cost, int n_pe, unsigned char *paths,
+                         double *score, int *bins)
+{
+    if (nt < 1 || nt > ORC_MAX_NT || !bits_of(qam) || n_pe < 1 || n_pe > ORC_MAX_NPE) return -1;
+    if ((double)n_pe > ipow((double)qam, nt)) return -1;
+    if (!(sigma2 > 0.0) || n_bins < 1) return -1;
+    int M = qam;
+    double logp[ORC_MAX_NT][ORC_MAX_M + 1];
+    for (int l = 0; l < nt; l++) {
+        int b = lut_bin(rdiag[l], sigma2, n_bins, edges);
+        if (bins) bins[l] = b;
+        for (int k = 1; k <= M; k++)
+            logp[l][k] = -(double)cost[(size_t)b * M + (k - 1)];
+    }
+    return select_best_first(nt, qam, logp, n_pe, paths, score);
 }
 
 /* ---------------------------------------------------------------------------
