@@ -457,6 +457,12 @@ def run_mpnl(args):
                           "detect_tflops": fl / (dms / 1e3) / 1e12})
             del b2
 
+    # ---- the table-driven rank model beside the geometric one: the table's
+    # build, the selection time and the BER of the slot with each table
+    rank_lut = None
+    if not args.no_sweep:
+        rank_lut = run_rank_lut(args, dev, n_pe)
+
     # ---- mixed-size batch (64 radio units of random sizes) in persistent
     # launches under a CUDA graph, knobs from the autotuner, beside the same
     # units launched one by one
@@ -535,6 +541,7 @@ def run_mpnl(args):
                          "peak_measured_ffma": probe_tflops,
                          "frac_of_measured_ffma": achieved_tflops / probe_tflops},
             "sweep": sweep,
+            "rank_lut": rank_lut,
             "mixed_batch": mixed,
             "serving": serving_res,
             "cpu_baseline": cpu,
@@ -549,6 +556,61 @@ def run_mpnl(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def run_rank_lut(args, dev, n_pe):
+    """Table-driven rank model on the bench workload: build a table (0.5 dB
+    bins from -10 to 40 dB, 2^20 Monte-Carlo trials each) on the GPU, time
+    mpnl_select_paths_lut against mpnl_select_paths on one slot, and compare
+    the BER of the whole GPU path with either table."""
+    import torch
+
+    from paper_2409_14355_gb300 import mpnl
+
+    sl = inputs.workload_slot(args.workload, args.snr_index, n_sc=args.n_sc)
+    qam, nt, nr = sl.qam, sl.nt, sl.nr
+    n_sc, n_sym = sl.H.shape[0], sl.Y.shape[1]
+    B = {4: 2, 16: 4, 64: 6}[qam]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    trials = 1 << 20
+    e0.record()
+    lut = mpnl.RankLut.build(qam, -10.0, 40.0, 0.5, n_trials=trials, device=dev)
+    e1.record()
+    torch.cuda.synchronize()
+    build_ms = e0.elapsed_time(e1)
+    H = torch.from_numpy(sl.H).to(dev)
+    Y = torch.from_numpy(sl.Y).to(dev)
+    R, invd, perm, Z = mpnl.preprocess(H, Y)
+    pg = mpnl.select_paths(R, sl.sigma2, qam, n_pe, nt)
+    pt = mpnl.select_paths_lut(R, sl.sigma2, lut, n_pe, nt)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_g = timed(lambda: mpnl.select_paths(R, sl.sigma2, qam, n_pe, nt, out=pg))
+    ms_t = timed(lambda: mpnl.select_paths_lut(R, sl.sigma2, lut, n_pe, nt, out=pt))
+    labels = sl.labels
+
+    def ber(paths):
+        hard, _, _ = mpnl.detect(R, invd, perm, paths, Z, sl.sigma2, qam, want_llr=False)
+        h = hard.cpu().numpy()
+        e = sum(int(np.sum(((h >> (B - 1 - b)) & 1) != ((labels >> (B - 1 - b)) & 1)))
+                for b in range(B))
+        return e / (labels.size * B)
+
+    differ = (pg != pt).flatten(1).any(dim=1).float().mean().item()
+    mpnl.check_status(dev.index)
+    return {"bins": lut.n_bins, "db_range": [-10.0, 40.0, 0.5], "trials_per_bin": trials,
+            "build_ms": build_ms, "select_ms_geometric": ms_g, "select_ms_table": ms_t,
+            "tables_differ_frac": differ, "ber_geometric": ber(pg), "ber_table": ber(pt)}
 
 
 def accuracy_vs_oracle(sl, ref, n_used, qam, n_pe, dev):

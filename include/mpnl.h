@@ -13,6 +13,7 @@
  * The path, per subcarrier (sc) and OFDM symbol, with y = H s + n:
  *   mpnl_preprocess    sorted QR  H P = Q R  and  z = Q^H y
  *   mpnl_select_paths  the N_pe most probable position vectors per sc
+ *                      (mpnl_select_paths_lut: with a table of rank costs)
  *   mpnl_detect        N_pe SIC / partial-Euclidean-distance walks, argmin
  *                      -> hard decisions, max-log LLRs over the list
  *   mpnl_linear_mmse   linear MMSE baseline (hard decisions + LLRs)
@@ -161,6 +162,50 @@ int mpnl_refine_qr(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const vo
  *   paths  out u8  [n_sc][n_pe][nt]     ranks 1..qam, level index last */
 int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, float sigma2,
                       uint8_t *paths, void *ws, void *stream);
+
+/* Table-driven rank model (a reading: the paper gives no per-level model;
+ * this is the FlexCore-style alternative to the geometric model above).  The
+ * chance that the transmitted symbol is the k-th closest is estimated once
+ * per SNR, offline, and looked up per level: the table's bin for level l is
+ * the number of edges e with gamma_l = R_ll^2 / sigma2 >= e (float), and the
+ * N_pe vectors of smallest sum_l cost[bin_l][p_l - 1] are written in the
+ * order and with the tie rule of mpnl_select_paths.
+ *   qam, n_bins  the table's constellation (must equal dims->qam) and bins
+ *   edges  in  f32 [n_bins - 1]     ascending linear SNRs (device)
+ *   cost   in  f32 [n_bins][qam]    c(k) at k - 1: c(1) = 0, nondecreasing in
+ *                                   k, finite (device; mpnl_rank_costs)  */
+typedef struct {
+    int qam, n_bins;
+    const float *edges;
+    const float *cost;
+} mpnl_rank_lut;
+
+/* Errors: as mpnl_select_paths; a table whose qam differs from dims->qam,
+ * n_bins < 1 or NULL arrays.  Rows that break the cost rules are the
+ * caller's error and give an unspecified (but bounded, in-range) table. */
+int mpnl_select_paths_lut(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, float sigma2,
+                          const mpnl_rank_lut *lut, uint8_t *paths, void *ws, void *stream);
+
+/* Monte-Carlo rank histogram for the table: for each of n_bins SNRs
+ * gamma[b] (linear), n_trials draws of a uniform symbol and of complex
+ * Gaussian noise of variance 1/gamma[b] (the law of b_l = s + n_l / R_ll),
+ * counting the rank of the sent symbol among all qam points by (distance,
+ * label).  Random numbers: SplitMix64 used as a counter-based generator
+ * keyed by (seed, bin, trial), so the table depends only on its arguments.
+ *   gamma   in   f64 [n_bins]        (device), all > 0
+ *   counts  out  u64 [n_bins][qam]   (device), zeroed first
+ * Errors: qam not 4/16/64, n_bins < 1 or > 65535, n_trials < 1 or >= 2^38,
+ * NULL or host pointers. */
+int mpnl_rank_counts(mpnl_ctx *ctx, int qam, int n_bins, const double *gamma, long long n_trials,
+                     unsigned long long seed, unsigned long long *counts, void *stream);
+
+/* Rank costs from the histogram (a reading): P(k) = max(counts, 1/2) /
+ * n_trials, c(k) = log P(1) - log P(k), made nondecreasing in k by a running
+ * maximum, c(1) = 0 -- the cost table of mpnl_select_paths_lut.
+ *   counts  in   u64 [n_bins][qam];  cost  out  f32 [n_bins][qam]  (device)
+ * Errors: as mpnl_rank_counts. */
+int mpnl_rank_costs(mpnl_ctx *ctx, int qam, int n_bins, const unsigned long long *counts,
+                    long long n_trials, float *cost, void *stream);
 
 /* Evaluation of the position vectors (§II: the most promising solutions
  * "processed in parallel").  For every (sc, symbol) and every row p of the

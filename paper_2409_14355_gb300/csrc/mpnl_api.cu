@@ -649,6 +649,68 @@ int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, float si
     return MPNL_OK;
 }
 
+int mpnl_select_paths_lut(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, float sigma2,
+                          const mpnl_rank_lut *lut, uint8_t *paths, void *ws, void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_dims(ctx, d, true));
+    MPNL_TRY(check_sigma2(ctx, sigma2));
+    if (!lut) return fail(ctx, MPNL_ERR_INVALID_ARG, "lut is NULL");
+    if (lut->qam != d->qam)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "table qam=%d differs from dims qam=%d", lut->qam,
+                    d->qam);
+    if (lut->n_bins < 1 || lut->n_bins > 65535)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "n_bins=%d outside 1..65535", lut->n_bins);
+    if (d->n_sc == 0) return MPNL_OK;
+    MPNL_TRY(check_ptr(ctx, R, 8, "R", false));
+    MPNL_TRY(check_ptr(ctx, paths, 1, "paths", false));
+    MPNL_TRY(check_ptr(ctx, lut->cost, 4, "cost", false));
+    MPNL_TRY(check_ptr(ctx, lut->edges, 4, "edges", lut->n_bins == 1));
+    cudaError_t e = mpnl::launch_select_paths_lut(d->n_sc, d->nt, d->qam, d->n_pe, sigma2,
+                                                  (const float2 *)R, lut->edges, lut->cost,
+                                                  lut->n_bins, paths, tuned_select_warps(ctx, d),
+                                                  (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "select_paths_lut launch", e);
+    return MPNL_OK;
+}
+
+static int check_lut_args(mpnl_ctx *ctx, int qam, int n_bins, long long n_trials)
+{
+    if (!bits_of(qam)) return fail(ctx, MPNL_ERR_INVALID_ARG, "qam=%d not in {4,16,64}", qam);
+    if (n_bins < 1 || n_bins > 65535)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "n_bins=%d outside 1..65535", n_bins);
+    if (n_trials < 1 || n_trials >= (1ll << 38))
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "n_trials=%lld outside 1..2^38-1", n_trials);
+    return MPNL_OK;
+}
+
+int mpnl_rank_counts(mpnl_ctx *ctx, int qam, int n_bins, const double *gamma, long long n_trials,
+                     unsigned long long seed, unsigned long long *counts, void *stream)
+{
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_lut_args(ctx, qam, n_bins, n_trials));
+    MPNL_TRY(check_ptr(ctx, gamma, 8, "gamma", false));
+    MPNL_TRY(check_ptr(ctx, counts, 8, "counts", false));
+    cudaError_t e = mpnl::launch_rank_counts(qam, n_bins, gamma, n_trials, seed, counts,
+                                             (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "rank_counts launch", e);
+    return MPNL_OK;
+}
+
+int mpnl_rank_costs(mpnl_ctx *ctx, int qam, int n_bins, const unsigned long long *counts,
+                    long long n_trials, float *cost, void *stream)
+{
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_lut_args(ctx, qam, n_bins, n_trials));
+    MPNL_TRY(check_ptr(ctx, counts, 8, "counts", false));
+    MPNL_TRY(check_ptr(ctx, cost, 4, "cost", false));
+    cudaError_t e = mpnl::launch_rank_costs(qam, n_bins, counts, n_trials, cost,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "rank_costs launch", e);
+    return MPNL_OK;
+}
+
 static int detect_impl(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, const float *inv_diag,
                        const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
                        uint8_t *hard, float *llr, float *ped2, void *stream, bool f16)

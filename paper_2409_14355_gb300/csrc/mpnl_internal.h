@@ -47,6 +47,21 @@ cudaError_t launch_qhy(int n_sc, int n_sym, int nr, int nt, const float2 *Q, con
 cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,
                                 const float2 *R, uint8_t *paths, int warps, cudaStream_t stream);
 
+// Table-driven rank model (mpnl_select_paths_lut): edges [n_bins - 1],
+// cost [n_bins][qam], device pointers.
+cudaError_t launch_select_paths_lut(int n_sc, int nt, int qam, int n_pe, float sigma2,
+                                    const float2 *R, const float *edges, const float *cost,
+                                    int n_bins, uint8_t *paths, int warps, cudaStream_t stream);
+
+// Monte-Carlo rank histogram (mpnl_rank_counts): counts [n_bins][qam] are
+// zeroed and filled; gamma [n_bins] device doubles.
+cudaError_t launch_rank_counts(int qam, int n_bins, const double *gamma, long long n_trials,
+                               unsigned long long seed, unsigned long long *counts,
+                               cudaStream_t stream);
+// Rank costs from the histogram (mpnl_rank_costs): cost [n_bins][qam].
+cudaError_t launch_rank_costs(int qam, int n_bins, const unsigned long long *counts,
+                              long long n_trials, float *cost, cudaStream_t stream);
+
 // f16: residuals in half2 with FP32 ranking / PED and an FP32 re-check of
 // the best and runner-up paths (mpnl_detect_mixed); false: all FP32.
 // sym: symbols per lane (1 or 2; a tuning knob, results do not depend on it).

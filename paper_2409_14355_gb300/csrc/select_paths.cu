@@ -72,15 +72,27 @@ __device__ __forceinline__ void group_sync(int group)
     }
 }
 
+// Table-driven rank model (mpnl_select_paths_lut): the cost of rank 1 + j
+// at level l is a row of a caller's table instead of j w_l.  The row is the
+// level's SNR bin: the number of the ascending edges e with
+// gamma_l = R_ll^2 / sigma2 >= e (all in float).  Rows start at 0 and are
+// nondecreasing, which is all the merges below need.
+struct RankLut {
+    const float *edges;  // [n_bins - 1]
+    const float *cost;   // [n_bins][qam]
+    int n_bins;
+};
+
 // One subcarrier by one group of G warps (thread tid of the group, which is
 // group number `group` of its CTA), in the group's shared-memory region at
 // byte offset base_off (at least sel_group_bytes(n_pe)).  Inlined into
-// the per-call and the batch kernels alike (no contraction).
-template <int QAM, int G>
+// the per-call and the batch kernels alike (no contraction).  LUT: costs
+// from the table `lut` (else the geometric model, w_l = -log Pe_l).
+template <int QAM, int G, bool LUT = false>
 __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, float sigma2,
                                                const float2 *__restrict__ Rp,
                                                uint8_t *__restrict__ paths, int base_off,
-                                               int group, int tid)
+                                               int group, int tid, RankLut lut = RankLut{})
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = smem_raw + base_off;
@@ -98,7 +110,16 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
 #define cost(b) (CO + (size_t)(b) * n_pe)
 
     const int P = nt * (nt + 1) / 2;
-    if (tid < nt) {
+    if (LUT && tid < nt) {  // w[l] holds the level's table row (its bin)
+        const int l = tid;
+        const float rll = Rp[(size_t)sc * P + l * nt - l * (l - 1) / 2].x;
+        const float sq = rll * rll;
+        const float gamma = sq / sigma2;
+        int b = 0;
+        for (int e = 0; e < lut.n_bins - 1; ++e)
+            if (gamma >= __ldg(lut.edges + e)) b = e + 1;
+        w[l] = __int_as_float(b);
+    } else if (!LUT && tid < nt) {
         const int l = tid;
         const float rll = Rp[(size_t)sc * P + l * nt - l * (l - 1) / 2].x;
         const float gamma = rll * rll / sigma2;
@@ -111,6 +132,11 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         w[l] = -logf(pe);
     }
     group_sync<G>(group);
+    // cost of rank 1 + j at level m
+    auto shift_cost = [&](int m, int j) -> float {
+        if constexpr (LUT) return __ldg(lut.cost + (size_t)__float_as_int(w[m]) * QAM + j);
+        else return (float)j * w[m];
+    };
     // Upper bound on the final N_pe-th cost: the vectors that deviate from
     // all-ones at a single level (cost j w_l) plus all-ones itself are valid
     // vectors, so if N_pe of them cost <= v, the answer's N_pe-th cost is
@@ -122,7 +148,40 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     // w_m is formed with a rounded reciprocal (relative error below 2^-22 <<
     // 1e-6), so the quotient stays below the exact v / w_m and its floor
     // cannot overshoot.
-    if (tid < 32) {
+    if (LUT && tid < 32) {
+        // the same bound with the table's rows: count(v) = 1 + the number of
+        // (m, j >= 1) with cost(m, j) <= v, a binary search per row (rows are
+        // nondecreasing); exact comparisons, no rounding to guard against
+        unsigned bbits = 0x7f800000u;
+        if (tid < nt) {
+            const int l = tid;
+            auto count = [&](float v) {
+                int cnt = 1;
+                for (int m = 0; m < nt; ++m) {
+                    int lo_j = 0, hi_j = QAM - 1;  // cost(m, 0) = 0 <= v
+                    while (lo_j < hi_j) {
+                        const int mid = (lo_j + hi_j + 1) >> 1;
+                        if (shift_cost(m, mid) <= v) lo_j = mid;
+                        else hi_j = mid - 1;
+                    }
+                    cnt += lo_j;
+                }
+                return cnt;
+            };
+            if (count(shift_cost(l, QAM - 1)) >= n_pe) {
+                int lo_j = 1, hi_j = QAM - 1;
+                while (lo_j < hi_j) {
+                    const int mid = (lo_j + hi_j) >> 1;
+                    if (count(shift_cost(l, mid)) >= n_pe) hi_j = mid;
+                    else lo_j = mid + 1;
+                }
+                const float v = shift_cost(l, lo_j);
+                bbits = __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f);
+            }
+        }
+        bbits = __reduce_min_sync(FULL, bbits);
+        if (tid == 0) *s_bound = bbits;
+    } else if (!LUT && tid < 32) {
         unsigned bbits = 0x7f800000u;  // +inf
         if (tid < nt) {
             const float wl = w[tid];
@@ -162,8 +221,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     int li = 0, nL = 1;
     {
         const int mt = nt - 1;
-        const float wt = w[mt];
-        while (nL < QAM && nL < n_pe && (float)nL * wt <= bound) ++nL;
+        while (nL < QAM && nL < n_pe && shift_cost(mt, nL) <= bound) ++nL;
         unsigned long long h = 0, o = 0;
         for (int l = 0; l < nt; ++l) {
             bool in_hi;
@@ -179,12 +237,11 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
             const unsigned long long add = (unsigned long long)j << sh;
             hi(0)[j] = h + (in_hi ? add : 0ull);
             lo(0)[j] = o + (in_hi ? 0ull : add);
-            cost(0)[j] = (float)j * wt;
+            cost(0)[j] = shift_cost(mt, j);
         }
     }
     group_sync<G>(group);
     for (int m = nt - 2; m >= 0; --m) {
-        const float wm = w[m];
         bool in_hi;
         int sh;
         level_shift(nt, m, in_hi, sh);
@@ -192,7 +249,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         int oi = (li + 1) % 3;         // first output buffer
         for (int j = 1; j < QAM; ++j) {
             const unsigned long long add = (unsigned long long)j << sh;
-            const float cj = (float)j * wm;
+            const float cj = shift_cost(m, j);
             if (cj > bound) break;
             // first entry of the shifted list vs the last entry of B
             {
@@ -280,6 +337,19 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
                               group * (int)sel_group_bytes(n_pe), group, tid);
 }
 
+template <int QAM, int G>
+__global__ void __launch_bounds__(kSelMaxWarps * 32)
+select_paths_lut_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
+                        uint8_t *__restrict__ paths, RankLut lut)
+{
+    constexpr int T = 32 * G;
+    const int group = threadIdx.x / T, tid = threadIdx.x % T;
+    const int sc = blockIdx.x * (blockDim.x / T) + group;
+    if (sc >= n_sc) return;
+    select_group_body<QAM, G, true>(sc, nt, n_pe, sigma2, Rp, paths,
+                                    group * (int)sel_group_bytes(n_pe), group, tid, lut);
+}
+
 // Persistent variant over a batch of radio units of mixed sizes: every
 // group takes (unit, subcarrier) work items from a global counter.
 template <int G>
@@ -307,6 +377,22 @@ select_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__
         default: select_group_body<64, G>(sc, it.nt, it.n_pe, it.sigma2, it.R, it.paths, base, group, tid); break;
         }
     }
+}
+
+template <int QAM, int G>
+cudaError_t launch_group_lut(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
+                             uint8_t *paths, RankLut lut, cudaStream_t stream)
+{
+    const size_t per = sel_group_bytes(n_pe);
+    int groups = (int)((100 * 1024) / per);
+    groups = groups < 1 ? 1 : (groups > kSelMaxWarps / G ? kSelMaxWarps / G : groups);
+    const size_t smem = per * groups;
+    cudaError_t e = allow_dynamic_smem(select_paths_lut_kernel<QAM, G>, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (n_sc + groups - 1) / groups;
+    select_paths_lut_kernel<QAM, G><<<grid, groups * G * 32, smem, stream>>>(n_sc, nt, n_pe,
+                                                                            sigma2, R, paths, lut);
+    return cudaGetLastError();
 }
 
 template <int QAM, int G>
@@ -362,6 +448,25 @@ cudaError_t launch_select_batch(const BatchItem *items, const int *start, int n_
     if (warps == 4) return launch_select_batch_g<4>(items, start, n_items, counter, group_bytes, grid, stream);
     if (warps == 2) return launch_select_batch_g<2>(items, start, n_items, counter, group_bytes, grid, stream);
     return launch_select_batch_g<1>(items, start, n_items, counter, group_bytes, grid, stream);
+}
+
+cudaError_t launch_select_paths_lut(int n_sc, int nt, int qam, int n_pe, float sigma2,
+                                    const float2 *R, const float *edges, const float *cost,
+                                    int n_bins, uint8_t *paths, int warps, cudaStream_t stream)
+{
+    if (n_sc == 0) return cudaSuccess;
+    const RankLut lut{edges, cost, n_bins};
+    const int g = warps == 4 ? 4 : (warps == 2 ? 2 : 1);
+#define MPNL_SEL_LUT(Q)                                                                     \
+    return g == 4 ? launch_group_lut<Q, 4>(n_sc, nt, n_pe, sigma2, R, paths, lut, stream)   \
+         : g == 2 ? launch_group_lut<Q, 2>(n_sc, nt, n_pe, sigma2, R, paths, lut, stream)   \
+                  : launch_group_lut<Q, 1>(n_sc, nt, n_pe, sigma2, R, paths, lut, stream)
+    switch (qam) {
+    case 4: MPNL_SEL_LUT(4);
+    case 16: MPNL_SEL_LUT(16);
+    default: MPNL_SEL_LUT(64);
+    }
+#undef MPNL_SEL_LUT
 }
 
 cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,

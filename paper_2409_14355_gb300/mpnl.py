@@ -39,13 +39,20 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_detect_mixed",
             "mpnl_linear_mmse", "mpnl_check_status", "mpnl_probe_ffma", "mpnl_set_tuning",
             "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy",
-            "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr")
+            "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr",
+            "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16 = 1, 2, 4
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
 RUN_GRAPH = 16
 RESET_TRUSTED_POINTERS = 1
 PRECISIONS = ("fp32", "fp16")
+
+
+class RankLutC(ctypes.Structure):
+    """mpnl_rank_lut."""
+    _fields_ = [("qam", ctypes.c_int), ("n_bins", ctypes.c_int),
+                ("edges", ctypes.c_void_p), ("cost", ctypes.c_void_p)]
 
 
 class MpnlError(RuntimeError):
@@ -112,6 +119,13 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_preprocess_mmse.restype = I
         lib.mpnl_select_paths.argtypes = [P, D, P, F, P, P, P]
         lib.mpnl_select_paths.restype = I
+        lib.mpnl_select_paths_lut.argtypes = [P, D, P, F, ctypes.POINTER(RankLutC), P, P, P]
+        lib.mpnl_select_paths_lut.restype = I
+        LL, ULL = ctypes.c_longlong, ctypes.c_ulonglong
+        lib.mpnl_rank_counts.argtypes = [P, I, I, P, LL, ULL, P, P]
+        lib.mpnl_rank_counts.restype = I
+        lib.mpnl_rank_costs.argtypes = [P, I, I, P, LL, P, P]
+        lib.mpnl_rank_costs.restype = I
         lib.mpnl_detect.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
         lib.mpnl_detect.restype = I
         lib.mpnl_detect_mixed.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
@@ -285,6 +299,87 @@ def select_paths(R: torch.Tensor, sigma2: float, qam: int, n_pe: int, nt: int, o
     st = load_library().mpnl_select_paths(ctx, ctypes.byref(d), _ptr(R), float(sigma2),
                                           _ptr(paths), None, _stream(dev))
     _raise(st, ctx)
+    return paths
+
+
+def rank_counts(qam: int, gamma: torch.Tensor, n_trials: int, seed: int, out=None):
+    """Monte-Carlo rank histogram u64 (as int64) [n_bins][qam] for the linear
+    SNRs `gamma` (f64 device tensor) (mpnl_rank_counts)."""
+    dev = _dev_of(gamma)
+    _need(gamma, torch.float64, (gamma.shape[0],), "gamma")
+    n_bins = gamma.shape[0]
+    counts = out if out is not None else torch.empty((n_bins, qam), dtype=torch.int64, device=dev)
+    ctx = context(dev.index)
+    _raise(load_library().mpnl_rank_counts(ctx, qam, n_bins, _ptr(gamma), int(n_trials),
+                                           ctypes.c_ulonglong(seed), _ptr(counts), _stream(dev)),
+           ctx)
+    return counts
+
+
+def rank_costs(counts: torch.Tensor, n_trials: int, out=None):
+    """Rank costs f32 [n_bins][qam] from a histogram (mpnl_rank_costs)."""
+    dev = _dev_of(counts)
+    n_bins, qam = counts.shape
+    _need(counts, torch.int64, (n_bins, qam), "counts")
+    cost = out if out is not None else torch.empty((n_bins, qam), dtype=torch.float32, device=dev)
+    ctx = context(dev.index)
+    _raise(load_library().mpnl_rank_costs(ctx, qam, n_bins, _ptr(counts), int(n_trials),
+                                          _ptr(cost), _stream(dev)), ctx)
+    return cost
+
+
+class RankLut:
+    """A rank-cost table on the device: `edges` f32 [n_bins - 1] (ascending
+    linear SNRs) and `cost` f32 [n_bins][qam]."""
+
+    def __init__(self, qam: int, edges: torch.Tensor, cost: torch.Tensor):
+        self.qam = qam
+        self.edges = edges
+        self.cost = cost
+        self.n_bins = cost.shape[0]
+        if edges.shape[0] != self.n_bins - 1 or cost.shape[1] != qam:
+            raise ValueError("edges must hold n_bins - 1 values and cost [n_bins][qam]")
+
+    @classmethod
+    def build(cls, qam: int, db_min: float = -10.0, db_max: float = 40.0, db_step: float = 0.5,
+              n_trials: int = 1 << 20, seed: int = 0x2409_14355, device=None) -> "RankLut":
+        """Bins centred every db_step dB from db_min to db_max, the edges
+        half-way between centres (in dB); costs from n_trials Monte-Carlo
+        trials per bin, on the GPU."""
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None
+                           else torch.device(device).index or 0)
+        n_bins = int(round((db_max - db_min) / db_step)) + 1
+        centres = [db_min + b * db_step for b in range(n_bins)]
+        gamma = torch.tensor([10.0 ** (c / 10.0) for c in centres], dtype=torch.float64,
+                             device=dev)
+        edges = torch.tensor([10.0 ** ((c + 0.5 * db_step) / 10.0) for c in centres[:-1]],
+                             dtype=torch.float32, device=dev)
+        with torch.cuda.device(dev):
+            counts = rank_counts(qam, gamma, n_trials, seed)
+            cost = rank_costs(counts, n_trials)
+        lut = cls(qam, edges, cost)
+        lut.counts, lut.gamma = counts, gamma
+        return lut
+
+    def c_struct(self) -> RankLutC:
+        return RankLutC(self.qam, self.n_bins,
+                        self.edges.data_ptr() if self.edges.numel() else None,
+                        self.cost.data_ptr())
+
+
+def select_paths_lut(R: torch.Tensor, sigma2: float, lut: RankLut, n_pe: int, nt: int, out=None):
+    """Position-vector table u8 [n_sc][n_pe][nt] under the table-driven rank
+    model (mpnl_select_paths_lut)."""
+    dev = _dev_of(R)
+    n_sc = R.shape[0]
+    _need(R, torch.complex64, (n_sc, nt * (nt + 1) // 2), "R")
+    paths = out if out is not None else torch.empty((n_sc, n_pe, nt), dtype=torch.uint8, device=dev)
+    ctx = context(dev.index)
+    d = Dims(n_sc, 1, nt, nt, lut.qam, n_pe)
+    c = lut.c_struct()
+    _raise(load_library().mpnl_select_paths_lut(ctx, ctypes.byref(d), _ptr(R), float(sigma2),
+                                                ctypes.byref(c), _ptr(paths), None, _stream(dev)),
+           ctx)
     return paths
 
 
