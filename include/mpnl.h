@@ -303,6 +303,10 @@ typedef struct {
 #define MPNL_STAGE_DETECT 4
 #define MPNL_STAGE_MMSE 8
 #define MPNL_RUN_GRAPH 16  /* capture the stages into a CUDA graph once, then replay it */
+/* leave room on every SM for other work (e.g. a higher-priority stream's
+ * launches): the walk stage runs one CTA per SM fewer than tuned (at least
+ * one), the other stages half their workers; results are unchanged */
+#define MPNL_RUN_SHARE_SMS 64
 #define MPNL_STAGE_QHY 32
 #define MPNL_STAGES_ALL 47
 
@@ -332,9 +336,9 @@ int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
 int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *batch, const mpnl_batch_item *items,
                      int n_items, int flags);
 
-/* Enqueue the stages in `stages` (MPNL_STAGE_* bits, in pipeline order) on
- * `stream`; with MPNL_RUN_GRAPH the stream must not be the legacy default
- * stream (NULL).  Device-side argument errors go to mpnl_check_status. */
+/* Enqueue the stages in `stages` (MPNL_STAGE_* bits, in pipeline order,
+ * optionally with MPNL_RUN_GRAPH and MPNL_RUN_SHARE_SMS) on `stream`; with
+ * MPNL_RUN_GRAPH the stream must not be the legacy default stream (NULL).  Device-side argument errors go to mpnl_check_status. */
 int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *batch, int stages, void *stream);
 
 /* Release a batch (NULL is ignored); its work must have completed. */

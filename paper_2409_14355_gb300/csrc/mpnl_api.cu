@@ -143,6 +143,7 @@ int begin(mpnl_ctx *ctx)
 
 // Stage slots of a batch, in execution order.
 enum BatchStage { kBPre, kBSel, kBQhy, kBDet, kBMmse, kBStages };
+constexpr int kGraphSlots = 2 * (MPNL_STAGES_ALL + 1);
 static const int kStageBit[kBStages] = {MPNL_STAGE_PREPROCESS, MPNL_STAGE_SELECT, MPNL_STAGE_QHY,
                                         MPNL_STAGE_DETECT, MPNL_STAGE_MMSE};
 
@@ -162,7 +163,7 @@ struct mpnl_batch {
     size_t det_smem;
     int sel_warps, det_ctas;
     int sms;
-    cudaGraphExec_t graph[MPNL_STAGES_ALL + 1];
+    cudaGraphExec_t graph[kGraphSlots];  // by stage mask, and MPNL_RUN_SHARE_SMS
 };
 
 namespace {
@@ -316,7 +317,7 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
     b->det_smem = det;
     b->sel_warps = sel_warps;
     b->det_ctas = det_ctas;
-    for (int k = 0; k <= MPNL_STAGES_ALL; ++k)
+    for (int k = 0; k < kGraphSlots; ++k)
         if (b->graph[k]) {
             cudaGraphExecDestroy(b->graph[k]);
             b->graph[k] = nullptr;
@@ -339,8 +340,13 @@ int upload_batch(mpnl_ctx *ctx, mpnl_batch *b, cudaStream_t st)
     return MPNL_OK;
 }
 
-int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st)
+// share: leave room on every SM for other work (MPNL_RUN_SHARE_SMS): the walk
+// stage runs one CTA per SM fewer than tuned (at least one), the warp- and
+// group-worker stages half their workers.
+int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st, bool share)
 {
+    const int workers = share ? b->sms * 2 : b->sms * 4;
+    const int det_ctas = share && b->det_ctas > 1 ? b->det_ctas - 1 : b->det_ctas;
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, kBStages * sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(ctx, "batch counter reset", e);
     const int cap1 = b->capacity + 1;
@@ -349,27 +355,27 @@ int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st)
     const int n = b->n_items;
     if ((stages & MPNL_STAGE_PREPROCESS) && b->stage_units[kBPre]) {
         e = mpnl::launch_preprocess_batch(b->d_items, start[kBPre], n, b->d_counters + kBPre,
-                                          b->pre_warp_bytes, b->sms * 4, st);
+                                          b->pre_warp_bytes, workers, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch preprocess launch", e);
     }
     if ((stages & MPNL_STAGE_SELECT) && b->stage_units[kBSel]) {
         e = mpnl::launch_select_batch(b->d_items, start[kBSel], n, b->d_counters + kBSel,
-                                      b->sel_group_bytes, b->sel_warps, b->sms * 4, st);
+                                      b->sel_group_bytes, b->sel_warps, workers, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch select launch", e);
     }
     if ((stages & MPNL_STAGE_QHY) && b->stage_units[kBQhy]) {
         e = mpnl::launch_qhy_batch(b->d_items, start[kBQhy], n, b->d_counters + kBQhy,
-                                   b->qhy_warp_bytes, b->sms * 4, st);
+                                   b->qhy_warp_bytes, workers, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch qhy launch", e);
     }
     if ((stages & MPNL_STAGE_DETECT) && b->stage_units[kBDet]) {
         e = mpnl::launch_detect_batch(b->d_items, start[kBDet], n, b->d_counters + kBDet,
-                                      ctx->status, b->det_smem, b->sms * b->det_ctas, st);
+                                      ctx->status, b->det_smem, b->sms * det_ctas, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch detect launch", e);
     }
     if ((stages & MPNL_STAGE_MMSE) && b->stage_units[kBMmse]) {
         e = mpnl::launch_mmse_batch(b->d_items, start[kBMmse], n, b->d_counters + kBMmse,
-                                    b->mmse_warp_bytes, b->sms * 4, st);
+                                    b->mmse_warp_bytes, workers, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch mmse launch", e);
     }
     return MPNL_OK;
@@ -434,17 +440,19 @@ int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *b, int stages, void *stream)
     if (b->device != ctx->device)
         return fail(ctx, MPNL_ERR_INVALID_ARG, "batch lives on device %d, context on %d", b->device,
                     ctx->device);
-    if (stages & ~(MPNL_STAGES_ALL | MPNL_RUN_GRAPH))
+    if (stages & ~(MPNL_STAGES_ALL | MPNL_RUN_GRAPH | MPNL_RUN_SHARE_SMS))
         return fail(ctx, MPNL_ERR_INVALID_ARG, "unknown stage bits 0x%x", stages);
     const int mask = stages & MPNL_STAGES_ALL;
+    const bool share = (stages & MPNL_RUN_SHARE_SMS) != 0;
+    const int slot = mask + (share ? MPNL_STAGES_ALL + 1 : 0);
     cudaStream_t st = (cudaStream_t)stream;
     MPNL_TRY(upload_batch(ctx, b, st));
-    if (!(stages & MPNL_RUN_GRAPH)) return enqueue_batch(ctx, b, mask, st);
+    if (!(stages & MPNL_RUN_GRAPH)) return enqueue_batch(ctx, b, mask, st, share);
     if (!st) return fail(ctx, MPNL_ERR_INVALID_ARG, "graph capture needs a non-default stream");
-    if (!b->graph[mask]) {
+    if (!b->graph[slot]) {
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(ctx, "graph capture begin", e);
-        const int rc = enqueue_batch(ctx, b, mask, st);
+        const int rc = enqueue_batch(ctx, b, mask, st, share);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
         if (rc != MPNL_OK) {
@@ -452,14 +460,14 @@ int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *b, int stages, void *stream)
             return rc;
         }
         if (e != cudaSuccess) return cuda_fail(ctx, "graph capture end", e);
-        e = cudaGraphInstantiate(&b->graph[mask], g, 0);
+        e = cudaGraphInstantiate(&b->graph[slot], g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) {
-            b->graph[mask] = nullptr;
+            b->graph[slot] = nullptr;
             return cuda_fail(ctx, "graph instantiate", e);
         }
     }
-    cudaError_t e = cudaGraphLaunch(b->graph[mask], st);
+    cudaError_t e = cudaGraphLaunch(b->graph[slot], st);
     if (e != cudaSuccess) return cuda_fail(ctx, "graph launch", e);
     return MPNL_OK;
 }
@@ -470,7 +478,7 @@ void mpnl_batch_destroy(mpnl_batch *b)
     int prev = -1;
     cudaGetDevice(&prev);
     cudaSetDevice(b->device);
-    for (int k = 0; k <= MPNL_STAGES_ALL; ++k)
+    for (int k = 0; k < kGraphSlots; ++k)
         if (b->graph[k]) cudaGraphExecDestroy(b->graph[k]);
     if (b->d_items) cudaFree(b->d_items);
     if (b->d_start) cudaFree(b->d_start);

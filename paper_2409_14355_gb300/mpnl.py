@@ -45,6 +45,7 @@ ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16 = 1, 2, 4
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
 RUN_GRAPH = 16
+RUN_SHARE_SMS = 64
 RESET_TRUSTED_POINTERS = 1
 PRECISIONS = ("fp32", "fp16")
 
@@ -686,11 +687,13 @@ class Batch:
                                                RESET_TRUSTED_POINTERS if trusted_pointers else 0),
                self._ctx)
 
-    def run(self, stages: int = STAGES_ALL, graph: bool = False, stream=None) -> None:
+    def run(self, stages: int = STAGES_ALL, graph: bool = False, stream=None,
+            share_sms: bool = False) -> None:
         """Enqueue the stages on `stream` (default: the current stream; a
-        graph needs a non-default stream)."""
+        graph needs a non-default stream).  share_sms leaves room on every SM
+        for other streams' work (MPNL_RUN_SHARE_SMS)."""
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
-        flags = stages | (RUN_GRAPH if graph else 0)
+        flags = stages | (RUN_GRAPH if graph else 0) | (RUN_SHARE_SMS if share_sms else 0)
         _raise(load_library().mpnl_batch_run(self._ctx, self._h, flags,
                                              ctypes.c_void_p(st.cuda_stream)), self._ctx)
 

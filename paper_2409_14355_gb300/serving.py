@@ -123,7 +123,8 @@ class _Round:
     def __init__(self, server, slot_index: int):
         self.server = server
         self.index = slot_index
-        self._stream = None
+        self._streams = {}
+        self.big = False
         self.batch = None
         self.requests: list[Request] = []
         self.buffers: list = []
@@ -131,11 +132,17 @@ class _Round:
         self.event = None
         self.round_id = -1
 
-    @property
-    def stream(self):
-        if self._stream is None:  # created on first use (the loop's logic needs no GPU)
-            self._stream = torch.cuda.Stream(self.server.device)
-        return self._stream
+    def stream_for(self, big: bool):
+        """The round's stream for its size class, created on first use (the
+        loop's logic needs no GPU): small units' rounds run on a
+        high-priority stream, so their CTAs are scheduled ahead of a large
+        unit's walks still in flight."""
+        if big not in self._streams:
+            lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") \
+                else (0, -1)
+            self._streams[big] = torch.cuda.Stream(self.server.device,
+                                                   priority=lo if big else hi)
+        return self._streams[big]
 
     @property
     def free(self) -> bool:
@@ -148,7 +155,8 @@ class Server:
     def __init__(self, device=None, mem_budget: int = 2 << 30, max_units_per_round: int = 64,
                  max_inflight: int = 4, llr: bool = True, starve_s: float = 5e-3,
                  slots_per_ru: int = 2, keep_results: bool = False,
-                 big_cost: float = 936 * 14 * 64 * 16 * 20):
+                 big_cost: float = 936 * 14 * 64 * 16 * 20, max_large_rounds: int | None = None,
+                 share_sms: bool = False):
         self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
                        else torch.device(device))
         self.mem_budget = int(mem_budget)
@@ -157,6 +165,15 @@ class Server:
         self.starve_s = starve_s
         self.slots_per_ru = slots_per_ru
         self.big_cost = big_cost  # units at least this costly form rounds of their own
+        # at most this many large units' rounds in flight, so that a small
+        # unit's slot always finds a round to go into
+        self.max_large_rounds = (max(1, max_inflight // 2) if max_large_rounds is None
+                                 else max_large_rounds)
+        # large units' rounds leave a CTA slot per SM to the small units'
+        # high-priority rounds (MPNL_RUN_SHARE_SMS); off by default: measured
+        # on the serving mix it slowed the large units more than it sped up
+        # the small ones
+        self.share_sms = share_sms
         self.keep_results = keep_results  # copy each result out (else a view valid
         # until the RU's pool buffer is reused)
         self.rus: dict[int, RU] = {}
@@ -237,6 +254,7 @@ class Server:
                                                     self.rus[q.ru].cost, q.arrival))
         self.waiting = collections.deque(order)
         size_class = None
+        large_ok = sum(1 for r in self.rounds if not r.free and r.big) < self.max_large_rounds
         while self.waiting and len(chosen) < self.max_units:
             q = self.waiting.popleft()
             ru = self.rus[q.ru]
@@ -246,6 +264,8 @@ class Server:
             # not wait for a large unit's walks in the same round
             big = ru.cost >= self.big_cost
             if ok and size_class is not None and big != size_class:
+                ok = False
+            if ok and big and not large_ok:
                 ok = False
             if ok and q.kind == "slot":
                 # a free buffer set of the RU (its earlier slots in this round hold theirs)
@@ -282,7 +302,9 @@ class Server:
         if r.batch is None:
             r.items = (mpnl.BatchItemC * self.max_units)()
         items = r.items
-        st = r.stream
+        big = any(self.rus[q.ru].cost >= self.big_cost for q in reqs)
+        r.big = big
+        st = r.stream_for(big)
         n = 0
         with torch.cuda.stream(st):
             # channel updates first in the item list (the batch runs stages in
@@ -322,7 +344,7 @@ class Server:
                 r.batch = mpnl.Batch(items=list(items), device=dev)
             r.batch.reset((mpnl.BatchItemC * n).from_buffer(items), trusted_pointers=True)
             r.batch.run(mpnl.STAGE_PREPROCESS | mpnl.STAGE_SELECT | mpnl.STAGE_QHY |
-                        mpnl.STAGE_DETECT, stream=st)
+                        mpnl.STAGE_DETECT, stream=st, share_sms=big and self.share_sms)
             for q in reqs:
                 if q.bufs is not None:
                     q.bufs.hard_host.copy_(q.bufs.hard, non_blocking=True)

@@ -79,6 +79,22 @@ def test_batch_results_equal_each_unit_alone(dev):
     batch.close()
 
 
+def test_sharing_sms_leaves_results_unchanged(dev):
+    mpnl = _mpnl()
+    units, _ = _fill(dev, _specs()[:6])
+    batch = mpnl.Batch(units, dev)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    for graph in (False, True):
+        with torch.cuda.stream(side):
+            batch.run(graph=graph, stream=side, share_sms=True)
+        side.synchronize()
+        mpnl.check_status()
+        for k, unit in enumerate(units):
+            _assert_same(unit, _alone(dev, unit), k)
+    batch.close()
+
+
 def test_batch_graph_replay_follows_new_inputs(dev):
     mpnl = _mpnl()
     specs = _specs()

@@ -103,3 +103,26 @@ def test_small_and_large_units_form_separate_rounds():
     assert [q.rid for q in chosen] == [1, 2]       # the small units' round
     chosen, _ = s._form()
     assert [q.rid for q in chosen] == [0]          # then the large unit's
+
+
+def test_large_rounds_leave_room_for_small_units():
+    s = serving.Server(device="cpu", mem_budget=1 << 30, max_units_per_round=8, max_inflight=4,
+                       max_large_rounds=1)
+    for k in range(2):
+        s.rus[k] = serving.RU(k, 4, 4, 16, 12 + k, 16, 0.1)
+        s.rus[k].pool = [object(), object()]
+    for k in (2, 3):
+        s.rus[k] = serving.RU(k, 16, 16, 64, 3276, 256, 0.1)
+        s.rus[k].pool = [object(), object()]
+    # one large unit's round in flight: the other large unit waits, small ones go
+    s.rounds[0].big = True
+    s.rounds[0].event = object()
+    for q in (_req(0, 3, "slot"), _req(1, 0, "slot"), _req(2, 2, "slot")):
+        s.submit(q)
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [1]
+    chosen, _ = s._form()
+    assert chosen == []
+    s.rounds[0].event = None                       # the large round completed
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [0, 2]       # both large units, one round
