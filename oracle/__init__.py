@@ -76,9 +76,13 @@ def _load():
             lib.orc_rank_counts_mc.argtypes = [I, I, P, LL, ctypes.c_ulonglong, P]
             lib.orc_rank_costs.argtypes = [I, I, P, LL, P]
             lib.orc_select_paths_lut.argtypes = [I, I, P, D, I, P, P, I, P, P, P]
+            lib.orc_pam_points.argtypes = [I, P]
+            lib.orc_select_paths_pam.argtypes = [I, I, P, D, I, P, P, P]
+            lib.orc_detect_pam.argtypes = [I, I, I, P, P, P, I, P, D, P, P, P, P, D, P]
             for f in ("orc_constellation", "orc_sqrd", "orc_sqrd_mmse", "orc_qhy", "orc_select_paths",
                       "orc_detect", "orc_mmse", "orc_detect_slot", "orc_rank_counts_mc",
-                      "orc_rank_costs", "orc_select_paths_lut"):
+                      "orc_rank_costs", "orc_select_paths_lut", "orc_pam_points",
+                      "orc_select_paths_pam", "orc_detect_pam"):
                 getattr(lib, f).restype = I
             _lib = lib
     return _lib
@@ -277,4 +281,105 @@ def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, paths=None, n_threads:
     if with_mmse:
         out["mmse_hard"] = mh
         out["mmse_llr"] = ml
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Real-valued decomposition (RVD) variant: 2 nt real levels, L-PAM each
+# ---------------------------------------------------------------------------
+def rvd_embed(H, Y):
+    """[Re y; Im y] = [[Re H, -Im H]; [Im H, Re H]] [Re s; Im s]: H [..][nr][nt]
+    -> [..][2nr][2nt], Y [..][n_sym][nr] -> [..][n_sym][2nr], as complex128
+    with zero imaginary parts (so the complex routines run on them)."""
+    H = _c128(H)
+    Y = _c128(Y)
+    top = np.concatenate([H.real, -H.imag], axis=-1)
+    bot = np.concatenate([H.imag, H.real], axis=-1)
+    Hr = np.concatenate([top, bot], axis=-2).astype(np.complex128)
+    Yr = np.concatenate([Y.real, Y.imag], axis=-1).astype(np.complex128)
+    return Hr, Yr
+
+
+def pam_points(qam: int) -> np.ndarray:
+    """Axis positions of the L-PAM of a square QAM, indexed by axis label."""
+    L = 1 << (BITS[qam] // 2)
+    out = np.zeros(L, np.float64)
+    _check(_load().orc_pam_points(qam, _p(out)), "pam_points")
+    return out
+
+
+def select_paths_pam(rdiag, sigma2: float, qam: int, n_pe: int):
+    """Best-first table over 2 nt real levels (ranks 1..L) -> (paths, score, pe)."""
+    rdiag = np.ascontiguousarray(np.asarray(rdiag, np.float64))
+    ntr = rdiag.shape[0]
+    paths = np.zeros((n_pe, ntr), np.uint8)
+    score = np.zeros(n_pe, np.float64)
+    pe = np.zeros(ntr, np.float64)
+    _check(_load().orc_select_paths_pam(ntr, qam, _p(rdiag), float(sigma2), n_pe, _p(paths),
+                                        _p(score), _p(pe)), "select_paths_pam")
+    return paths, score, pe
+
+
+def join_axes(hard_r, llr_r, qam: int):
+    """Per-column axis labels / LLRs of the real levels ([..][2nt], [..][2nt][B/2])
+    -> user labels [..][nt] and LLRs [..][nt][B]: bits b0 b2 .. of user u from
+    column u, b1 b3 .. from column nt + u (TS 38.211 §5.1)."""
+    B = BITS[qam]
+    H = B // 2
+    nt = hard_r.shape[-1] // 2
+    re, im = hard_r[..., :nt].astype(np.int64), hard_r[..., nt:].astype(np.int64)
+    lab = np.zeros(re.shape, np.int64)
+    for t in range(H):
+        lab |= ((re >> (H - 1 - t)) & 1) << (B - 1 - 2 * t)
+        lab |= ((im >> (H - 1 - t)) & 1) << (B - 2 - 2 * t)
+    llr = np.zeros(hard_r.shape[:-1] + (nt, B), np.float64)
+    llr[..., 0::2] = llr_r[..., :nt, :]
+    llr[..., 1::2] = llr_r[..., nt:, :]
+    return lab.astype(np.uint8), llr
+
+
+def detect_rvd(R, Z, perm, paths, sigma2: float, qam: int, tie_eps: float = 0.0):
+    """Walks over the 2 nt real levels of one subcarrier (R real upper
+    [2nt][2nt], Z [n_sym][2nt], perm, paths [n_pe][2nt] with ranks 1..L)."""
+    R = _c128(R)
+    Z = _c128(Z)
+    perm = np.ascontiguousarray(np.asarray(perm, np.int32))
+    paths = np.ascontiguousarray(np.asarray(paths, np.uint8))
+    ntr = R.shape[0]
+    n_sym = Z.shape[0]
+    Bh = BITS[qam] // 2
+    hard_r = np.zeros((n_sym, ntr), np.uint8)
+    llr_r = np.zeros((n_sym, ntr, Bh), np.float64)
+    ped2 = np.zeros((n_sym, 2), np.float64)
+    margin = np.zeros(n_sym, np.float64)
+    flip = np.zeros(n_sym, np.float64)
+    _check(_load().orc_detect_pam(ntr, qam, n_sym, _p(R), _p(Z), _p(perm), paths.shape[0],
+                                  _p(paths), float(sigma2), _p(hard_r), _p(llr_r), _p(ped2),
+                                  _p(margin), float(tie_eps), _p(flip)), "detect_pam")
+    hard, llr = join_axes(hard_r, llr_r, qam)
+    return dict(hard=hard, llr=llr, ped2=ped2, margin=margin, flip_floor=flip, hard_r=hard_r,
+                llr_r=llr_r)
+
+
+def detect_slot_rvd(H, Y, sigma2: float, qam: int, n_pe: int, tie_eps: float = 0.0):
+    """The RVD path over a slot, subcarrier by subcarrier: embed, sorted QR of
+    the real matrix, z, PAM-level selection, walks, axes joined per user."""
+    Hr, Yr = rvd_embed(H, Y)
+    n_sc, n_sym = Yr.shape[0], Yr.shape[1]
+    ntr = Hr.shape[-1]
+    nt = ntr // 2
+    B = BITS[qam]
+    out = dict(hard=np.zeros((n_sc, n_sym, nt), np.uint8),
+               llr=np.zeros((n_sc, n_sym, nt, B)), ped2=np.zeros((n_sc, n_sym, 2)),
+               flip_floor=np.zeros((n_sc, n_sym)), R=np.zeros((n_sc, ntr, ntr), np.complex128),
+               perm=np.zeros((n_sc, ntr), np.int32), Z=np.zeros((n_sc, n_sym, ntr), np.complex128),
+               paths=np.zeros((n_sc, n_pe, ntr), np.uint8))
+    for c in range(n_sc):
+        Q, R, perm, _ = sqrd(Hr[c])
+        Z = qhy(Q, Yr[c])
+        paths, _, _ = select_paths_pam(np.real(np.diag(R)), sigma2, qam, n_pe)
+        o = detect_rvd(R, Z, perm, paths, sigma2, qam, tie_eps)
+        for k in ("hard", "llr", "ped2", "flip_floor"):
+            out[k][c] = o[k]
+        out["R"][c], out["perm"][c], out["Z"][c], out["paths"][c] = R, perm, Z, paths
     return out

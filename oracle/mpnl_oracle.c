@@ -527,14 +527,15 @@ int orc_select_paths_lut(int nt, int qam, const double *rdiag, double sigma2, in
  * level; +inf if none).  margin and flip_floor are diagnostics for the tests:
  * they do not change any result.
  * ------------------------------------------------------------------------- */
-static int detect_sc(int nt, int qam, int n_sym, const cplx *R, const cplx *Z, const int *perm,
-                     int n_pe, const unsigned char *paths, double sigma2, unsigned char *hard,
-                     double *llr, double *ped2, double *margin, double *ped_all,
-                     unsigned char *sym_all, double tie_eps, double *flip_floor)
+/* The walks, argmin and LLRs over a constellation given as its M points
+ * (label-indexed) with B bits per label: the square QAM of the complex model
+ * (detect_sc), or one PAM axis of it in the real-valued decomposition. */
+static int detect_pts(int nt, const cplx *pts, int M, int B, int n_sym, const cplx *R,
+                      const cplx *Z, const int *perm, int n_pe, const unsigned char *paths,
+                      double sigma2, unsigned char *hard, double *llr, double *ped2,
+                      double *margin, double *ped_all, unsigned char *sym_all, double tie_eps,
+                      double *flip_floor)
 {
-    int M = qam, B = bits_of(qam);
-    cplx pts[ORC_MAX_M];
-    for (int q = 0; q < M; q++) pts[q] = qam_point(qam, q);
 
     double *d = (double *)malloc((size_t)n_pe * sizeof(double));
     unsigned char *lab = (unsigned char *)malloc((size_t)n_pe * nt);
@@ -641,6 +642,17 @@ static int detect_sc(int nt, int qam, int n_sym, const cplx *R, const cplx *Z, c
     return 0;
 }
 
+static int detect_sc(int nt, int qam, int n_sym, const cplx *R, const cplx *Z, const int *perm,
+                     int n_pe, const unsigned char *paths, double sigma2, unsigned char *hard,
+                     double *llr, double *ped2, double *margin, double *ped_all,
+                     unsigned char *sym_all, double tie_eps, double *flip_floor)
+{
+    cplx pts[ORC_MAX_M];
+    for (int q = 0; q < qam; q++) pts[q] = qam_point(qam, q);
+    return detect_pts(nt, pts, qam, bits_of(qam), n_sym, R, Z, perm, n_pe, paths, sigma2, hard,
+                      llr, ped2, margin, ped_all, sym_all, tie_eps, flip_floor);
+}
+
 int orc_detect(int nt, int qam, int n_sym, const double *R, const double *Z, const int *perm,
                int n_pe, const unsigned char *paths, double sigma2, unsigned char *hard, double *llr,
                double *ped2, double *margin, double *ped_all, unsigned char *sym_all,
@@ -654,6 +666,85 @@ int orc_detect(int nt, int qam, int n_sym, const double *R, const double *Z, con
         }
     return detect_sc(nt, qam, n_sym, (const cplx *)R, (const cplx *)Z, perm, n_pe, paths, sigma2,
                      hard, llr, ped2, margin, ped_all, sym_all, tie_eps, flip_floor);
+}
+
+/* ---------------------------------------------------------------------------
+ * Real-valued decomposition (RVD; a variant, the paper uses complex levels):
+ *   [Re y; Im y] = [[Re H, -Im H]; [Im H, Re H]] [Re s; Im s] + [Re n; Im n],
+ * 2 nt real levels, real column c < nt carrying the real part of user c and
+ * column nt + c its imaginary part.  Each real level is one axis of the
+ * square QAM: an L-PAM (L = sqrt M) whose points, indexed by the axis label
+ * (the label's real-axis bits b0 b2 b4 .. read as an integer, MSB first),
+ * are the real parts of the QAM points with those bits and all imaginary-axis
+ * bits 0 (TS 38.211 §5.1 maps the two axes by the same rule).  The sorted QR
+ * of the real matrix is the complex routine on a matrix with zero imaginary
+ * parts (every product and sum stays real).
+ *
+ * Per-level model for a real level: noise variance sigma2/2 per real
+ * dimension, so with gamma_l = R_ll^2 / sigma2 an L-PAM level errs with
+ * Pe_l = 2 (1 - 1/L) Q(sqrt(3 gamma_l / (M - 1))) (the same Q argument as the
+ * square QAM's), floored as before; P_l(k) geometric over k = 1..L.
+ *
+ * orc_detect_pam returns, per real level in column order, the chosen axis
+ * labels (hard [n_sym][2nt]) and the LLRs of their B/2 bits
+ * (llr [n_sym][2nt][B/2]); joining the two axes of each user is left to the
+ * caller (bits b0 b2 .. from column u, b1 b3 .. from column nt + u).
+ * ------------------------------------------------------------------------- */
+static void pam_points(int qam, cplx *pts)
+{
+    int B = bits_of(qam), H = B / 2, L = 1 << H;
+    for (int a = 0; a < L; a++) {
+        int lab = 0;
+        for (int t = 0; t < H; t++)
+            lab |= ((a >> (H - 1 - t)) & 1) << (B - 1 - 2 * t);
+        pts[a] = creal(qam_point(qam, lab));
+    }
+}
+
+int orc_pam_points(int qam, double *pos)
+{
+    if (!bits_of(qam)) return -1;
+    cplx pts[8];
+    pam_points(qam, pts);
+    for (int a = 0; a < (1 << (bits_of(qam) / 2)); a++) pos[a] = creal(pts[a]);
+    return 0;
+}
+
+int orc_select_paths_pam(int ntr, int qam, const double *rdiag, double sigma2, int n_pe,
+                         unsigned char *paths, double *score, double *pe_out)
+{
+    int L = 1 << (bits_of(qam) / 2);
+    if (ntr < 1 || ntr > ORC_MAX_NT || !bits_of(qam) || n_pe < 1 || n_pe > ORC_MAX_NPE) return -1;
+    if ((double)n_pe > ipow((double)L, ntr)) return -1;
+    if (!(sigma2 > 0.0)) return -1;
+    double logp[ORC_MAX_NT][ORC_MAX_M + 1];
+    for (int l = 0; l < ntr; l++) {
+        double gamma = rdiag[l] * rdiag[l] / sigma2;
+        double x = sqrt(3.0 * gamma / (double)(qam - 1));
+        double pe = 2.0 * (1.0 - 1.0 / (double)L) * 0.5 * erfc(x / sqrt(2.0));
+        if (pe < ORC_PE_FLOOR) pe = ORC_PE_FLOOR;
+        if (pe_out) pe_out[l] = pe;
+        for (int k = 1; k <= L; k++)
+            logp[l][k] = log(1.0 - pe) + (double)(k - 1) * log(pe);
+    }
+    return select_best_first(ntr, L, logp, n_pe, paths, score);
+}
+
+int orc_detect_pam(int ntr, int qam, int n_sym, const double *R, const double *Z, const int *perm,
+                   int n_pe, const unsigned char *paths, double sigma2, unsigned char *hard,
+                   double *llr, double *ped2, double *margin, double tie_eps, double *flip_floor)
+{
+    int B = bits_of(qam), L = 1 << (B / 2);
+    if (ntr < 1 || ntr > ORC_MAX_NT || !B || n_pe < 1 || n_pe > ORC_MAX_NPE) return -1;
+    for (int row = 0; row < n_pe; row++)
+        for (int l = 0; l < ntr; l++) {
+            int v = paths[(size_t)row * ntr + l];
+            if (v < 1 || v > L) return -1;
+        }
+    cplx pts[8];
+    pam_points(qam, pts);
+    return detect_pts(ntr, pts, L, B / 2, n_sym, (const cplx *)R, (const cplx *)Z, perm, n_pe,
+                      paths, sigma2, hard, llr, ped2, margin, NULL, NULL, tie_eps, flip_floor);
 }
 
 /* ---------------------------------------------------------------------------
