@@ -186,6 +186,39 @@ typedef struct {
 int mpnl_select_paths_lut(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, float sigma2,
                           const mpnl_rank_lut *lut, uint8_t *paths, void *ws, void *stream);
 
+/* Real-valued decomposition (RVD; a variant: the paper's levels are
+ * complex).  [Re y; Im y] = [[Re H, -Im H]; [Im H, Re H]] [Re s; Im s] +
+ * noise: 2 nt real levels, real column u the real part of user u and column
+ * nt + u its imaginary part, each an L-PAM axis (L = sqrt qam) of the square
+ * QAM labelled by that axis's Gray bits.  The path: mpnl_rvd_embed, then
+ * mpnl_preprocess with nr' = 2 nr, nt' = 2 nt on the embedded arrays (its R
+ * and z come out real), mpnl_select_paths_pam, mpnl_detect_rvd.  In these
+ * three calls dims describe the complex problem: nt <= 8 users (2 nt real
+ * levels <= 16), and for the embedding nr <= 16.
+ *   mpnl_rvd_embed:  H in c64 [n_sc][nr][nt], Y in c64 [n_sc][n_sym][nr];
+ *                    Hr out c64 [n_sc][2nr][2nt], Yr out c64 [n_sc][n_sym][2nr]
+ *                    (imaginary parts zero)
+ *   mpnl_select_paths_pam:  per real level the L-PAM error probability
+ *                    Pe_l = 2 (1 - 1/L) Q(sqrt(3 gamma_l / (qam - 1))),
+ *                    gamma_l = R_ll^2 / sigma2 (noise sigma2/2 per real
+ *                    dimension), geometric over ranks 1..L; order and ties as
+ *                    mpnl_select_paths.  R in c64 [n_sc][2nt(2nt+1)/2];
+ *                    paths out u8 [n_sc][n_pe][2nt]; n_pe <= min(1024, L^(2nt))
+ *   mpnl_detect_rvd: the walks over the real levels (p-th closest PAM point
+ *                    by (distance, axis label)); hard decisions, LLRs and PED
+ *                    pairs in the layouts of mpnl_detect, each user's label
+ *                    joining its two axes (bits b0 b2 .. from the real part,
+ *                    b1 b3 .. from the imaginary part, TS 38.211 §5.1).
+ *                    R, inv_diag, perm, Z over the 2 nt real levels.
+ * Errors: as the complex calls, and nt > 8, 2 nr > MPNL_MAX_NR (embedding). */
+int mpnl_rvd_embed(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const void *Y, void *Hr,
+                   void *Yr, void *stream);
+int mpnl_select_paths_pam(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, float sigma2,
+                          uint8_t *paths, void *ws, void *stream);
+int mpnl_detect_rvd(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const float *inv_diag,
+                    const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
+                    uint8_t *hard, float *llr, float *ped2, void *ws, void *stream);
+
 /* Monte-Carlo rank histogram for the table: for each of n_bins SNRs
  * gamma[b] (linear), n_trials draws of a uniform symbol and of complex
  * Gaussian noise of variance 1/gamma[b] (the law of b_l = s + n_l / R_ll),

@@ -683,6 +683,87 @@ int mpnl_select_paths_lut(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, floa
     return MPNL_OK;
 }
 
+// The real-valued decomposition: dims describe the complex problem; its 2 nt
+// real levels must fit the walks (2 nt <= MPNL_MAX_NT) and n_pe is bounded
+// by L^(2 nt) instead of M^nt.
+static int check_rvd_dims(mpnl_ctx *ctx, const mpnl_dims *d, bool need_pe)
+{
+    MPNL_TRY(check_dims(ctx, d, false));
+    if (2 * d->nt > MPNL_MAX_NT)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "nt=%d: 2 nt real levels exceed %d", d->nt,
+                    MPNL_MAX_NT);
+    if (need_pe) {
+        const double L = (double)(1 << (bits_of(d->qam) / 2));
+        const double cap = pow(L, 2.0 * d->nt);
+        if (d->n_pe < 1 || d->n_pe > MPNL_MAX_NPE || (double)d->n_pe > cap)
+            return fail(ctx, MPNL_ERR_INVALID_ARG, "n_pe=%d outside 1..min(%d, L^(2 nt))",
+                        d->n_pe, MPNL_MAX_NPE);
+    }
+    return MPNL_OK;
+}
+
+int mpnl_rvd_embed(mpnl_ctx *ctx, const mpnl_dims *d, const void *H, const void *Y, void *Hr,
+                   void *Yr, void *stream)
+{
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_rvd_dims(ctx, d, false));
+    if (2 * d->nr > MPNL_MAX_NR)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "nr=%d: 2 nr real rows exceed %d", d->nr,
+                    MPNL_MAX_NR);
+    if (d->n_sc == 0) return MPNL_OK;
+    MPNL_TRY(check_ptr(ctx, H, 8, "H", false));
+    MPNL_TRY(check_ptr(ctx, Y, 8, "Y", false));
+    MPNL_TRY(check_ptr(ctx, Hr, 8, "Hr", false));
+    MPNL_TRY(check_ptr(ctx, Yr, 8, "Yr", false));
+    cudaError_t e = mpnl::launch_rvd_embed(d->n_sc, d->n_sym, d->nr, d->nt, (const float2 *)H,
+                                           (const float2 *)Y, (float2 *)Hr, (float2 *)Yr,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "rvd_embed launch", e);
+    return MPNL_OK;
+}
+
+int mpnl_select_paths_pam(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, float sigma2,
+                          uint8_t *paths, void *ws, void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_rvd_dims(ctx, d, true));
+    MPNL_TRY(check_sigma2(ctx, sigma2));
+    if (d->n_sc == 0) return MPNL_OK;
+    MPNL_TRY(check_ptr(ctx, R, 8, "R", false));
+    MPNL_TRY(check_ptr(ctx, paths, 1, "paths", false));
+    cudaError_t e = mpnl::launch_select_paths_pam(d->n_sc, 2 * d->nt, d->qam, d->n_pe, sigma2,
+                                                  (const float2 *)R, paths,
+                                                  d->n_pe >= 256 ? 2 : 1, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "select_paths_pam launch", e);
+    return MPNL_OK;
+}
+
+int mpnl_detect_rvd(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, const float *inv_diag,
+                    const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
+                    uint8_t *hard, float *llr, float *ped2, void *ws, void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_rvd_dims(ctx, d, true));
+    MPNL_TRY(check_sigma2(ctx, sigma2));
+    if (d->n_sc == 0) return MPNL_OK;
+    MPNL_TRY(check_ptr(ctx, R, 8, "R", false));
+    MPNL_TRY(check_ptr(ctx, inv_diag, 4, "inv_diag", false));
+    MPNL_TRY(check_ptr(ctx, perm, 1, "perm", false));
+    MPNL_TRY(check_ptr(ctx, paths, 1, "paths", false));
+    MPNL_TRY(check_ptr(ctx, Z, 8, "Z", false));
+    MPNL_TRY(check_ptr(ctx, hard, 1, "hard", false));
+    MPNL_TRY(check_ptr(ctx, llr, 4, "llr", true));
+    MPNL_TRY(check_ptr(ctx, ped2, 4, "ped2", true));
+    cudaError_t e = mpnl::launch_detect_rvd(d->n_sc, d->n_sym, d->nt, d->qam, d->n_pe, sigma2,
+                                            (const float2 *)R, inv_diag, perm, paths,
+                                            (const float2 *)Z, hard, llr, ped2, ctx->status,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "detect_rvd launch", e);
+    return MPNL_OK;
+}
+
 static int check_lut_args(mpnl_ctx *ctx, int qam, int n_bins, long long n_trials)
 {
     if (!bits_of(qam)) return fail(ctx, MPNL_ERR_INVALID_ARG, "qam=%d not in {4,16,64}", qam);

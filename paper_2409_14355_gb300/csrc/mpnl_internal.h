@@ -62,6 +62,20 @@ cudaError_t launch_rank_counts(int qam, int n_bins, const double *gamma, long lo
 cudaError_t launch_rank_costs(int qam, int n_bins, const unsigned long long *counts,
                               long long n_trials, float *cost, cudaStream_t stream);
 
+// Real-valued decomposition (mpnl_rvd_embed, mpnl_select_paths_pam,
+// mpnl_detect_rvd): the embedding, the PAM-level selection over ntr = 2 nt
+// real levels, and the real walks (nt = users; R, perm, Z over 2 nt levels).
+cudaError_t launch_rvd_embed(int n_sc, int n_sym, int nr, int nt, const float2 *H, const float2 *Y,
+                             float2 *Hr, float2 *Yr, cudaStream_t stream);
+cudaError_t launch_select_paths_pam(int n_sc, int ntr, int qam, int n_pe, float sigma2,
+                                    const float2 *R, uint8_t *paths, int warps,
+                                    cudaStream_t stream);
+cudaError_t launch_detect_rvd(int n_sc, int n_sym, int nt, int qam, int n_pe, float sigma2,
+                              const float2 *R, const float *inv_diag, const uint8_t *perm,
+                              const uint8_t *paths, const float2 *Z, uint8_t *hard, float *llr,
+                              float *ped2, unsigned *status, cudaStream_t stream);
+size_t rvd_smem_bytes(int nt, int qam, int n_pe, int n_sym);
+
 // f16: residuals in half2 with FP32 ranking / PED and an FP32 re-check of
 // the best and runner-up paths (mpnl_detect_mixed); false: all FP32.
 // sym: symbols per lane (1 or 2; a tuning knob, results do not depend on it).

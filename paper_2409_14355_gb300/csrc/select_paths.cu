@@ -88,12 +88,20 @@ struct RankLut {
 // byte offset base_off (at least sel_group_bytes(n_pe)).  Inlined into
 // the per-call and the batch kernels alike (no contraction).  LUT: costs
 // from the table `lut` (else the geometric model, w_l = -log Pe_l).
-template <int QAM, int G, bool LUT = false>
+// Cost models: the geometric rank model of square M-QAM levels, a caller's
+// rank-cost table, or the geometric model of the L-PAM levels of the
+// real-valued decomposition (ranks 1..L, Pe = 2 (1 - 1/L) Q(.) per level).
+enum SelMode { kSelGeo = 0, kSelLut = 1, kSelPam = 2 };
+
+template <int QAM, int G, int MODE = kSelGeo>
 __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, float sigma2,
                                                const float2 *__restrict__ Rp,
                                                uint8_t *__restrict__ paths, int base_off,
                                                int group, int tid, RankLut lut = RankLut{})
 {
+    constexpr bool LUT = MODE == kSelLut;
+    constexpr bool PAM = MODE == kSelPam;
+    constexpr int RK = PAM ? Qam<QAM>::L : QAM;  // ranks per level
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *base = smem_raw + base_off;
     constexpr unsigned FULL = 0xffffffffu;
@@ -127,7 +135,9 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         const float qf = 0.5f * erfcf(x * 0.70710678118654752f);
         constexpr float c = 2.0f * (1.0f - 1.0f / (float)Qam<QAM>::L);  // 2 (1 - 1/sqrt(M))
         const float cq = c * qf;
-        float pe = cq * (2.0f - cq);  // = 1 - (1 - cq)^2 without cancellation
+        // square QAM: 1 - (1 - cq)^2 = cq (2 - cq) without cancellation; an
+        // L-PAM level: cq
+        float pe = PAM ? cq : cq * (2.0f - cq);
         pe = fmaxf(pe, kPeFloor);
         w[l] = -logf(pe);
     }
@@ -158,7 +168,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
             auto count = [&](float v) {
                 int cnt = 1;
                 for (int m = 0; m < nt; ++m) {
-                    int lo_j = 0, hi_j = QAM - 1;  // cost(m, 0) = 0 <= v
+                    int lo_j = 0, hi_j = RK - 1;  // cost(m, 0) = 0 <= v
                     while (lo_j < hi_j) {
                         const int mid = (lo_j + hi_j + 1) >> 1;
                         if (shift_cost(m, mid) <= v) lo_j = mid;
@@ -168,8 +178,8 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
                 }
                 return cnt;
             };
-            if (count(shift_cost(l, QAM - 1)) >= n_pe) {
-                int lo_j = 1, hi_j = QAM - 1;
+            if (count(shift_cost(l, RK - 1)) >= n_pe) {
+                int lo_j = 1, hi_j = RK - 1;
                 while (lo_j < hi_j) {
                     const int mid = (lo_j + hi_j) >> 1;
                     if (count(shift_cost(l, mid)) >= n_pe) hi_j = mid;
@@ -194,12 +204,12 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
 #pragma unroll
                 for (int m = 0; m < kMaxNt; ++m) {
                     const int c = (int)floorf(v * inv[m]);
-                    cnt += m < nt ? (c < 0 ? 0 : (c > QAM - 1 ? QAM - 1 : c)) : 0;
+                    cnt += m < nt ? (c < 0 ? 0 : (c > RK - 1 ? RK - 1 : c)) : 0;
                 }
                 return cnt;
             };
-            if (count(QAM - 1) >= n_pe) {
-                int lo_j = 1, hi_j = QAM - 1;  // count(hi_j) >= n_pe
+            if (count(RK - 1) >= n_pe) {
+                int lo_j = 1, hi_j = RK - 1;  // count(hi_j) >= n_pe
                 while (lo_j < hi_j) {
                     const int mid = (lo_j + hi_j) >> 1;
                     if (count(mid) >= n_pe) hi_j = mid;
@@ -221,7 +231,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     int li = 0, nL = 1;
     {
         const int mt = nt - 1;
-        while (nL < QAM && nL < n_pe && shift_cost(mt, nL) <= bound) ++nL;
+        while (nL < RK && nL < n_pe && shift_cost(mt, nL) <= bound) ++nL;
         unsigned long long h = 0, o = 0;
         for (int l = 0; l < nt; ++l) {
             bool in_hi;
@@ -247,7 +257,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         level_shift(nt, m, in_hi, sh);
         int bi = li, nB = nL;          // B starts as L itself (read only)
         int oi = (li + 1) % 3;         // first output buffer
-        for (int j = 1; j < QAM; ++j) {
+        for (int j = 1; j < RK; ++j) {
             const unsigned long long add = (unsigned long long)j << sh;
             const float cj = shift_cost(m, j);
             if (cj > bound) break;
@@ -346,8 +356,22 @@ select_paths_lut_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *
     const int group = threadIdx.x / T, tid = threadIdx.x % T;
     const int sc = blockIdx.x * (blockDim.x / T) + group;
     if (sc >= n_sc) return;
-    select_group_body<QAM, G, true>(sc, nt, n_pe, sigma2, Rp, paths,
-                                    group * (int)sel_group_bytes(n_pe), group, tid, lut);
+    select_group_body<QAM, G, kSelLut>(sc, nt, n_pe, sigma2, Rp, paths,
+                                       group * (int)sel_group_bytes(n_pe), group, tid, lut);
+}
+
+// The 2 nt real levels of the real-valued decomposition (nt here: 2 nt).
+template <int QAM, int G>
+__global__ void __launch_bounds__(kSelMaxWarps * 32)
+select_paths_pam_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
+                        uint8_t *__restrict__ paths)
+{
+    constexpr int T = 32 * G;
+    const int group = threadIdx.x / T, tid = threadIdx.x % T;
+    const int sc = blockIdx.x * (blockDim.x / T) + group;
+    if (sc >= n_sc) return;
+    select_group_body<QAM, G, kSelPam>(sc, nt, n_pe, sigma2, Rp, paths,
+                                       group * (int)sel_group_bytes(n_pe), group, tid);
 }
 
 // Persistent variant over a batch of radio units of mixed sizes: every
@@ -392,6 +416,22 @@ cudaError_t launch_group_lut(int n_sc, int nt, int n_pe, float sigma2, const flo
     const int grid = (n_sc + groups - 1) / groups;
     select_paths_lut_kernel<QAM, G><<<grid, groups * G * 32, smem, stream>>>(n_sc, nt, n_pe,
                                                                             sigma2, R, paths, lut);
+    return cudaGetLastError();
+}
+
+template <int QAM, int G>
+cudaError_t launch_group_pam(int n_sc, int ntr, int n_pe, float sigma2, const float2 *R,
+                             uint8_t *paths, cudaStream_t stream)
+{
+    const size_t per = sel_group_bytes(n_pe);
+    int groups = (int)((100 * 1024) / per);
+    groups = groups < 1 ? 1 : (groups > kSelMaxWarps / G ? kSelMaxWarps / G : groups);
+    const size_t smem = per * groups;
+    cudaError_t e = allow_dynamic_smem(select_paths_pam_kernel<QAM, G>, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = (n_sc + groups - 1) / groups;
+    select_paths_pam_kernel<QAM, G><<<grid, groups * G * 32, smem, stream>>>(n_sc, ntr, n_pe,
+                                                                            sigma2, R, paths);
     return cudaGetLastError();
 }
 
@@ -467,6 +507,24 @@ cudaError_t launch_select_paths_lut(int n_sc, int nt, int qam, int n_pe, float s
     default: MPNL_SEL_LUT(64);
     }
 #undef MPNL_SEL_LUT
+}
+
+cudaError_t launch_select_paths_pam(int n_sc, int ntr, int qam, int n_pe, float sigma2,
+                                    const float2 *R, uint8_t *paths, int warps,
+                                    cudaStream_t stream)
+{
+    if (n_sc == 0) return cudaSuccess;
+    const int g = warps == 4 ? 4 : (warps == 2 ? 2 : 1);
+#define MPNL_SEL_PAM(Q)                                                                     \
+    return g == 4 ? launch_group_pam<Q, 4>(n_sc, ntr, n_pe, sigma2, R, paths, stream)       \
+         : g == 2 ? launch_group_pam<Q, 2>(n_sc, ntr, n_pe, sigma2, R, paths, stream)       \
+                  : launch_group_pam<Q, 1>(n_sc, ntr, n_pe, sigma2, R, paths, stream)
+    switch (qam) {
+    case 4: MPNL_SEL_PAM(4);
+    case 16: MPNL_SEL_PAM(16);
+    default: MPNL_SEL_PAM(64);
+    }
+#undef MPNL_SEL_PAM
 }
 
 cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,

@@ -40,7 +40,8 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_linear_mmse", "mpnl_check_status", "mpnl_probe_ffma", "mpnl_set_tuning",
             "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy",
             "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr",
-            "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs")
+            "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs",
+            "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16 = 1, 2, 4
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
@@ -127,6 +128,12 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_rank_counts.restype = I
         lib.mpnl_rank_costs.argtypes = [P, I, I, P, LL, P, P]
         lib.mpnl_rank_costs.restype = I
+        lib.mpnl_rvd_embed.argtypes = [P, D, P, P, P, P, P]
+        lib.mpnl_rvd_embed.restype = I
+        lib.mpnl_select_paths_pam.argtypes = [P, D, P, F, P, P, P]
+        lib.mpnl_select_paths_pam.restype = I
+        lib.mpnl_detect_rvd.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
+        lib.mpnl_detect_rvd.restype = I
         lib.mpnl_detect.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
         lib.mpnl_detect.restype = I
         lib.mpnl_detect_mixed.argtypes = [P, D, P, P, P, P, P, F, P, P, P, P, P]
@@ -382,6 +389,81 @@ def select_paths_lut(R: torch.Tensor, sigma2: float, lut: RankLut, n_pe: int, nt
                                                 ctypes.byref(c), _ptr(paths), None, _stream(dev)),
            ctx)
     return paths
+
+
+def rvd_embed(H: torch.Tensor, Y: torch.Tensor, out=None):
+    """Real-valued decomposition of a slot (mpnl_rvd_embed): returns
+    (Hr [n_sc][2nr][2nt], Yr [n_sc][n_sym][2nr]), complex with zero imaginary
+    parts, ready for preprocess()."""
+    dev = _dev_of(H)
+    n_sc, nr, nt = H.shape
+    n_sym = Y.shape[1]
+    _need(H, torch.complex64, (n_sc, nr, nt), "H")
+    _need(Y, torch.complex64, (n_sc, n_sym, nr), "Y")
+    if out is None:
+        Hr = torch.empty((n_sc, 2 * nr, 2 * nt), dtype=torch.complex64, device=dev)
+        Yr = torch.empty((n_sc, n_sym, 2 * nr), dtype=torch.complex64, device=dev)
+    else:
+        Hr, Yr = out
+    ctx = context(dev.index)
+    d = Dims(n_sc, n_sym, nr, nt, 4, 1)
+    _raise(load_library().mpnl_rvd_embed(ctx, ctypes.byref(d), _ptr(H), _ptr(Y), _ptr(Hr),
+                                         _ptr(Yr), _stream(dev)), ctx)
+    return Hr, Yr
+
+
+def select_paths_pam(R: torch.Tensor, sigma2: float, qam: int, n_pe: int, nt: int, out=None):
+    """Position vectors over the 2 nt real levels (ranks 1..sqrt qam),
+    u8 [n_sc][n_pe][2nt] (mpnl_select_paths_pam); nt = users."""
+    dev = _dev_of(R)
+    n_sc = R.shape[0]
+    ntr = 2 * nt
+    _need(R, torch.complex64, (n_sc, ntr * (ntr + 1) // 2), "R")
+    paths = out if out is not None else torch.empty((n_sc, n_pe, ntr), dtype=torch.uint8,
+                                                    device=dev)
+    ctx = context(dev.index)
+    d = Dims(n_sc, 1, nt, nt, qam, n_pe)
+    _raise(load_library().mpnl_select_paths_pam(ctx, ctypes.byref(d), _ptr(R), float(sigma2),
+                                                _ptr(paths), None, _stream(dev)), ctx)
+    return paths
+
+
+def detect_rvd(R, inv_diag, perm, paths, Z, sigma2: float, qam: int, want_llr: bool = True,
+               want_ped2: bool = True, out=None):
+    """Walks over the real levels (mpnl_detect_rvd); R, inv_diag, perm, paths,
+    Z over 2 nt levels.  Returns (hard [n_sc][n_sym][nt], llr or None, ped2
+    or None) in the complex users' layout."""
+    dev = _dev_of(R)
+    n_sc, n_sym, ntr = Z.shape
+    nt = ntr // 2
+    n_pe = paths.shape[1]
+    B = BITS[qam]
+    _need(paths, torch.uint8, (n_sc, n_pe, ntr), "paths")
+    if out is None:
+        hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, device=dev)
+        llr = torch.empty((n_sc, n_sym, nt, B), dtype=torch.float32, device=dev) if want_llr else None
+        ped2 = torch.empty((n_sc, n_sym, 2), dtype=torch.float32, device=dev) if want_ped2 else None
+    else:
+        hard, llr, ped2 = out
+    ctx = context(dev.index)
+    d = Dims(n_sc, n_sym, nt, nt, qam, n_pe)
+    _raise(load_library().mpnl_detect_rvd(ctx, ctypes.byref(d), _ptr(R), _ptr(inv_diag),
+                                          _ptr(perm), _ptr(paths), _ptr(Z), float(sigma2),
+                                          _ptr(hard), _ptr(llr), _ptr(ped2), None, _stream(dev)),
+           ctx)
+    return hard, llr, ped2
+
+
+def run_slot_rvd(H: torch.Tensor, Y: torch.Tensor, sigma2: float, qam: int, n_pe: int) -> dict:
+    """The real-valued path over a slot on device tensors: embedding, sorted
+    QR of the real matrix + z, PAM-level selection, walks."""
+    Hr, Yr = rvd_embed(H, Y)
+    R, inv_diag, perm, Z = preprocess(Hr, Yr)
+    nt = H.shape[2]
+    paths = select_paths_pam(R, sigma2, qam, n_pe, nt)
+    hard, llr, ped2 = detect_rvd(R, inv_diag, perm, paths, Z, sigma2, qam)
+    return dict(hard=hard, llr=llr, ped2=ped2, R=R, inv_diag=inv_diag, perm=perm, Z=Z,
+                paths=paths, Hr=Hr, Yr=Yr)
 
 
 def detect(R, inv_diag, perm, paths, Z, sigma2: float, qam: int, want_llr: bool = True,
