@@ -460,8 +460,10 @@ def run_mpnl(args):
     # ---- the table-driven rank model beside the geometric one: the table's
     # build, the selection time and the BER of the slot with each table
     rank_lut = None
+    rvd = None
     if not args.no_sweep:
         rank_lut = run_rank_lut(args, dev, n_pe)
+        rvd = run_rvd(dev)
 
     # ---- mixed-size batch (64 radio units of random sizes) in persistent
     # launches under a CUDA graph, knobs from the autotuner, beside the same
@@ -542,6 +544,7 @@ def run_mpnl(args):
                          "frac_of_measured_ffma": achieved_tflops / probe_tflops},
             "sweep": sweep,
             "rank_lut": rank_lut,
+            "rvd": rvd,
             "mixed_batch": mixed,
             "serving": serving_res,
             "cpu_baseline": cpu,
@@ -611,6 +614,58 @@ def run_rank_lut(args, dev, n_pe):
     return {"bins": lut.n_bins, "db_range": [-10.0, 40.0, 0.5], "trials_per_bin": trials,
             "build_ms": build_ms, "select_ms_geometric": ms_g, "select_ms_table": ms_t,
             "tables_differ_frac": differ, "ber_geometric": ber(pg), "ber_table": ber(pt)}
+
+
+def run_rvd(dev, name: str = "8x8-16qam-936sc", snr_index: int = 3, n_pe: int = 64):
+    """The real-valued decomposition beside the complex path on the 8x8
+    16-QAM workload (16 real levels; the 16x16 workload would need 32):
+    walk-kernel and whole-path time per slot, and the BER of each."""
+    import torch
+
+    from paper_2409_14355_gb300 import mpnl
+
+    sl = inputs.workload_slot(name, snr_index)
+    qam, nt = sl.qam, sl.nt
+    B = {4: 2, 16: 4, 64: 6}[qam]
+    H = torch.from_numpy(sl.H).to(dev)
+    Y = torch.from_numpy(sl.Y).to(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    rv = mpnl.run_slot_rvd(H, Y, sl.sigma2, qam, n_pe)
+    ms_rvd = timed(lambda: mpnl.run_slot_rvd(H, Y, sl.sigma2, qam, n_pe))
+    ms_rvd_walk = timed(lambda: mpnl.detect_rvd(rv["R"], rv["inv_diag"], rv["perm"], rv["paths"],
+                                                rv["Z"], sl.sigma2, qam,
+                                                out=(rv["hard"], rv["llr"], rv["ped2"])))
+    buf = mpnl.SlotBuffers(sl.H.shape[0], sl.Y.shape[1], sl.nr, nt, qam, n_pe, dev, mmse=False)
+    ms_cx = timed(lambda: mpnl.run_slot(buf, H, Y, sl.sigma2, mmse=False))
+    ms_cx_walk = timed(lambda: mpnl.detect(buf.R, buf.inv_diag, buf.perm, buf.paths, buf.Z,
+                                           sl.sigma2, qam, out=(buf.hard, buf.llr, buf.ped2)))
+    mpnl.check_status(dev.index)
+
+    def ber(hard):
+        h = hard.cpu().numpy()
+        e = sum(int(np.sum(((h >> (B - 1 - b)) & 1) != ((sl.labels >> (B - 1 - b)) & 1)))
+                for b in range(B))
+        return e / (sl.labels.size * B)
+
+    dets = sl.H.shape[0] * sl.Y.shape[1]
+    return {"workload": f"{name} snr {inputs.WORKLOADS[name]['snrs'][snr_index]} dB, N_pe {n_pe}",
+            "rvd_ms_per_slot": ms_rvd, "rvd_walk_ms": ms_rvd_walk,
+            "complex_ms_per_slot": ms_cx, "complex_walk_ms": ms_cx_walk,
+            "rvd_detections_per_s": dets / (ms_rvd / 1e3),
+            "complex_detections_per_s": dets / (ms_cx / 1e3),
+            "ber_rvd": ber(rv["hard"]), "ber_complex": ber(buf.hard)}
 
 
 def accuracy_vs_oracle(sl, ref, n_used, qam, n_pe, dev):
