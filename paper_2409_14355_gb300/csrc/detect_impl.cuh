@@ -772,10 +772,17 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     for (int r = tid; r < np2; r += kThreads) {
         if (r < nrows) {
             int mx = 1, ndev = 0, d1 = 0, d2 = 0, hi3 = 0, top = 1, second = 1;
+            // a 16-level row is one 16-byte load (rows are 16-byte aligned then)
+            const bool vec = NT == 16 && nt == 16 && r < n_pe;
+            uint4 row4 = make_uint4(0u, 0u, 0u, 0u);
+            if (vec) row4 = *reinterpret_cast<const uint4 *>(paths + ((size_t)sc * n_pe + r) * 16);
+            const unsigned rw[4] = {row4.x, row4.y, row4.z, row4.w};
+#pragma unroll
             for (int l = 0; l < NT; ++l) {
                 int v = 1;  // padding rows and levels: rank 1
                 if (r < n_pe && l < nt) {
-                    v = paths[((size_t)sc * n_pe + r) * nt + l];
+                    v = vec ? (int)((rw[l >> 2] >> (8 * (l & 3))) & 0xffu)
+                            : paths[((size_t)sc * n_pe + r) * nt + l];
                     if (v < 1 || v > QAM) {
                         atomicOr(status, kStatusBadPathEntry);
                         v = v < 1 ? 1 : QAM;
