@@ -181,8 +181,11 @@ typedef struct {
 } mpnl_rank_lut;
 
 /* Errors: as mpnl_select_paths; a table whose qam differs from dims->qam,
- * n_bins < 1 or NULL arrays.  Rows that break the cost rules are the
- * caller's error and give an unspecified (but bounded, in-range) table. */
+ * n_bins < 1 or NULL arrays.  Rows that break the cost rules (decreasing,
+ * NaN) are the caller's error: the position-vector table is then
+ * unspecified, though every access stays within its buffers, and
+ * mpnl_detect clamps ranks outside 1..qam and reports them through
+ * mpnl_check_status. */
 int mpnl_select_paths_lut(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, float sigma2,
                           const mpnl_rank_lut *lut, uint8_t *paths, void *ws, void *stream);
 
