@@ -135,6 +135,15 @@ int mpnl_factor(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, float sigma
 int mpnl_qhy(mpnl_ctx *ctx, const mpnl_dims *dims, const void *Q, const void *Y, void *Z,
              void *ws, void *stream);
 
+/* z = Q^H y as mpnl_qhy, on the tensor cores with FP16 operands and FP32
+ * accumulation (the Q^H y of the mixed-precision path): per subcarrier the
+ * symbols form one small real GEMM [Re y | Im y] [[Re Q, -Im Q]; [Im Q,
+ * Re Q]] = [Re z | Im z] (mma.sync m16n8k16).  Q and y are rounded to FP16
+ * (11-bit significand, range +-65504): each z_j is off by about 2^-11
+ * sum_i |Q_ij| |y_i|.  Arguments and errors as mpnl_qhy. */
+int mpnl_qhy_mixed(mpnl_ctx *ctx, const mpnl_dims *dims, const void *Q, const void *Y, void *Z,
+                   void *ws, void *stream);
+
 /* FP64 re-factorisation of ill-conditioned channels.  Run after
  * mpnl_preprocess / mpnl_preprocess_mmse (sigma2 > 0 selects the latter's
  * augmented matrix, 0 the plain one) or mpnl_factor (Y and Z NULL, Q not

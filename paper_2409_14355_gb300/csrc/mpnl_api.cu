@@ -640,6 +640,22 @@ int mpnl_qhy(mpnl_ctx *ctx, const mpnl_dims *d, const void *Q, const void *Y, vo
     return MPNL_OK;
 }
 
+int mpnl_qhy_mixed(mpnl_ctx *ctx, const mpnl_dims *d, const void *Q, const void *Y, void *Z,
+                   void *ws, void *stream)
+{
+    (void)ws;
+    MPNL_TRY(begin(ctx));
+    MPNL_TRY(check_dims(ctx, d, false, kNrAny));
+    if (d->n_sc == 0) return MPNL_OK;
+    MPNL_TRY(check_ptr(ctx, Q, 8, "Q", false));
+    MPNL_TRY(check_ptr(ctx, Y, 8, "Y", false));
+    MPNL_TRY(check_ptr(ctx, Z, 8, "Z", false));
+    cudaError_t e = mpnl::launch_qhy_mma(d->n_sc, d->n_sym, d->nr, d->nt, (const float2 *)Q,
+                                         (const float2 *)Y, (float2 *)Z, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, "qhy_mixed launch", e);
+    return MPNL_OK;
+}
+
 int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *d, const void *R, float sigma2,
                       uint8_t *paths, void *ws, void *stream)
 {

@@ -42,6 +42,10 @@ cudaError_t launch_refine(int n_sc, int n_sym, int nr, int nt, float sigma, floa
 // z = Q^H y from a stored Q (mpnl_qhy).
 cudaError_t launch_qhy(int n_sc, int n_sym, int nr, int nt, const float2 *Q, const float2 *Y,
                        float2 *Z, cudaStream_t stream);
+// The same on the tensor cores, FP16 operands, FP32 accumulation (mpnl_qhy_mixed).
+cudaError_t launch_qhy_mma(int n_sc, int n_sym, int nr, int nt, const float2 *Q, const float2 *Y,
+                           float2 *Z, cudaStream_t stream);
+size_t qhy_mma_warp_bytes(int n_sym, int nr, int nt);
 
 // warps: threads of one subcarrier's merges, 32 x (1, 2 or 4).
 cudaError_t launch_select_paths(int n_sc, int nt, int qam, int n_pe, float sigma2,

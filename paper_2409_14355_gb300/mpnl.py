@@ -41,7 +41,7 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy",
             "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr",
             "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs",
-            "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd")
+            "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd", "mpnl_qhy_mixed")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16 = 1, 2, 4
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
@@ -155,6 +155,8 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_refine_qr.restype = I
         lib.mpnl_qhy.argtypes = [P, D, P, P, P, P, P]
         lib.mpnl_qhy.restype = I
+        lib.mpnl_qhy_mixed.argtypes = [P, D, P, P, P, P, P]
+        lib.mpnl_qhy_mixed.restype = I
         lib.mpnl_batch_run.argtypes = [P, P, I, P]
         lib.mpnl_batch_run.restype = I
         lib.mpnl_batch_destroy.argtypes = [P]
@@ -281,8 +283,11 @@ def refine_qr(H, Y, R, inv_diag, perm, Z=None, Q=None, sigma2: float | None = No
                                          _ptr(count), None, _stream(dev)), ctx)
 
 
-def qhy(Q: torch.Tensor, Y: torch.Tensor, out=None):
-    """z = Q^H y for every symbol (Q from factor)."""
+def qhy(Q: torch.Tensor, Y: torch.Tensor, out=None, precision: str = "fp32"):
+    """z = Q^H y for every symbol (Q from factor).  precision "fp16":
+    mpnl_qhy_mixed (tensor cores, FP16 operands, FP32 accumulation)."""
+    if precision not in PRECISIONS:
+        raise MpnlError(ERR_INVALID_ARG, f"precision {precision!r} not in {PRECISIONS}")
     dev = _dev_of(Q)
     n_sc, nr, nt = Q.shape
     n_sym = Y.shape[1]
@@ -291,8 +296,8 @@ def qhy(Q: torch.Tensor, Y: torch.Tensor, out=None):
     Z = out if out is not None else torch.empty((n_sc, n_sym, nt), dtype=torch.complex64, device=dev)
     ctx = context(dev.index)
     d = Dims(n_sc, n_sym, nr, nt, 4, 1)
-    _raise(load_library().mpnl_qhy(ctx, ctypes.byref(d), _ptr(Q), _ptr(Y), _ptr(Z), None,
-                                   _stream(dev)), ctx)
+    fn = load_library().mpnl_qhy_mixed if precision == "fp16" else load_library().mpnl_qhy
+    _raise(fn(ctx, ctypes.byref(d), _ptr(Q), _ptr(Y), _ptr(Z), None, _stream(dev)), ctx)
     return Z
 
 
