@@ -337,7 +337,8 @@ typedef struct {
 
 #define MPNL_ITEM_MMSE_QR 1      /* MMSE-extended QR (mpnl_preprocess_mmse); allows nt > nr */
 #define MPNL_ITEM_LINEAR_MMSE 2  /* also run the linear MMSE baseline */
-#define MPNL_ITEM_FP16 4         /* walks with FP16 residuals, as mpnl_detect_mixed */
+#define MPNL_ITEM_FP16 4         /* the mixed-precision path: walks as mpnl_detect_mixed and,
+                                    in the Q^H y stage, z as mpnl_qhy_mixed */
 
 /* Stages run in the order QR, selection, Q^H y, walks, MMSE.  A unit whose
  * stages include MPNL_STAGE_QHY gets z from its stored Q; otherwise, if its

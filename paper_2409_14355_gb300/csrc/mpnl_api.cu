@@ -274,6 +274,8 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
         }
         if (st_bits & MPNL_STAGE_SELECT) sel = std::max(sel, mpnl::select_group_bytes(d->n_pe));
         if (qhy_on) qhy = std::max(qhy, mpnl::qhy_warp_bytes(d->n_sym, d->nr, d->nt));
+        if (qhy_on && (it.flags & MPNL_ITEM_FP16))
+            qhy = std::max(qhy, mpnl::qhy_mma_warp_bytes(d->n_sym, d->nr, d->nt));
         if (st_bits & MPNL_STAGE_DETECT)
             det = std::max(det, mpnl::detect_smem_bytes(d->nt, d->qam, d->n_pe, d->n_sym));
         if (st_bits & MPNL_STAGE_MMSE) mm = std::max(mm, mpnl::mmse_warp_bytes(d->n_sym, d->nr, d->nt));

@@ -17,6 +17,7 @@
 
 #include "mpnl_common.cuh"
 #include "mpnl_internal.h"
+#include "qhy_mma.cuh"
 
 namespace mpnl {
 namespace {
@@ -307,7 +308,10 @@ qhy_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ st
         if (w >= total) break;
         const int i = find_item(start, n_items, w);
         const BatchItem &it = items[i];
-        qhy_warp(w - start[i], it.n_sym, it.nr, it.nt, it.Q, it.Y, it.Z, warp * warp_bytes);
+        // FP16-residual units take the tensor-core Q^H y of the mixed path
+        if (it.f16) qhy_mma_warp(w - start[i], it.n_sym, it.nr, it.nt, it.Q, it.Y, it.Z,
+                                 warp * warp_bytes);
+        else qhy_warp(w - start[i], it.n_sym, it.nr, it.nt, it.Q, it.Y, it.Z, warp * warp_bytes);
     }
 }
 

@@ -55,7 +55,7 @@ class RU:
     sigma2: float
     mmse_qr: bool = False
     n_sym: int = 14
-    precision: str = "fp32"   # walk arithmetic: "fp32" or "fp16" residuals
+    precision: str = "fp32"   # "fp16": tensor-core Q^H y and FP16-residual walks
     state: dict = field(default_factory=dict)   # Q, R, inv_diag, perm, paths (device)
     busy_rounds: set = field(default_factory=set)
     pool: list = field(default_factory=list)    # free per-slot buffer sets

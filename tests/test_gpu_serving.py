@@ -65,7 +65,7 @@ def _alone(dev, ru, H, Y):
     from paper_2409_14355_gb300 import mpnl
     Q, R, inv_diag, perm = mpnl.factor(H.to(dev), ru.sigma2 if ru.mmse_qr else None)
     paths = mpnl.select_paths(R, ru.sigma2, ru.qam, ru.n_pe, ru.nt)
-    Z = mpnl.qhy(Q, Y.to(dev))
+    Z = mpnl.qhy(Q, Y.to(dev), precision=ru.precision)
     hard, llr, _ = mpnl.detect(R, inv_diag, perm, paths, Z, ru.sigma2, ru.qam,
                                precision=ru.precision)
     return hard.cpu(), llr.cpu()
