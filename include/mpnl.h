@@ -244,8 +244,10 @@ int mpnl_detect_rvd(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const f
 int mpnl_rank_counts(mpnl_ctx *ctx, int qam, int n_bins, const double *gamma, long long n_trials,
                      unsigned long long seed, unsigned long long *counts, void *stream);
 
-/* Rank costs from the histogram (a reading): P(k) = max(counts, 1/2) /
- * n_trials, c(k) = log P(1) - log P(k), made nondecreasing in k by a running
+/* Rank costs from the histogram (a reading): c(k) = log P(1) - log P(k)
+ * with P(k) = counts / n_trials for the ranks seen; a rank never seen is
+ * taken as half as likely as the rank before it (c(k) = c(k-1) + ln 2), rank
+ * 1 never seen as half a trial; then made nondecreasing in k by a running
  * maximum, c(1) = 0 -- the cost table of mpnl_select_paths_lut.
  *   counts  in   u64 [n_bins][qam];  cost  out  f32 [n_bins][qam]  (device)
  * Errors: as mpnl_rank_counts. */

@@ -55,6 +55,7 @@ typedef double complex cplx;
  * that no level is ever treated as error-free (keeps every log finite). */
 #define ORC_PE_FLOOR 1e-12
 #define ORC_PI 3.14159265358979323846
+#define ORC_LN2 0.69314718055994530942
 
 static int bits_of(int qam)
 {
@@ -390,12 +391,14 @@ int orc_select_paths(int nt, int qam, const double *rdiag, double sigma2, int n_
  * 2^-53, in (0, 1).  Noise by Box-Muller: r = sqrt(-2 ln u1 / (2 gamma)),
  * n = r (cos 2 pi u2, sin 2 pi u2).
  *
- * Costs (Reading): P(k) = max(counts[k-1], 1/2) / n_trials (half a count for
- * a rank never seen, so every log is finite), c(k) = log P(1) - log P(k),
- * then made nondecreasing in k by a running maximum (so the top-N set stays
- * downward-closed); c(1) = 0.  Selection then maximises -sum_l c_l(p_l),
- * which orders vectors as sum_l log P_l(p_l) does wherever P is
- * nonincreasing.
+ * Costs (Reading): P(k) = counts[k-1] / n_trials, c(k) = log P(1) - log P(k)
+ * for the ranks seen; a rank never seen is taken as half as likely as the
+ * rank before it (c(k) = c(k-1) + ln 2, a geometric tail: every cost finite
+ * and the unseen ranks still ordered); rank 1 never seen counts as half a
+ * trial.  The costs are then made nondecreasing in k by a running maximum
+ * (so the top-N set stays downward-closed); c(1) = 0.  Selection then
+ * maximises -sum_l c_l(p_l), which orders vectors as sum_l log P_l(p_l)
+ * does wherever P is nonincreasing.
  *
  * Lookup: the bin of a level is the number of edges e (ascending, n_bins - 1
  * of them) with gamma >= e, where gamma = R_ll^2 / sigma2 is formed in
@@ -460,8 +463,8 @@ int orc_rank_costs(int qam, int n_bins, const long long *counts, long long n_tri
         double lp1 = log((cnt[0] > 0 ? (double)cnt[0] : 0.5) / (double)n_trials);
         c[0] = 0.0;
         for (int k = 1; k < M; k++) {
-            double lp = log((cnt[k] > 0 ? (double)cnt[k] : 0.5) / (double)n_trials);
-            double v = lp1 - lp;
+            double v = cnt[k] > 0 ? lp1 - log((double)cnt[k] / (double)n_trials)
+                                  : c[k - 1] + ORC_LN2;
             c[k] = v > c[k - 1] ? v : c[k - 1];
         }
     }

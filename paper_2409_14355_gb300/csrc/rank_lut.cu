@@ -29,6 +29,7 @@ namespace {
 
 constexpr int kLutThreads = 256;
 constexpr double kTwoPi = 6.283185307179586476925;
+constexpr double kLn2 = 0.69314718055994530942;
 
 __device__ __forceinline__ unsigned long long splitmix64_at(unsigned long long seed,
                                                             unsigned long long n)
@@ -91,8 +92,10 @@ rank_counts_kernel(const double *__restrict__ gamma, long long n_trials, unsigne
         atomicAdd(counts + (size_t)bin * M + threadIdx.x, (unsigned long long)hist[threadIdx.x]);
 }
 
-// Costs (a reading): P(k) = max(count_k, 1/2) / n_trials (half a count for a
-// rank never seen, so every log is finite), c(k) = log P(1) - log P(k), made
+// Costs (a reading): c(k) = log P(1) - log P(k) with P(k) = count_k /
+// n_trials for the ranks seen; a rank never seen is taken as half as likely
+// as the rank before it (c(k) = c(k-1) + ln 2: every cost finite, the unseen
+// ranks still ordered); rank 1 never seen counts as half a trial.  Made
 // nondecreasing in k by a running maximum; c(1) = 0.  One thread per bin.
 __global__ void rank_costs_kernel(int qam, int n_bins, const unsigned long long *__restrict__ counts,
                                   long long n_trials, float *__restrict__ cost)
@@ -106,8 +109,7 @@ __global__ void rank_costs_kernel(int qam, int n_bins, const unsigned long long 
     double run = 0.0;
     c[0] = 0.f;
     for (int k = 1; k < qam; ++k) {
-        const double lp = log((cnt[k] > 0 ? (double)cnt[k] : 0.5) / n);
-        const double v = lp1 - lp;
+        const double v = cnt[k] > 0 ? lp1 - log((double)cnt[k] / n) : run + kLn2;
         run = v > run ? v : run;
         c[k] = (float)run;
     }

@@ -64,8 +64,16 @@ def test_costs_are_zero_at_rank_one_and_nondecreasing():
     k = 1
     assert counts[1, 0] > counts[1, k] > 0
     assert math.isclose(math.exp(-cost[1, k]), p[k] / p[0], rel_tol=1e-12)
-    # a rank never seen counts as half a trial: a finite cost
+    # ranks never seen: each half as likely as the one before it (ln 2 more)
     assert np.all(np.isfinite(cost))
+    c = np.zeros((1, 16), np.int64)
+    c[0, :4] = [9000, 700, 250, 50]
+    cc = oracle.rank_costs(c, 10_000)[0]
+    np.testing.assert_allclose(np.diff(cc[3:]), math.log(2.0), rtol=1e-12)
+    assert math.isclose(cc[3], math.log(9000 / 50), rel_tol=1e-12)
+    # rank 1 never seen: half a trial
+    c0 = np.array([[0, 3, 1, 0]], np.int64)
+    assert math.isclose(oracle.rank_costs(c0, 100)[0, 1], max(0.0, math.log(0.5 / 3)), abs_tol=1e-12)
 
 
 def _bins(rdiag, sigma2, edges):
