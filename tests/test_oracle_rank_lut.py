@@ -32,13 +32,13 @@ def test_qpsk_rank_probabilities_closed_form(snr_db):
     assert _binomial_ok(c[1] + c[2], n, 2 * q * (1 - q))
 
 
-@pytest.mark.parametrize("snr_db", [8.0, 14.0, 20.0])
-def test_16qam_rank_one_is_the_exact_symbol_error_rate(snr_db):
-    # square 16QAM: P(correct) = (1 - 2 (1 - 1/4) Q(sqrt(3 gamma / 15)))^2 (Proakis)
+@pytest.mark.parametrize("qam,snr_db", [(16, 8.0), (16, 14.0), (16, 20.0), (64, 16.0), (64, 24.0)])
+def test_rank_one_is_the_exact_symbol_error_rate(qam, snr_db):
+    # square M-QAM: P(correct) = (1 - 2 (1 - 1/sqrt M) Q(sqrt(3 gamma / (M - 1))))^2 (Proakis)
     g = 10 ** (snr_db / 10)
     n = 100_000
-    c = oracle.rank_counts_mc(16, [g], n, seed=11)[0]
-    p1 = (1 - 1.5 * qfunc(math.sqrt(g / 5))) ** 2
+    c = oracle.rank_counts_mc(qam, [g], n, seed=11)[0]
+    p1 = (1 - 2 * (1 - 1 / math.sqrt(qam)) * qfunc(math.sqrt(3 * g / (qam - 1)))) ** 2
     assert _binomial_ok(c[0], n, p1)
 
 

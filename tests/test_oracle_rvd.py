@@ -1,8 +1,9 @@
 """Pins of the oracle's real-valued decomposition (RVD) variant: a complete
 list over the 2 nt real levels is exhaustive ML, equal to the complex
 model's complete list; N_pe = 1 is the real sorted-QR SIC written as a plain
-slicer loop; noise-free recovery; selection against brute force; the axes
-join back to the constellation's points."""
+slicer loop; noise-free recovery; selection against brute force; the PAM
+level error model against simulated slicing; the axes join back to the
+constellation's points."""
 import itertools
 import math
 
@@ -138,3 +139,22 @@ def test_pam_selection_matches_bruteforce(ntr, qam, n_pe):
         sep = np.abs(np.diff(score)) > 1e-9
         ok = np.concatenate([[True], sep]) & np.concatenate([sep, [True]])
         np.testing.assert_array_equal(paths[ok], want[ok])
+
+
+@pytest.mark.parametrize("qam,snr_db", [(4, 6.0), (16, 14.0), (64, 22.0)])
+def test_pam_level_model_matches_simulated_slicing(qam, snr_db):
+    # a real level b = s + n / R_ll with noise sigma2/2 per real dimension:
+    # simulate the slicer and compare its error rate with the model's Pe
+    rng = np.random.default_rng(qam)
+    pam = oracle.pam_points(qam)
+    sigma2 = 1.0
+    gamma = 10 ** (snr_db / 10)
+    rll = math.sqrt(gamma * sigma2)
+    n = 400_000
+    a = rng.integers(0, len(pam), n)
+    b = pam[a] + rng.standard_normal(n) * math.sqrt(sigma2 / 2) / rll
+    dec = np.argmin(np.abs(b[:, None] - pam[None, :]), axis=1)
+    ser = np.mean(dec != a)
+    _, _, pe = oracle.select_paths_pam(np.array([rll]), sigma2, qam, 1)
+    sd = math.sqrt(pe[0] * (1 - pe[0]) / n)
+    assert abs(ser - pe[0]) <= 5 * sd, (ser, pe[0])
