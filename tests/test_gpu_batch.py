@@ -1,7 +1,6 @@
 """Mixed-size batches in persistent launches (mpnl_batch_*): every unit's
 results in the mix equal the per-call path on that unit alone, with and
 without a captured CUDA graph; launch-shape knobs leave results unchanged."""
-import numpy as np
 import pytest
 
 from paper_2409_14355_gb300 import inputs

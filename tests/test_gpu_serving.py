@@ -4,7 +4,6 @@ with the channel that applied to it; z from a stored Q matches the oracle."""
 import numpy as np
 import pytest
 
-import oracle
 from paper_2409_14355_gb300 import inputs
 
 torch = pytest.importorskip("torch")
