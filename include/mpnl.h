@@ -17,6 +17,11 @@
  *   mpnl_detect        N_pe SIC / partial-Euclidean-distance walks, argmin
  *                      -> hard decisions, max-log LLRs over the list
  *   mpnl_linear_mmse   linear MMSE baseline (hard decisions + LLRs)
+ * Variants: mpnl_preprocess_mmse (more users than antennas), mpnl_detect_mixed
+ * and mpnl_qhy_mixed (FP16), mpnl_refine_qr (FP64 re-factorisation), the
+ * rank-cost table (mpnl_rank_counts, mpnl_rank_costs), the real-valued
+ * decomposition (mpnl_rvd_embed, mpnl_select_paths_pam, mpnl_detect_rvd);
+ * for serving: mpnl_factor, mpnl_qhy and the batch calls (mpnl_batch_*).
  *
  * Conventions shared by every call
  * --------------------------------
