@@ -76,3 +76,22 @@ def test_binding_refuses_to_run_without_gpu(lib):
     H = torch.zeros((2, 4, 4), dtype=torch.complex64)
     with pytest.raises(mpnl.MpnlError):
         mpnl.preprocess(H, torch.zeros((2, 14, 4), dtype=torch.complex64))
+
+
+def test_binding_argument_checks_need_no_gpu(lib):
+    # checks the binding makes before touching a device
+    import torch
+    from paper_2409_14355_gb300 import mpnl
+    with pytest.raises(ValueError):
+        mpnl.SlotPipeline(4, 14, 4, 4, 4, 16, device="cuda:0", depth=0)
+    edges = torch.zeros(3, dtype=torch.float32)
+    with pytest.raises(ValueError):            # 4 bins need 3 edges and a [4][qam] table
+        mpnl.RankLut(16, edges, torch.zeros((5, 16)))
+    with pytest.raises(ValueError):
+        mpnl.RankLut(16, edges, torch.zeros((4, 64)))
+    lut = mpnl.RankLut(16, edges, torch.zeros((4, 16)))
+    c = lut.c_struct()
+    assert (c.qam, c.n_bins) == (16, 4)
+    with pytest.raises(mpnl.MpnlError):        # precision names are checked first
+        mpnl.qhy(torch.zeros((1, 4, 4), dtype=torch.complex64),
+                 torch.zeros((1, 14, 4), dtype=torch.complex64), precision="bf8")
