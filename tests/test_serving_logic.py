@@ -126,3 +126,29 @@ def test_large_rounds_leave_room_for_small_units():
     s.rounds[0].event = None                       # the large round completed
     chosen, _ = s._form()
     assert [q.rid for q in chosen] == [0, 2]       # both large units, one round
+
+
+def test_latency_statistics_per_size_class():
+    reqs = []
+    # ten small-unit slots at 0.1 .. 1.0 ms, five large-unit slots at 2 ms,
+    # a channel update and an unfinished slot that must not count
+    for k in range(10):
+        q = _req(k, 0, "slot")
+        q.arrival, q.done = 0.0, (k + 1) * 1e-4
+        reqs.append(q)
+    for k in range(5):
+        q = _req(10 + k, 3, "slot")
+        q.arrival, q.done = 1.0, 1.0 + 2e-3
+        reqs.append(q)
+    ch = _req(20, 0, "channel")
+    ch.arrival, ch.done = 0.0, 5.0
+    reqs.append(ch)
+    reqs.append(_req(21, 0, "slot"))                 # never done
+    st = serving.latency_stats(reqs, deadline_s=0.5e-3, dets_of=lambda q: 100,
+                               big_of=lambda q: q.ru == 3)
+    assert st["requests"] == 17 and st["slots_done"] == 15
+    assert abs(st["small_units"]["p50_ms"] - 0.55) < 1e-9
+    assert st["small_units"]["miss_rate"] == 0.5     # 0.6 .. 1.0 ms are over 0.5 ms
+    assert st["large_units"]["miss_rate"] == 1.0 and abs(st["large_units"]["p50_ms"] - 2.0) < 1e-9
+    assert abs(st["miss_rate"] - 10 / 15) < 1e-12
+    assert abs(st["detections_per_s"] - 15 * 100 / (1.0 + 2e-3)) < 1e-6
