@@ -95,3 +95,16 @@ def test_binding_argument_checks_need_no_gpu(lib):
     with pytest.raises(mpnl.MpnlError):        # precision names are checked first
         mpnl.qhy(torch.zeros((1, 4, 4), dtype=torch.complex64),
                  torch.zeros((1, 14, 4), dtype=torch.complex64), precision="bf8")
+
+
+def test_header_is_plain_c():
+    # the boundary is a C ABI: the header compiles as strict C99 and as C++
+    import shutil
+    import subprocess
+    hdr = os.path.join(ROOT, "include", "mpnl.h")
+    for cc, std in (("gcc", ["-std=c99", "-pedantic", "-x", "c"]), ("g++", ["-x", "c++"])):
+        if shutil.which(cc) is None:
+            pytest.skip(f"{cc} not installed")
+        r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Wextra", "-Werror", *std, hdr],
+                           capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
