@@ -397,6 +397,48 @@ int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *batch, int stages, void *stream);
 /* Release a batch (NULL is ignored); its work must have completed. */
 void mpnl_batch_destroy(mpnl_batch *batch);
 
+/* Walks of up to MPNL_NOALLOC_MAX_UNITS radio units in one persistent launch,
+ * without allocating anything.  The paper has no counterpart: this is an
+ * interface for callers that must not allocate device memory once they are
+ * running -- a distributed unit's real-time threads, where cudaMalloc and
+ * cudaFree can block or synchronise the device and so cost a slot deadline,
+ * and host frameworks that hand out all device memory from their own pool
+ * and forbid libraries to allocate behind their back.  Those callers cannot
+ * create an mpnl_batch (its creation allocates the descriptor table and work
+ * counters) or even an mpnl_ctx (which allocates a status word).
+ *
+ * Each item is as for the batch calls, restricted to the walk stage: dims,
+ * sigma2, flags (0 or MPNL_ITEM_FP16, the arithmetic of mpnl_detect_mixed),
+ * stages (0 or MPNL_STAGE_DETECT), and the device arrays R, inv_diag, perm,
+ * Z, paths (inputs, as mpnl_preprocess and mpnl_select_paths write them) and
+ * hard, llr, ped2 (outputs; llr and ped2 nullable).  The other fields are
+ * ignored.  Results equal those of mpnl_detect / mpnl_detect_mixed on each
+ * unit alone.  Runs on the calling thread's current device; every array must
+ * be reachable from it.
+ *
+ * The scratch the persistent kernel needs (the units' descriptors, the
+ * prefix sums of their subcarrier counts, its work counter and a status
+ * word; about 10 KB for 64 units) is one fixed array in the library's device
+ * code, held by every device that loads the library until the process exits.
+ * The first call on a device looks up that array's device address (and the
+ * SM count); make that first call before capturing any stream into a graph.
+ * Every call reuses the same array: the work counter and status word are
+ * cleared at the start of each call, and two calls whose work overlaps on
+ * the device (on different streams, or from different threads without
+ * ordering) race on the array and give wrong results.  Calls on one stream
+ * are ordered and safe.  The host copies the descriptors from the caller's
+ * stack (pageable memory), so the call returns once they have been staged.
+ * Table entries outside 1..qam are clamped as by mpnl_detect but not
+ * reported (there is no context to hold the status).
+ *
+ * Returns MPNL_OK; MPNL_ERR_INVALID_ARG (NULL items, n_items < 1, a bad size,
+ * flag, stage, sigma2 or pointer in some item); MPNL_ERR_UNSUPPORTED (n_items
+ * > MPNL_NOALLOC_MAX_UNITS, or a unit needing more shared memory than an SM
+ * has); MPNL_ERR_CUDA (no current device, set-up or launch failed).  There
+ * is no context, so no message: the code is the whole report. */
+#define MPNL_NOALLOC_MAX_UNITS 64
+int mpnl_detect_units_noalloc(const mpnl_batch_item *items, int n_items, void *stream);
+
 /* Launch-shape knobs.  They change how the work is spread over threads,
  * never the results.  Indexed by problem class: nt class (0: nt <= 4,
  * 1: nt <= 8, 2: nt <= 16), qam class (0: 4, 1: 16, 2: 64) and N_pe class

@@ -41,13 +41,15 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy",
             "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr",
             "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs",
-            "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd", "mpnl_qhy_mixed")
+            "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd", "mpnl_qhy_mixed",
+            "mpnl_detect_units_noalloc")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16 = 1, 2, 4
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
 RUN_GRAPH = 16
 RUN_SHARE_SMS = 64
 RESET_TRUSTED_POINTERS = 1
+NOALLOC_MAX_UNITS = 64
 PRECISIONS = ("fp32", "fp16")
 
 
@@ -161,6 +163,8 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_batch_run.restype = I
         lib.mpnl_batch_destroy.argtypes = [P]
         lib.mpnl_batch_destroy.restype = None
+        lib.mpnl_detect_units_noalloc.argtypes = [ctypes.POINTER(BatchItemC), I, P]
+        lib.mpnl_detect_units_noalloc.restype = I
         lib.mpnl_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
         lib.mpnl_set_tuning.restype = I
         lib.mpnl_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
@@ -795,3 +799,18 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def detect_units_noalloc(items, stream=None) -> None:
+    """Walks of up to NOALLOC_MAX_UNITS units in one persistent launch with
+    no device allocation (mpnl_detect_units_noalloc).  `items` are BatchItemC
+    descriptors (see batch_item) of device tensors the caller keeps alive:
+    R, inv_diag, perm, Z, paths in, hard, llr, ped2 out.  The walks run on
+    `stream` (default: the current stream) of the current device; calls whose
+    work overlaps on the device share one scratch array and race."""
+    arr = items if isinstance(items, ctypes.Array) else (BatchItemC * len(items))(*items)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    code = load_library().mpnl_detect_units_noalloc(arr, len(arr), ctypes.c_void_p(st.cuda_stream))
+    if code != OK:
+        raise MpnlError(code, "mpnl_detect_units_noalloc failed (no context: the code is the report)")
