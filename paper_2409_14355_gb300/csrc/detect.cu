@@ -9,7 +9,11 @@ size_t detect_smem_bytes(int nt, int qam, int n_pe, int n_sym)
 {
     const int NT = nt <= 4 ? 4 : (nt <= 8 ? 8 : 16);
     const int B = qam == 4 ? 2 : (qam == 16 ? 4 : 6);
-    return det_layout(NT, B, n_pe, n_sym, (NT * B + 31) / 32).bytes;
+    // the larger of the two precisions' layouts (a batch mixes them)
+    const int W = (NT * B + 31) / 32;
+    const int a = det_layout(NT, B, n_pe, n_sym, W, false).bytes;
+    const int b = det_layout(NT, B, n_pe, n_sym, W, true).bytes;
+    return (size_t)(a > b ? a : b);
 }
 
 cudaError_t launch_detect(int n_sc, int n_sym, int nt, int qam, int n_pe, float sigma2,

@@ -404,8 +404,8 @@ __host__ __device__ inline int pow2_at_least(int n)
 
 struct DetSmem {
     int off_rc, off_r2, off_invd, off_perm, off_z, off_tab, off_order, off_m, off_best, off_wmin,
-        off_second, off_blab, off_top, off_l2, off_lut, off_rh, off_key2, off_blab2, off_scr,
-        bytes;
+        off_second, off_blab, off_top, off_l2, off_lut, off_rh, off_key2, off_blab2, off_rp,
+        off_scr, bytes;
 };
 
 // Small per-CTA counters of one subcarrier, kept in the dynamic shared
@@ -417,7 +417,11 @@ constexpr int kScrK1 = 0, kScrOff1 = 65, kScrUse2 = 130, kScrKmax = 131, kScrHis
               kScrWsum = 388, kScrInts = 388 + kWarps;
 static_assert(kThreads == 256, "the row sort gives each thread one of the 256 buckets");
 
-__host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym, int WORDS)
+// f16: the layout of the mixed-precision instances (half2 columns of R and
+// the runner-up rows for the FP32 re-check) instead of the FP32 instances'
+// packed-FMA columns of R.
+__host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym, int WORDS,
+                                              bool f16)
 {
     const int chunks = (n_pe + 31) / 32;
     const int np2 = pow2_at_least(chunks * 32);
@@ -453,13 +457,21 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     o = a16(o + (n_sym + 1) * kList2 * 16);
     s.off_lut = o;  // 2-D label of grid point (ire, iim) at ire * 8 + iim
     o = a16(o + 64);
-    // mixed precision only: R columns as half2 pairs, runner-up key and labels
-    s.off_rh = o;
-    o = a16(o + NT * NT * 8);
-    s.off_key2 = o;
-    o = a16(o + n_sym * chunks * 8);
-    s.off_blab2 = o;
-    o = a16(o + n_sym * chunks * WORDS * 4);
+    s.off_rh = s.off_key2 = s.off_blab2 = s.off_rp = o;
+    if (f16) {
+        // mixed precision: R columns as half2 pairs, runner-up key and labels
+        s.off_rh = o;
+        o = a16(o + NT * NT * 8);
+        s.off_key2 = o;
+        o = a16(o + n_sym * chunks * 8);
+        s.off_blab2 = o;
+        o = a16(o + n_sym * chunks * WORDS * 4);
+    } else {
+        // FP32: each term of the columns of R as {-Re, -Re, Im, Im} for the
+        // packed FMAs of the cancellation
+        s.off_rp = o;
+        o = a16(o + NT * NT * 16);
+    }
     s.off_scr = o;
     o = a16(o + kScrInts * 4);
     s.bytes = o;
@@ -572,33 +584,6 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
     }
 }
 
-// Interference cancellation fused with the shift of the residual register
-// file after level l is decided: e'[i] = e[i+1] - R_{l-1-i, l} s for i < W
-// (W >= l; col = the staged column l of R, bottom-up, two entries per 16-byte
-// broadcast load serving both symbols).  e'[i] for i >= W is not needed.
-template <int W, int NT, int SYM>
-__device__ __forceinline__ void cancel_shift(float (&ex)[SYM][NT], float (&ey)[SYM][NT],
-                                             const float2 *col, const float (&sx)[SYM],
-                                             const float (&sy)[SYM])
-{
-    static_assert(W < NT, "the shift reads entry W");
-    const float4 *c4 = reinterpret_cast<const float4 *>(col);
-#pragma unroll
-    for (int i2 = 0; i2 < (W + 1) / 2; ++i2) {
-        const float4 r = c4[i2];
-        const int i = 2 * i2;
-#pragma unroll
-        for (int k = 0; k < SYM; ++k) {
-            ex[k][i] = fmaf(-r.x, sx[k], fmaf(r.y, sy[k], ex[k][i + 1]));
-            ey[k][i] = fmaf(-r.x, sy[k], fmaf(-r.y, sx[k], ey[k][i + 1]));
-            if (i + 1 < W) {
-                ex[k][i + 1] = fmaf(-r.z, sx[k], fmaf(r.w, sy[k], ex[k][i + 2]));
-                ey[k][i + 1] = fmaf(-r.z, sy[k], fmaf(-r.w, sx[k], ey[k][i + 2]));
-            }
-        }
-    }
-}
-
 // half2 variant: e + (-Re,-Re)*(sx,sy) + (Im,-Im)*(sy,sx) per complex term.
 template <int W, int NT, int SYM>
 __device__ __forceinline__ void cancel_shift_h(__half2 (&eh)[SYM][NT], const uint2 *colh,
@@ -626,24 +611,6 @@ __device__ __forceinline__ void cancel_shift_h(__half2 (&eh)[SYM][NT], const uin
 // at most three unused terms (widths 15, 11, 7, 3 for NT = 16); level 0
 // needs no cancellation.  l is warp-uniform, so the branches do not diverge.
 template <int NT, int SYM>
-__device__ __forceinline__ void cancel_level(int l, float (&ex)[SYM][NT], float (&ey)[SYM][NT],
-                                             const float2 *col, const float (&sx)[SYM],
-                                             const float (&sy)[SYM])
-{
-    if constexpr (NT == 16) {
-        if (l > 11) cancel_shift<15>(ex, ey, col, sx, sy);
-        else if (l > 7) cancel_shift<11>(ex, ey, col, sx, sy);
-        else if (l > 3) cancel_shift<7>(ex, ey, col, sx, sy);
-        else if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
-    } else if constexpr (NT == 8) {
-        if (l > 3) cancel_shift<7>(ex, ey, col, sx, sy);
-        else if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
-    } else {
-        if (l > 0) cancel_shift<3>(ex, ey, col, sx, sy);
-    }
-}
-
-template <int NT, int SYM>
 __device__ __forceinline__ void cancel_level_h(int l, __half2 (&eh)[SYM][NT], const uint2 *colh,
                                                const __half2 (&sh)[SYM], const __half2 (&sw)[SYM])
 {
@@ -659,6 +626,49 @@ __device__ __forceinline__ void cancel_level_h(int l, __half2 (&eh)[SYM][NT], co
         if (l > 0) cancel_shift_h<3>(eh, colh, sh, sw);
     }
 }
+
+// FP32 cancellation with packed FMAs (two FP32 FMAs per instruction):
+// e'[i] = e[i+1] - R_{l-1-i, l} s as
+//   e'[i] = (-Re R, -Re R) * (sx, sy) + ((Im R, Im R) * (sy, -sx) + e[i+1]),
+// component by component the same two roundings as the scalar form
+// fmaf(-Re R, sx, fmaf(Im R, sy, ex)), fmaf(-Re R, sy, fmaf(-Im R, sx, ey)).
+// col = the staged column l as {-Re, -Re, Im, Im} per term (a broadcast
+// 16-byte load serving SYM walks); q = (sy, -sx).
+template <int W, int NT, int SYM>
+__device__ __forceinline__ void cancel_shift2(float2 (&e)[SYM][NT], const float4 *col,
+                                              const float2 (&sv)[SYM], const float2 (&q)[SYM])
+{
+    static_assert(W < NT, "the shift reads entry W");
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const float4 r = col[i];
+        const float2 a = make_float2(r.x, r.y), b = make_float2(r.z, r.w);
+#pragma unroll
+        for (int k = 0; k < SYM; ++k) e[k][i] = __ffma2_rn(a, sv[k], __ffma2_rn(b, q[k], e[k][i + 1]));
+    }
+}
+
+template <int NT, int SYM>
+__device__ __forceinline__ void cancel_level2(int l, float2 (&e)[SYM][NT], const float4 *col,
+                                              const float2 (&sv)[SYM], const float2 (&q)[SYM])
+{
+    if constexpr (NT == 16) {
+        if (l > 11) cancel_shift2<15>(e, col, sv, q);
+        else if (l > 7) cancel_shift2<11>(e, col, sv, q);
+        else if (l > 3) cancel_shift2<7>(e, col, sv, q);
+        else if (l > 0) cancel_shift2<3>(e, col, sv, q);
+    } else if constexpr (NT == 8) {
+        if (l > 3) cancel_shift2<7>(e, col, sv, q);
+        else if (l > 0) cancel_shift2<3>(e, col, sv, q);
+    } else {
+        if (l > 0) cancel_shift2<3>(e, col, sv, q);
+    }
+}
+
+template <bool V>
+struct BoolTag {
+    static constexpr bool value = V;
+};
 
 // One subcarrier of a slot, by one CTA of kThreads threads.
 // F16: the interference-cancelled residuals e are kept as half2 (re, im) and
@@ -687,7 +697,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     const int chunks = (n_pe + 31) / 32;
     const int nrows = chunks * 32;
     const int np2 = pow2_at_least(nrows);
-    const DetSmem S = det_layout(NT, B, n_pe, n_sym, WORDS);
+    const DetSmem S = det_layout(NT, B, n_pe, n_sym, WORDS, F16);
     // sRr[l*NT + i] = R_{l-1-i, l} for i < l (column l of R above the
     // diagonal, bottom-up: the order the shift-register walk consumes it)
     float2 *sRr = reinterpret_cast<float2 *>(smem + S.off_rc);
@@ -709,6 +719,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     int &s_use2 = sScr[kScrUse2];
     uint8_t *sLut = smem + S.off_lut;
     uint2 *sRh = reinterpret_cast<uint2 *>(smem + S.off_rh);  // sRr as {(-Re,-Re), (Im,-Im)} half2
+    float4 *sRp = reinterpret_cast<float4 *>(smem + S.off_rp);  // sRr as {-Re, -Re, Im, Im}
     unsigned long long *sKey2 = reinterpret_cast<unsigned long long *>(smem + S.off_key2);
     uint32_t *sBlab2 = reinterpret_cast<uint32_t *>(smem + S.off_blab2);
     int &s_kmax = sScr[kScrKmax];
@@ -727,6 +738,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
             v = gR[r * nt - (r * (r - 1)) / 2 + (l - r)];
         }
         sRr[k] = v;
+        if constexpr (!F16) sRp[k] = make_float4(-v.x, -v.x, v.y, v.y);
         if constexpr (F16) {
             const __half2 a = __floats2half2_rn(-v.x, -v.x), b = __floats2half2_rn(v.y, -v.y);
             sRh[k] = make_uint2(*reinterpret_cast<const unsigned *>(&a),
@@ -739,7 +751,8 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     }
     for (int k = tid; k < NT; k += kThreads) {
         if (k < nt) {
-            sInvd[k] = inv_diag[(size_t)sc * nt + k];
+            const float iv = inv_diag[(size_t)sc * nt + k];
+            sInvd[k] = iv;
             sPerm[k] = perm[(size_t)sc * nt + k];
         }
     }
@@ -896,122 +909,142 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
         const int row = (int)sOrder[np2 + chunk * 32 + lane];
         const bool active = row < n_pe;
         const uint8_t *trow = sTab + row * NT;
-        // shift register: when level l is decided, e[k][i] = e_{l-i} of
-        // symbol s0 + k; entries i > l are stale and never read
-        float ex[SYM][NT], ey[SYM][NT];
-        __half2 eh[SYM][NT];
-#pragma unroll
-        for (int i = 0; i < NT; ++i) {
-            const int lz = nt - 1 - i;
-#pragma unroll
-            for (int k = 0; k < SYM; ++k) {
-                const float2 z = lz >= 0 ? sZ[(s0 + k) * NT + lz] : make_float2(0.f, 0.f);
-                if constexpr (F16) {
-                    eh[k][i] = __floats2half2_rn(z.x, z.y);
-                } else {
-                    ex[k][i] = z.x;
-                    ey[k][i] = z.y;
-                }
-            }
-        }
         Lab lab[SYM];
-#pragma unroll
-        for (int k = 0; k < SYM; ++k) lab[k].clear();
         float d[SYM];
+        // A chunk whose rows reach rank 4 or more at a walked level takes the
+        // enumeration of kth_point_slow, an out-of-line call; the others
+        // (most chunks: those rows are ordered first) take rank 3 in closed
+        // form inline, with no call -- and no registers saved around one --
+        // in their loop.  Bucket < 8 marks a row with a rank >= 4 below the
+        // two list-served levels.
+        const bool deep = __any_sync(
+            0xffffffffu, active && (sOrder[row] < 8u || (!use2 && nt >= 2 && trow[nt - 2] > 3)));
+        auto walk = [&](auto deep_tag) {
+            constexpr bool kDeep = decltype(deep_tag)::value;
+            // shift register: when level l is decided, e[k][i] = e_{l-i} of
+            // symbol s0 + k; entries i > l are stale and never read
+            [[maybe_unused]] float2 e2[SYM][NT];
+            [[maybe_unused]] __half2 eh[SYM][NT];
 #pragma unroll
-        for (int k = 0; k < SYM; ++k) d[k] = 0.f;
-        int p_top = 1;
+            for (int i = 0; i < NT; ++i) {
+                const int lz = nt - 1 - i;
+#pragma unroll
+                for (int k = 0; k < SYM; ++k) {
+                    const float2 z = lz >= 0 ? sZ[(s0 + k) * NT + lz] : make_float2(0.f, 0.f);
+                    if constexpr (F16) eh[k][i] = __floats2half2_rn(z.x, z.y);
+                    else e2[k][i] = z;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < SYM; ++k) lab[k].clear();
+#pragma unroll
+            for (int k = 0; k < SYM; ++k) d[k] = 0.f;
+            int p_top = 1;
 #pragma unroll 1
-        for (int l = nt - 1; l >= 0; --l) {
-            const int p = trow[l];
-            float sx[SYM], sy[SYM], dist[SYM];
-            int lb[SYM];
-            if (l >= l_list) {  // list-served levels (warp-uniform branch)
-                const float4 *lst;
-                int stride;
-                if (l == nt - 1) {
-                    p_top = p;
-                    lst = sTop + s0 * kTopList + p - 1;
-                    stride = kTopList;
-                } else {
-                    lst = sL2 + s0 * kList2 + s_off1[p_top] + p - 1;
-                    stride = kList2;
-                }
-#pragma unroll
-                for (int k = 0; k < SYM; ++k) {
-                    const float4 q = lst[k * stride];
-                    sx[k] = q.x;
-                    sy[k] = q.y;
-                    dist[k] = q.z;
-                    lb[k] = __float_as_int(q.w);
-                }
-            } else {
-                const float iv = sInvd[l];
-                int ire[SYM], iim[SYM];
-                float dre[SYM], dim[SYM];
-#pragma unroll
-                for (int k = 0; k < SYM; ++k) {
-                    float bx, by;
-                    if constexpr (F16) {
-                        const float2 f = __half22float2(eh[k][0]);
-                        bx = f.x * iv;
-                        by = f.y * iv;
+            for (int l = nt - 1; l >= 0; --l) {
+                const int p = trow[l];
+                float sx[SYM], sy[SYM], dist[SYM];
+                int lb[SYM];
+                if (l >= l_list) {  // list-served levels (warp-uniform branch)
+                    const float4 *lst;
+                    int stride;
+                    if (l == nt - 1) {
+                        p_top = p;
+                        lst = sTop + s0 * kTopList + p - 1;
+                        stride = kTopList;
                     } else {
-                        bx = ex[k][0] * iv;
-                        by = ey[k][0] * iv;
+                        lst = sL2 + s0 * kList2 + s_off1[p_top] + p - 1;
+                        stride = kList2;
                     }
-                    ire[k] = axis_round<QAM>(bx, dre[k], sx[k]);
-                    iim[k] = axis_round<QAM>(by, dim[k], sy[k]);
-                    if (p == 2) {
-                        // second nearest: the next point along one axis
-                        const int nre = axis_next<QAM>(bx, ire[k]);
-                        const int nim = axis_next<QAM>(by, iim[k]);
-                        float a = bx - axis_pos<QAM>(nre), c = by - axis_pos<QAM>(nim);
-                        const float d_re = a * a + dim[k];  // (nre, iim)
-                        const float d_im = dre[k] + c * c;  // (ire, nim)
-                        bool take_re = d_re < d_im;
-                        if (d_re == d_im) take_re = sLut[nre * 8 + iim[k]] < sLut[ire[k] * 8 + nim];
-                        if (take_re) {
-                            ire[k] = nre;
-                            dre[k] = d_re;
-                            sx[k] = axis_pos<QAM>(nre);
-                        } else {
-                            iim[k] = nim;
-                            dre[k] = d_im;
-                            sy[k] = axis_pos<QAM>(nim);
-                        }
-                        dim[k] = 0.f;
-                    } else if (p > 2) {
-                        int oi, oj;
-                        dre[k] = kth_point_slow<QAM>(bx, by, p, ire[k], iim[k], oi, oj);
-                        dim[k] = 0.f;
-                        ire[k] = oi;
-                        iim[k] = oj;
-                        sx[k] = axis_pos<QAM>(oi);
-                        sy[k] = axis_pos<QAM>(oj);
-                    }
-                    dist[k] = dre[k] + dim[k];
-                    lb[k] = sLut[ire[k] * 8 + iim[k]];
-                }
-            }
-            const float r2 = sR2[l];
 #pragma unroll
-            for (int k = 0; k < SYM; ++k) {
-                d[k] = fmaf(r2, dist[k], d[k]);
-                lab[k].push(lb[k]);
-            }
-            if constexpr (F16) {
-                __half2 sh[SYM], sw[SYM];
+                    for (int k = 0; k < SYM; ++k) {
+                        const float4 q = lst[k * stride];
+                        sx[k] = q.x;
+                        sy[k] = q.y;
+                        dist[k] = q.z;
+                        lb[k] = __float_as_int(q.w);
+                    }
+                } else {
+                    const float iv = sInvd[l];
+                    int ire[SYM], iim[SYM];
+                    float dre[SYM], dim[SYM];
+#pragma unroll
+                    for (int k = 0; k < SYM; ++k) {
+                        float bx, by;
+                        if constexpr (F16) {
+                            const float2 f = __half22float2(eh[k][0]);
+                            bx = f.x * iv;
+                            by = f.y * iv;
+                            ire[k] = axis_round<QAM>(bx, dre[k], sx[k]);
+                            iim[k] = axis_round<QAM>(by, dim[k], sy[k]);
+                        } else {
+                            bx = e2[k][0].x * iv;
+                            by = e2[k][0].y * iv;
+                            ire[k] = axis_round<QAM>(bx, dre[k], sx[k]);
+                            iim[k] = axis_round<QAM>(by, dim[k], sy[k]);
+                        }
+                        if (p == 2) {
+                            // second nearest: the next point along one axis
+                            const int nre = axis_next<QAM>(bx, ire[k]);
+                            const int nim = axis_next<QAM>(by, iim[k]);
+                            float a = bx - axis_pos<QAM>(nre), c = by - axis_pos<QAM>(nim);
+                            const float d_re = a * a + dim[k];  // (nre, iim)
+                            const float d_im = dre[k] + c * c;  // (ire, nim)
+                            bool take_re = d_re < d_im;
+                            if (d_re == d_im) take_re = sLut[nre * 8 + iim[k]] < sLut[ire[k] * 8 + nim];
+                            if (take_re) {
+                                ire[k] = nre;
+                                dre[k] = d_re;
+                                sx[k] = axis_pos<QAM>(nre);
+                            } else {
+                                iim[k] = nim;
+                                dre[k] = d_im;
+                                sy[k] = axis_pos<QAM>(nim);
+                            }
+                            dim[k] = 0.f;
+                        } else if (p > 2) {
+                            int oi, oj;
+                            if constexpr (kDeep)
+                                dre[k] = kth_point_slow<QAM>(bx, by, p, ire[k], iim[k], oi, oj);
+                            else
+                                dre[k] = third_point<QAM>(bx, by, ire[k], iim[k], oi, oj);
+                            dim[k] = 0.f;
+                            ire[k] = oi;
+                            iim[k] = oj;
+                            sx[k] = axis_pos<QAM>(oi);
+                            sy[k] = axis_pos<QAM>(oj);
+                        }
+                        dist[k] = dre[k] + dim[k];
+                        lb[k] = sLut[ire[k] * 8 + iim[k]];
+                    }
+                }
+                const float r2 = sR2[l];
 #pragma unroll
                 for (int k = 0; k < SYM; ++k) {
-                    sh[k] = __floats2half2_rn(sx[k], sy[k]);
-                    sw[k] = __floats2half2_rn(sy[k], sx[k]);
+                    d[k] = fmaf(r2, dist[k], d[k]);
+                    lab[k].push(lb[k]);
                 }
-                cancel_level_h<NT>(l, eh, sRh + l * NT, sh, sw);
-            } else {
-                cancel_level<NT>(l, ex, ey, sRr + l * NT, sx, sy);
+                if constexpr (F16) {
+                    __half2 sh[SYM], sw[SYM];
+#pragma unroll
+                    for (int k = 0; k < SYM; ++k) {
+                        sh[k] = __floats2half2_rn(sx[k], sy[k]);
+                        sw[k] = __floats2half2_rn(sy[k], sx[k]);
+                    }
+                    cancel_level_h<NT>(l, eh, sRh + l * NT, sh, sw);
+                } else {
+                    float2 sv[SYM], q[SYM];
+#pragma unroll
+                    for (int k = 0; k < SYM; ++k) {
+                        sv[k] = make_float2(sx[k], sy[k]);
+                        q[k] = make_float2(sy[k], -sx[k]);
+                    }
+                    cancel_level2<NT>(l, e2, sRp + l * NT, sv, q);
+                }
             }
-        }
+        };
+        if (deep) walk(BoolTag<true>{});
+        else walk(BoolTag<false>{});
 #pragma unroll
         for (int k = 0; k < SYM; ++k)
             warp_reduce_symbol<NT, B>(s0 + k < n_sym, active, row, chunk, chunks, nt, d[k], lab[k],
@@ -1139,7 +1172,7 @@ template <int NT, int QAM, bool F16, int SYM>
 cudaError_t launch_sym(int n_sc, const DetArgs &a, cudaStream_t stream)
 {
     const size_t smem =
-        det_layout(NT, Qam<QAM>::B, a.n_pe, a.n_sym, Labels<NT, Qam<QAM>::B>::WORDS).bytes;
+        det_layout(NT, Qam<QAM>::B, a.n_pe, a.n_sym, Labels<NT, Qam<QAM>::B>::WORDS, F16).bytes;
     {
         cudaError_t e = allow_dynamic_smem(detect_walk_kernel<NT, QAM, F16, SYM>, smem);
         if (e != cudaSuccess) return e;
