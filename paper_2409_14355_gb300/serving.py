@@ -24,7 +24,8 @@ arrival to the completion of its round, against the 0.5 ms slot deadline
 (§III-B).  An RU's channel update never shares the device with a round that
 still reads the RU's previous state: it waits for those rounds to finish,
 and the RU's later slots wait behind it (they may join its round: the
-stages run in order, QR and selection before Q^H y and the walks).
+stages run in order, QR and selection before Q^H y and the walks; a slot
+never joins another round while the update is in flight).
 
 Nothing here does arithmetic of the detector: all of it runs in the CUDA
 kernels behind the C ABI (mpnl.py).
@@ -58,6 +59,8 @@ class RU:
     precision: str = "fp32"   # "fp16": tensor-core Q^H y and FP16-residual walks
     state: dict = field(default_factory=dict)   # Q, R, inv_diag, perm, paths (device)
     busy_rounds: set = field(default_factory=set)
+    update_round: int = -1    # round of the RU's channel update in flight (-1: none)
+    gone: bool = False        # deregistered; state released when its rounds retire
     pool: list = field(default_factory=list)    # free per-slot buffer sets
     H_dev: torch.Tensor | None = None           # device staging of a channel update
 
@@ -182,6 +185,7 @@ class Server:
         self.waiting: collections.deque[Request] = collections.deque()
         self.rounds = [_Round(self, k) for k in range(max_inflight)]
         self.completed: list[Request] = []
+        self.dropped: list[Request] = []
         self.n_rounds = 0
         self.t0 = time.perf_counter()
         self.peak_in_use = 0
@@ -212,8 +216,41 @@ class Server:
     def now(self) -> float:
         return time.perf_counter() - self.t0
 
-    def submit(self, req: Request) -> None:
+    def submit(self, req: Request) -> bool:
+        """Queue a request; a request of an unknown or deregistered RU is
+        dropped (done = -2, kept in `dropped`) and False returned."""
+        ru = self.rus.get(req.ru)
+        if ru is None or ru.gone:
+            req.done = -2.0
+            self.dropped.append(req)
+            return False
         self.waiting.append(req)
+        return True
+
+    def deregister(self, ru_id: int) -> list[Request]:
+        """An RU that disappears (its fronthaul link drops, it powers
+        down): its waiting requests are dropped (done = -2) and returned,
+        later submissions for it are refused, and its device state and
+        buffers are released as soon as no round in flight still uses them
+        (at once if none does).  Its requests already in a round complete
+        normally."""
+        ru = self.rus.get(ru_id)
+        if ru is None:
+            return []
+        ru.gone = True
+        out = [q for q in self.waiting if q.ru == ru_id]
+        self.waiting = collections.deque(q for q in self.waiting if q.ru != ru_id)
+        for q in out:
+            q.done = -2.0
+        self.dropped.extend(out)
+        self._release_if_idle(ru)
+        return out
+
+    def _release_if_idle(self, ru: RU) -> None:
+        if ru.gone and not ru.busy_rounds and ru.ru_id in self.rus:
+            self.state_bytes -= ru.state_bytes() if ru.state else 0
+            ru.state, ru.pool, ru.H_dev = {}, [], None
+            del self.rus[ru.ru_id]
 
     # ---- the loop
     def poll(self) -> int:
@@ -227,6 +264,8 @@ class Server:
                     self.completed.append(q)
                     ru = self.rus[q.ru]
                     ru.busy_rounds.discard(r.round_id)
+                    if ru.update_round == r.round_id:
+                        ru.update_round = -1
                     if q.bufs is not None:
                         if self.keep_results:
                             q.hard = q.bufs.hard_host.clone()
@@ -236,6 +275,10 @@ class Server:
                         ru.pool.append(q.bufs)
                         q.bufs = None
                 self.in_use -= r.bytes
+                for q in r.requests:
+                    ru = self.rus.get(q.ru)
+                    if ru is not None:
+                        self._release_if_idle(ru)
                 r.requests, r.buffers, r.bytes, r.event = [], [], 0, None
                 n += 1
         return n
@@ -267,6 +310,12 @@ class Server:
                 ok = False
             if ok and big and not large_ok:
                 ok = False
+            if ok and q.kind == "slot":
+                # the RU's channel update, if one is in flight in another
+                # round (on another stream), is still rewriting the state this
+                # slot reads: the slot waits until that round has finished
+                # (an update formed into this same round runs its stages first)
+                ok = ru.update_round < 0
             if ok and q.kind == "slot":
                 # a free buffer set of the RU (its earlier slots in this round hold theirs)
                 ok = len(ru.pool) > sum(1 for c in chosen if c.ru == q.ru and c.kind == "slot")
@@ -357,6 +406,8 @@ class Server:
         for q in reqs:
             q.round_id = r.round_id
             self.rus[q.ru].busy_rounds.add(r.round_id)
+            if q.kind == "channel":
+                self.rus[q.ru].update_round = r.round_id
         r.requests, r.bytes = reqs, nbytes
         self.in_use += nbytes
         self.peak_in_use = max(self.peak_in_use, self.in_use)

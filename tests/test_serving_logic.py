@@ -75,6 +75,45 @@ def test_channel_update_waits_for_rounds_reading_the_state():
     assert [q.rid for q in chosen] == [0, 1]       # update, then its slot, same round
 
 
+def test_slot_waits_while_its_rus_update_runs_in_another_round():
+    # round 1 (in flight) holds RU 2's channel update; a later slot of RU 2
+    # must not go into the next round, which runs on another stream and
+    # could read the state while the update still rewrites it
+    s = _server()
+    s.submit(_req(0, 2, "channel"))
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [0]
+    s.rus[2].busy_rounds.add(1)
+    s.rus[2].update_round = 1        # what the launch records for the update
+    for q in (_req(1, 2, "slot"), _req(2, 0, "slot")):
+        s.submit(q)
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [2]
+    assert [q.rid for q in s.waiting] == [1]
+    # the update's round retires: the slot goes into the next round
+    s.rus[2].busy_rounds.clear()
+    s.rus[2].update_round = -1
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [1]
+
+
+def test_poll_clears_the_update_mark_with_its_round():
+    s = _server()
+    ru = s.rus[1]
+    q = _req(0, 1, "channel")
+
+    class Done:
+        def query(self):
+            return True
+
+    r = s.rounds[0]
+    r.requests, r.event, r.round_id, r.bytes = [q], Done(), 5, 0
+    ru.busy_rounds.add(5)
+    ru.update_round = 5
+    assert s.poll() == 1
+    assert ru.update_round == -1 and not ru.busy_rounds
+
+
 def test_slots_wait_for_a_free_buffer_set_of_their_ru():
     s = _server()
     for q in (_req(0, 1, "slot"), _req(1, 1, "slot"), _req(2, 1, "slot"), _req(3, 2, "slot")):
@@ -152,3 +191,36 @@ def test_latency_statistics_per_size_class():
     assert st["large_units"]["miss_rate"] == 1.0 and abs(st["large_units"]["p50_ms"] - 2.0) < 1e-9
     assert abs(st["miss_rate"] - 10 / 15) < 1e-12
     assert abs(st["detections_per_s"] - 15 * 100 / (1.0 + 2e-3)) < 1e-6
+
+
+def test_a_radio_unit_that_disappears_mid_trace():
+    # RU 1 drops out: its waiting requests are dropped and reported, later
+    # submissions for it are refused, the other RUs are served as before,
+    # and its state is released once the round still using it retires
+    s = _server()
+    s.rus[1].state = {"Q": None}
+    s.rus[1].busy_rounds.add(3)                  # a round in flight holds one of its slots
+    for q in (_req(0, 1, "slot"), _req(1, 0, "slot"), _req(2, 1, "channel"), _req(3, 2, "slot")):
+        s.submit(q)
+    dropped = s.deregister(1)
+    assert [q.rid for q in dropped] == [0, 2] and all(q.done == -2.0 for q in dropped)
+    assert 1 in s.rus                            # still read by round 3
+    assert not s.submit(_req(4, 1, "slot")) and s.dropped[-1].rid == 4
+    chosen, _ = s._form()
+    assert [q.rid for q in chosen] == [1, 3]
+
+    class Done:
+        def query(self):
+            return True
+
+    r = s.rounds[0]
+    inflight = _req(9, 1, "slot")
+    r.requests, r.event, r.round_id, r.bytes = [inflight], Done(), 3, 0
+    assert s.poll() == 1
+    assert inflight.done >= 0 and inflight in s.completed   # its last slot completed
+    assert 1 not in s.rus                                   # state released
+    assert not s.submit(_req(5, 1, "slot"))
+    # an RU with nothing in flight is released at once
+    s.deregister(2)
+    assert 2 not in s.rus
+
