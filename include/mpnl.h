@@ -282,15 +282,19 @@ int mpnl_detect(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const float
                 uint8_t *hard, float *llr, float *ped2, void *ws, void *stream);
 
 /* Mixed-precision variant of mpnl_detect (same arguments, same layouts).
- * The walks keep the interference-cancelled residuals e in FP16 (half2) and
- * update them with packed half-precision FMAs; b = e_l / R_ll, the ranking
- * and the PED accumulation stay in FP32.  The final best and runner-up paths
- * are re-checked in FP32 (d = ||z - R s||^2 from their symbols) and the
- * better of the two gives the hard decisions; ped2 holds those two FP32
- * metrics (smaller first).  LLRs come from the FP16-walk PEDs.  Decisions can
- * differ from mpnl_detect's where FP16 rounding changes a ranking; the
- * decision-mismatch rate and BER delta against the FP64 oracle are reported
- * by the tests and the benchmark. */
+ * The walks choose their vectors with the interference-cancelled residuals
+ * e in FP16 (half2, packed half-precision FMAs); b = e_l / R_ll, the ranking
+ * and the PED accumulation of the walk stay in FP32.  Every metric the call
+ * reports is then recomputed in FP32 from the chosen vector -- the re-check
+ * covers every row, not only the best and runner-up: d = ||z - R s||^2
+ * replayed level by level -- so the hard decisions are the argmin of FP32
+ * metrics over the FP16 walks' list, ped2 holds the best and runner-up of
+ * those metrics, and each LLR is a difference of two of them (its sign agrees
+ * with the decided bit).  R and z are scaled per subcarrier by a power of
+ * two before the conversion to FP16, so any input scale is handled exactly.
+ * Decisions can differ from mpnl_detect's where FP16 rounding changes a
+ * ranking and so the list; the decision-mismatch rate and BER delta against
+ * the FP64 oracle are reported by the tests and the benchmark. */
 int mpnl_detect_mixed(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const float *inv_diag,
                       const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
                       uint8_t *hard, float *llr, float *ped2, void *ws, void *stream);

@@ -374,6 +374,17 @@ struct Labels {
         for (int k = WORDS - 1; k > 0; --k) w[k] = __funnelshift_l(w[k - 1], w[k], B);
         w[0] = (w[0] << B) | (uint32_t)lab;
     }
+    // level l for a run-time l, without indexing the register array
+    __device__ __forceinline__ int get_rt(int l) const
+    {
+        const int bit = B * l, k = bit >> 5, off = bit & 31;
+        const uint32_t w0 = w[0];
+        const uint32_t w1 = WORDS > 1 ? w[WORDS > 1 ? 1 : 0] : 0u;
+        const uint32_t w2 = WORDS > 2 ? w[WORDS > 2 ? 2 : 0] : 0u;
+        const uint32_t lo = k == 0 ? w0 : (k == 1 ? w1 : w2);
+        const uint32_t hi = k == 0 ? w1 : (k == 1 ? w2 : 0u);
+        return (int)(__funnelshift_r(lo, hi, off) & ((1u << B) - 1));
+    }
     // level l (a compile-time constant after unrolling)
     __device__ __forceinline__ int get(int l) const
     {
@@ -404,17 +415,18 @@ __host__ __device__ inline int pow2_at_least(int n)
 
 struct DetSmem {
     int off_rc, off_r2, off_invd, off_perm, off_z, off_tab, off_order, off_m, off_best, off_wmin,
-        off_second, off_blab, off_top, off_l2, off_lut, off_rh, off_key2, off_blab2, off_rp,
-        off_scr, bytes;
+        off_second, off_blab, off_top, off_l2, off_lut, off_rh, off_rd, off_pt, off_rp, off_scr,
+        bytes;
 };
 
 // Small per-CTA counters of one subcarrier, kept in the dynamic shared
 // memory rather than as function-scope __shared__ arrays: every instance of
 // the walk body would otherwise add its own static copy to a kernel that
 // calls several instances (the persistent batch kernel), cutting its
-// residency.  Ints: k1[65], off1[65], use2, kmax, hist[256], wsum[warps].
+// residency.  Ints: k1[65], off1[65], use2, kmax, hist[256], wsum[warps],
+// and the largest magnitude of R and z (FP16 instances).
 constexpr int kScrK1 = 0, kScrOff1 = 65, kScrUse2 = 130, kScrKmax = 131, kScrHist = 132,
-              kScrWsum = 388, kScrInts = 388 + kWarps;
+              kScrWsum = 388, kScrMax = 388 + kWarps, kScrInts = 389 + kWarps;
 static_assert(kThreads == 256, "the row sort gives each thread one of the 256 buckets");
 
 // f16: the layout of the mixed-precision instances (half2 columns of R and
@@ -457,15 +469,16 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     o = a16(o + (n_sym + 1) * kList2 * 16);
     s.off_lut = o;  // 2-D label of grid point (ire, iim) at ire * 8 + iim
     o = a16(o + 64);
-    s.off_rh = s.off_key2 = s.off_blab2 = s.off_rp = o;
+    s.off_rh = s.off_rd = s.off_pt = s.off_rp = o;
     if (f16) {
-        // mixed precision: R columns as half2 pairs, runner-up key and labels
+        // mixed precision: R columns as half2 pairs (scaled), the diagonal of
+        // R and the constellation points by label for the FP32 replays
         s.off_rh = o;
         o = a16(o + NT * NT * 8);
-        s.off_key2 = o;
-        o = a16(o + n_sym * chunks * 8);
-        s.off_blab2 = o;
-        o = a16(o + n_sym * chunks * WORDS * 4);
+        s.off_rd = o;
+        o = a16(o + NT * 4);
+        s.off_pt = o;
+        o = a16(o + 64 * 8);
     } else {
         // FP32: each term of the columns of R as {-Re, -Re, Im, Im} for the
         // packed FMAs of the cancellation
@@ -512,9 +525,7 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
                                                    const Labels<NT, B> &lab, int s,
                                                    unsigned long long *sBest, unsigned *sWmin,
                                                    unsigned *sSecond, uint32_t *sBlab,
-                                                   unsigned *sM, bool want_llr,
-                                                   unsigned long long *sKey2 = nullptr,
-                                                   uint32_t *sBlab2 = nullptr)
+                                                   unsigned *sM, bool want_llr)
 {
     using Lab = Labels<NT, B>;
     constexpr int WORDS = Lab::WORDS;
@@ -542,18 +553,6 @@ __device__ __forceinline__ void warp_reduce_symbol(bool valid, bool active, int 
     Lab bl;
 #pragma unroll
     for (int k = 0; k < WORDS; ++k) bl.w[k] = __shfl_sync(FULL, lab.w[k], blane);
-    if (sKey2 != nullptr) {
-        // the warp's runner-up row (key and labels), for the FP32 re-check
-        const int rlane = (int)(runner & 31u);
-        uint32_t rw[WORDS];
-#pragma unroll
-        for (int k = 0; k < WORDS; ++k) rw[k] = __shfl_sync(FULL, lab.w[k], rlane);
-        if (valid && lane == 0) {
-            sKey2[s * chunks + chunk] = runner;
-#pragma unroll
-            for (int k = 0; k < WORDS; ++k) sBlab2[(s * chunks + chunk) * WORDS + k] = rw[k];
-        }
-    }
     if (!valid) return;  // (warp-uniform) second symbol slot beyond n_sym
     if (lane == 0) {
         atomicMin(&sBest[s], best);
@@ -665,10 +664,67 @@ __device__ __forceinline__ void cancel_level2(int l, float2 (&e)[SYM][NT], const
     }
 }
 
-template <bool V>
-struct BoolTag {
-    static constexpr bool value = V;
+template <int V>
+struct IntTag {
+    static constexpr int value = V;
 };
+
+// FP32 replay of a walk's vector x (its labels): the metric
+// ||z - R x||^2, accumulated level by level in the walk's order as
+// |e_l - R_ll x_l|^2 with e_l = z_l - sum_{j>l} R_lj x_j formed in FP32 by
+// the shift-register cancellation.  The mixed-precision walks choose their
+// vectors with FP16 residuals; every metric they report comes from here.
+// z: the symbol's staged z; col: columns of R bottom-up as in sRr; rd: R_ll;
+// pt: constellation points by label.
+template <int NT, int B>
+__device__ __forceinline__ float replay_metric(const float2 *z, const float2 *col, const float *rd,
+                                               const float2 *pt, int nt, const Labels<NT, B> &lab)
+{
+    float ex[NT], ey[NT];
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        const int lz = nt - 1 - i;
+        const float2 v = lz >= 0 ? z[lz] : make_float2(0.f, 0.f);
+        ex[i] = v.x;
+        ey[i] = v.y;
+    }
+    float m = 0.f;
+#pragma unroll 1
+    for (int l = nt - 1; l >= 0; --l) {
+        const float2 x = pt[lab.get_rt(l)];
+        const float r = rd[l];
+        const float dx = fmaf(-r, x.x, ex[0]), dy = fmaf(-r, x.y, ey[0]);
+        m = fmaf(dx, dx, fmaf(dy, dy, m));
+        // e'[i] = e[i+1] - R_{l-1-i, l} x, width grouped by four levels
+        const float4 *c4 = reinterpret_cast<const float4 *>(col + l * NT);
+        auto shift = [&](auto wtag) {
+            constexpr int W = decltype(wtag)::value;
+#pragma unroll
+            for (int i2 = 0; i2 < (W + 1) / 2; ++i2) {
+                const float4 rr = c4[i2];
+                const int i = 2 * i2;
+                ex[i] = fmaf(-rr.x, x.x, fmaf(rr.y, x.y, ex[i + 1]));
+                ey[i] = fmaf(-rr.x, x.y, fmaf(-rr.y, x.x, ey[i + 1]));
+                if (i + 1 < W) {
+                    ex[i + 1] = fmaf(-rr.z, x.x, fmaf(rr.w, x.y, ex[i + 2]));
+                    ey[i + 1] = fmaf(-rr.z, x.y, fmaf(-rr.w, x.x, ey[i + 2]));
+                }
+            }
+        };
+        if constexpr (NT == 16) {
+            if (l > 11) shift(IntTag<15>{});
+            else if (l > 7) shift(IntTag<11>{});
+            else if (l > 3) shift(IntTag<7>{});
+            else if (l > 0) shift(IntTag<3>{});
+        } else if constexpr (NT == 8) {
+            if (l > 3) shift(IntTag<7>{});
+            else if (l > 0) shift(IntTag<3>{});
+        } else {
+            if (l > 0) shift(IntTag<3>{});
+        }
+    }
+    return m;
+}
 
 // One subcarrier of a slot, by one CTA of kThreads threads.
 // F16: the interference-cancelled residuals e are kept as half2 (re, im) and
@@ -720,8 +776,8 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     uint8_t *sLut = smem + S.off_lut;
     uint2 *sRh = reinterpret_cast<uint2 *>(smem + S.off_rh);  // sRr as {(-Re,-Re), (Im,-Im)} half2
     float4 *sRp = reinterpret_cast<float4 *>(smem + S.off_rp);  // sRr as {-Re, -Re, Im, Im}
-    unsigned long long *sKey2 = reinterpret_cast<unsigned long long *>(smem + S.off_key2);
-    uint32_t *sBlab2 = reinterpret_cast<uint32_t *>(smem + S.off_blab2);
+    float *sRd = reinterpret_cast<float *>(smem + S.off_rd);    // R_ll (FP16 replays)
+    float2 *sPt = reinterpret_cast<float2 *>(smem + S.off_pt);  // point of each label
     int &s_kmax = sScr[kScrKmax];
 
     const int tid = threadIdx.x;
@@ -730,6 +786,35 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     // ---- stage the subcarrier
     const int P = nt * (nt + 1) / 2;
     const float2 *gR = Rp + (size_t)sc * P;
+    // FP16 residuals: the subcarrier's R and z are scaled by the power of two
+    // 2^-x that brings their largest component into [0.5, 1) -- exact, and
+    // within FP16's range (+-65504, subnormal below 2^-14) for any caller
+    // scale; b = e / R_ll multiplies the scale back (1/R_ll times 2^x).
+    [[maybe_unused]] float hscale = 1.f, hunscale = 1.f;
+    if constexpr (F16) {
+        unsigned mx = 0u;
+        for (int k = tid; k < P; k += kThreads) {
+            const float2 v = gR[k];
+            mx = max(mx, max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))));
+        }
+        for (int k = tid; k < n_sym * nt; k += kThreads) {
+            const float2 v = Z[(size_t)sc * n_sym * nt + k];
+            mx = max(mx, max(__float_as_uint(fabsf(v.x)), __float_as_uint(fabsf(v.y))));
+        }
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (tid == 0) sScr[kScrMax] = 0;
+        __syncthreads();
+        if (lane == 0) atomicMax(reinterpret_cast<unsigned *>(sScr + kScrMax), mx);
+        __syncthreads();
+        const float m = __uint_as_float((unsigned)sScr[kScrMax]);
+        if (m > 0.f && m < INFINITY) {  // finite and nonzero (NaN bits compare above inf)
+            int x;
+            frexpf(m, &x);
+            x = min(max(x, -100), 100);
+            hscale = ldexpf(1.f, -x);
+            hunscale = ldexpf(1.f, x);
+        }
+    }
     for (int k = tid; k < NT * NT; k += kThreads) {
         const int l = k / NT, i = k - l * NT;
         float2 v = make_float2(0.f, 0.f);  // entries i >= l feed only stale registers
@@ -740,7 +825,8 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
         sRr[k] = v;
         if constexpr (!F16) sRp[k] = make_float4(-v.x, -v.x, v.y, v.y);
         if constexpr (F16) {
-            const __half2 a = __floats2half2_rn(-v.x, -v.x), b = __floats2half2_rn(v.y, -v.y);
+            const float rx = v.x * hscale, ry = v.y * hscale;
+            const __half2 a = __floats2half2_rn(-rx, -rx), b = __floats2half2_rn(ry, -ry);
             sRh[k] = make_uint2(*reinterpret_cast<const unsigned *>(&a),
                                 *reinterpret_cast<const unsigned *>(&b));
         }
@@ -748,6 +834,10 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     for (int l = tid; l < nt; l += kThreads) {
         const float2 v = gR[l * nt - (l * (l - 1)) / 2];
         sR2[l] = v.x * v.x;
+        if constexpr (F16) sRd[l] = v.x;
+    }
+    if constexpr (F16) {
+        for (int k = tid; k < QAM; k += kThreads) sPt[k] = label_point<QAM>(k);
     }
     for (int k = tid; k < NT; k += kThreads) {
         if (k < nt) {
@@ -911,16 +1001,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
         const uint8_t *trow = sTab + row * NT;
         Lab lab[SYM];
         float d[SYM];
-        // A chunk whose rows reach rank 4 or more at a walked level takes the
-        // enumeration of kth_point_slow, an out-of-line call; the others
-        // (most chunks: those rows are ordered first) take rank 3 in closed
-        // form inline, with no call -- and no registers saved around one --
-        // in their loop.  Bucket < 8 marks a row with a rank >= 4 below the
-        // two list-served levels.
-        const bool deep = __any_sync(
-            0xffffffffu, active && (sOrder[row] < 8u || (!use2 && nt >= 2 && trow[nt - 2] > 3)));
-        auto walk = [&](auto deep_tag) {
-            constexpr bool kDeep = decltype(deep_tag)::value;
+        {
             // shift register: when level l is decided, e[k][i] = e_{l-i} of
             // symbol s0 + k; entries i > l are stale and never read
             [[maybe_unused]] float2 e2[SYM][NT];
@@ -931,7 +1012,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
 #pragma unroll
                 for (int k = 0; k < SYM; ++k) {
                     const float2 z = lz >= 0 ? sZ[(s0 + k) * NT + lz] : make_float2(0.f, 0.f);
-                    if constexpr (F16) eh[k][i] = __floats2half2_rn(z.x, z.y);
+                    if constexpr (F16) eh[k][i] = __floats2half2_rn(z.x * hscale, z.y * hscale);
                     else e2[k][i] = z;
                 }
             }
@@ -973,8 +1054,8 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
                         float bx, by;
                         if constexpr (F16) {
                             const float2 f = __half22float2(eh[k][0]);
-                            bx = f.x * iv;
-                            by = f.y * iv;
+                            bx = f.x * (iv * hunscale);
+                            by = f.y * (iv * hunscale);
                             ire[k] = axis_round<QAM>(bx, dre[k], sx[k]);
                             iim[k] = axis_round<QAM>(by, dim[k], sy[k]);
                         } else {
@@ -1004,10 +1085,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
                             dim[k] = 0.f;
                         } else if (p > 2) {
                             int oi, oj;
-                            if constexpr (kDeep)
-                                dre[k] = kth_point_slow<QAM>(bx, by, p, ire[k], iim[k], oi, oj);
-                            else
-                                dre[k] = third_point<QAM>(bx, by, ire[k], iim[k], oi, oj);
+                            dre[k] = kth_point_slow<QAM>(bx, by, p, ire[k], iim[k], oi, oj);
                             dim[k] = 0.f;
                             ire[k] = oi;
                             iim[k] = oj;
@@ -1042,14 +1120,17 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
                     cancel_level2<NT>(l, e2, sRp + l * NT, sv, q);
                 }
             }
-        };
-        if (deep) walk(BoolTag<true>{});
-        else walk(BoolTag<false>{});
+            if constexpr (F16) {
+                // every reported metric is the FP32 metric of the walk's vector
+#pragma unroll
+                for (int k = 0; k < SYM; ++k)
+                    d[k] = replay_metric<NT, B>(sZ + (s0 + k) * NT, sRr, sRd, sPt, nt, lab[k]);
+            }
+        }
 #pragma unroll
         for (int k = 0; k < SYM; ++k)
             warp_reduce_symbol<NT, B>(s0 + k < n_sym, active, row, chunk, chunks, nt, d[k], lab[k],
-                                      s0 + k, sBest, sWmin, sSecond, sBlab, sM, llr != nullptr,
-                                      F16 ? sKey2 : nullptr, sBlab2);
+                                      s0 + k, sBest, sWmin, sSecond, sBlab, sM, llr != nullptr);
     }
     __syncthreads();
 
@@ -1060,68 +1141,6 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
         const unsigned bd = (unsigned)(key >> 32);
         int bc = (int)((key & 0xffffu) >> 5);  // chunk of the best row's sorted position
         if (bc >= chunks) bc = 0;
-        if constexpr (F16) {
-            // runner-up: the best chunk's second row or another chunk's best
-            unsigned long long rk = ~0ull;
-            int rsrc = -1;  // >= 0: sBlab of chunk rsrc; -1: sBlab2 of chunk bc
-            for (int c = lane; c < chunks; c += 32) {
-                const unsigned long long kc = c == bc ? sKey2[s * chunks + c]
-                                                      : ((unsigned long long)sWmin[s * chunks + c] << 32);
-                if (kc < rk) {
-                    rk = kc;
-                    rsrc = c == bc ? -1 : c;
-                }
-            }
-            // warp min of (rk, rsrc): chunk keys of other chunks only carry the PED
-            // (their rows are unique per chunk), ties -> lower chunk
-            unsigned long long best_rk = rk;
-            int best_src = rsrc;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, best_rk, o);
-                const int s2 = __shfl_xor_sync(0xffffffffu, best_src, o);
-                if (k2 < best_rk || (k2 == best_rk && s2 < best_src)) {
-                    best_rk = k2;
-                    best_src = s2;
-                }
-            }
-            // FP32 metrics ||z - R s||^2 of both paths: lane l owns row l of R
-            const uint32_t *w1 = sBlab + (s * chunks + bc) * WORDS;
-            const uint32_t *w2 = best_src < 0 ? sBlab2 + (s * chunks + bc) * WORDS
-                                              : sBlab + (s * chunks + best_src) * WORDS;
-            const bool have2 = best_rk != ~0ull;
-            float m1 = 0.f, m2 = 0.f;
-            if (lane < nt) {
-                const float2 z = sZ[s * NT + lane];
-                float t1x = z.x, t1y = z.y, t2x = z.x, t2y = z.y;
-                for (int j = lane; j < nt; ++j) {
-                    const float2 r =
-                        j == lane ? make_float2(sqrtf(sR2[j]), 0.f) : sRr[j * NT + (j - 1 - lane)];
-                    const int lb1 = label_at<B>(w1, j);
-                    const int lb2 = label_at<B>(w2, j);
-                    const float2 p1 = label_point<QAM>(lb1), p2 = label_point<QAM>(lb2);
-                    t1x -= r.x * p1.x - r.y * p1.y;
-                    t1y -= r.x * p1.y + r.y * p1.x;
-                    t2x -= r.x * p2.x - r.y * p2.y;
-                    t2y -= r.x * p2.y + r.y * p2.x;
-                }
-                m1 = t1x * t1x + t1y * t1y;
-                m2 = t2x * t2x + t2y * t2y;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                m1 += __shfl_xor_sync(0xffffffffu, m1, o);
-                m2 += __shfl_xor_sync(0xffffffffu, m2, o);
-            }
-            if (!have2) m2 = INFINITY;
-            const bool swap = have2 && m2 < m1;
-            const uint32_t *wb = swap ? w2 : w1;
-            if (lane < nt) hard[det * nt + sPerm[lane]] = (uint8_t)label_at<B>(wb, lane);
-            if (ped2 != nullptr && lane == 0) {
-                ped2[det * 2] = fminf(m1, m2);
-                ped2[det * 2 + 1] = fmaxf(m1, m2);
-            }
-        } else {
         if (lane < nt)
             hard[det * nt + sPerm[lane]] = (uint8_t)label_at<B>(sBlab + (s * chunks + bc) * WORDS, lane);
         if (ped2 != nullptr) {
@@ -1133,7 +1152,6 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
                 ped2[det * 2] = __uint_as_float(bd);
                 ped2[det * 2 + 1] = __uint_as_float(sec);
             }
-        }
         }
         if (llr != nullptr) {
             for (int slot = lane; slot < nt * B; slot += 32) {

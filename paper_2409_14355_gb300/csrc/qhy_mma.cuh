@@ -70,14 +70,35 @@ __device__ __forceinline__ void qhy_mma_warp(int sc, int n_sym, int nr, int nt,
     float *Cs = reinterpret_cast<float *>(base + S.off_c);
     const int MP = S.MP, KP = S.KP, NP = S.NP;
 
-    // A[m][k]: k < nr the real part of y_k, nr <= k < 2nr the imaginary part
+    // y is scaled by the power of two 2^-x that brings its largest component
+    // into [0.5, 1) (exact; FP16's range is +-65504 with subnormals below
+    // 2^-14, a caller's y may sit at any scale) and z by 2^x at the end.
+    // Q needs none: its columns are orthonormal, every entry within 1.
     const float2 *y = Y + (size_t)sc * n_sym * nr;
+    unsigned mx = 0u;
+    for (int e = lane; e < n_sym * nr; e += 32) {
+        const float2 t = y[e];
+        mx = max(mx, max(__float_as_uint(fabsf(t.x)), __float_as_uint(fabsf(t.y))));
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    float ys = 1.f, yu = 1.f;
+    {
+        const float m = __uint_as_float(mx);
+        if (m > 0.f && m < INFINITY) {  // finite and nonzero (NaN bits compare above inf)
+            int x;
+            frexpf(m, &x);
+            x = min(max(x, -100), 100);
+            ys = ldexpf(1.f, -x);
+            yu = ldexpf(1.f, x);
+        }
+    }
+    // A[m][k]: k < nr the real part of y_k, nr <= k < 2nr the imaginary part
     for (int e = lane; e < MP * KP; e += 32) {
         const int m = e / KP, k = e - m * KP;
         float v = 0.f;
         if (m < n_sym && k < 2 * nr) {
             const float2 t = y[(size_t)m * nr + (k < nr ? k : k - nr)];
-            v = k < nr ? t.x : t.y;
+            v = (k < nr ? t.x : t.y) * ys;
         }
         As[e] = __float2half_rn(v);
     }
@@ -121,7 +142,7 @@ __device__ __forceinline__ void qhy_mma_warp(int sc, int n_sym, int nr, int nt,
     float2 *z = Z + (size_t)sc * n_sym * nt;
     for (int e = lane; e < n_sym * nt; e += 32) {
         const int m = e / nt, j = e - m * nt;
-        z[e] = make_float2(Cs[m * NP + j], Cs[m * NP + nt + j]);
+        z[e] = make_float2(Cs[m * NP + j] * yu, Cs[m * NP + nt + j] * yu);
     }
     __syncwarp();  // the region may be reused for the warp's next subcarrier
 }

@@ -49,3 +49,20 @@ def test_tensor_core_qhy_within_fp16_rounding(dev, nr, nt, n_sym, n_sc, mmse):
     # and it is FP16-close to the FP32 kernel, not equal to it
     d = (Z16 - Z32).abs().max().item()
     assert d > 0 and d < 1e-2 * Z32.abs().max().item()
+
+
+def test_tensor_core_qhy_does_not_depend_on_the_scale_of_y(dev):
+    # y at ADC-like scales (2^12) or tiny ones (2^-12) would overflow or go
+    # subnormal in FP16; the kernel normalises each subcarrier's y by a power
+    # of two, so z follows the scale exactly
+    from paper_2409_14355_gb300 import mpnl
+    sl = inputs.make_slot(16, 16, 64, 40, 14, 21.0, "iid", 0.3, 77)
+    H = torch.from_numpy(sl.H).to(dev)
+    Y = torch.from_numpy(sl.Y).to(dev)
+    Q, _, _, _ = mpnl.factor(H)
+    z0 = mpnl.qhy(Q, Y, precision="fp16")
+    for k in (12, -12, 20):
+        zk = mpnl.qhy(Q, Y * (2.0 ** k), precision="fp16")
+        torch.cuda.synchronize()
+        assert torch.equal(zk, z0 * (2.0 ** k)), k
+        assert torch.isfinite(torch.view_as_real(zk)).all(), k
