@@ -144,8 +144,10 @@ int mpnl_qhy(mpnl_ctx *ctx, const mpnl_dims *dims, const void *Q, const void *Y,
  * accumulation (the Q^H y of the mixed-precision path): per subcarrier the
  * symbols form one small real GEMM [Re y | Im y] [[Re Q, -Im Q]; [Im Q,
  * Re Q]] = [Re z | Im z] (mma.sync m16n8k16).  Q and y are rounded to FP16
- * (11-bit significand, range +-65504): each z_j is off by about 2^-11
- * sum_i |Q_ij| |y_i|.  Arguments and errors as mpnl_qhy. */
+ * (11-bit significand) after each subcarrier's y is scaled by the power of
+ * two that brings its largest component into [0.5, 1) (undone on z, so any
+ * input scale is exact): each z_j is off by about 2^-11 sum_i |Q_ij| |y_i|.
+ * Arguments and errors as mpnl_qhy. */
 int mpnl_qhy_mixed(mpnl_ctx *ctx, const mpnl_dims *dims, const void *Q, const void *Y, void *Z,
                    void *ws, void *stream);
 
