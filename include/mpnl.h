@@ -352,6 +352,9 @@ typedef struct {
 #define MPNL_ITEM_LINEAR_MMSE 2  /* also run the linear MMSE baseline */
 #define MPNL_ITEM_FP16 4         /* the mixed-precision path: walks as mpnl_detect_mixed and,
                                     in the Q^H y stage, z as mpnl_qhy_mixed */
+#define MPNL_ITEM_REFINE_QR 8    /* right after the QR stage, the FP64 re-factorisation of
+                                    mpnl_refine_qr with cond_threshold 1e3 (R, 1/R_ll, perm,
+                                    Q if given, and z where the QR stage formed it) */
 
 /* Stages run in the order QR, selection, Q^H y, walks, MMSE.  A unit whose
  * stages include MPNL_STAGE_QHY gets z from its stored Q; otherwise, if its

@@ -142,10 +142,15 @@ int begin(mpnl_ctx *ctx)
 }  // namespace
 
 // Stage slots of a batch, in execution order.
-enum BatchStage { kBPre, kBSel, kBQhy, kBDet, kBMmse, kBStages };
+// The FP64 refinement (units with MPNL_ITEM_REFINE_QR) runs with the QR stage.
+enum BatchStage { kBPre, kBRef, kBSel, kBQhy, kBDet, kBMmse, kBStages };
 constexpr int kGraphSlots = 2 * (MPNL_STAGES_ALL + 1);
-static const int kStageBit[kBStages] = {MPNL_STAGE_PREPROCESS, MPNL_STAGE_SELECT, MPNL_STAGE_QHY,
-                                        MPNL_STAGE_DETECT, MPNL_STAGE_MMSE};
+static const int kStageBit[kBStages] = {MPNL_STAGE_PREPROCESS, MPNL_STAGE_PREPROCESS,
+                                        MPNL_STAGE_SELECT,     MPNL_STAGE_QHY,
+                                        MPNL_STAGE_DETECT,     MPNL_STAGE_MMSE};
+// the condition-estimate threshold of the batch refinement (the one the
+// mixed-precision path is stated for)
+constexpr float kBatchRefineThreshold = 1e3f;
 
 struct mpnl_batch {
     int device;
@@ -159,7 +164,7 @@ struct mpnl_batch {
     int *d_start;              // kBStages x (capacity + 1) prefix sums of n_sc per stage
     int *d_counters;           // one per stage
     int stage_units[kBStages];
-    int pre_warp_bytes, sel_group_bytes, qhy_warp_bytes, mmse_warp_bytes;
+    int pre_warp_bytes, ref_warp_bytes, sel_group_bytes, qhy_warp_bytes, mmse_warp_bytes;
     size_t det_smem;
     int sel_warps, det_ctas;
     int sms;
@@ -187,7 +192,8 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
     cudaDeviceGetAttribute(&dev_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device);
     std::vector<mpnl::BatchItem> host(n_items);
     std::vector<int> order(n_items), stg(n_items);
-    size_t pre = 16, sel = 16, qhy = 16, mm = 16, det = 16;
+    size_t pre = 16, ref = 16, sel = 16, qhy = 16, mm = 16, det = 16;
+    std::vector<char> refine(n_items);
     for (int i = 0; i < n_items; ++i) {
         const mpnl_batch_item &it = items[i];
         const mpnl_dims *d = &it.dims;
@@ -199,8 +205,8 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
         const bool carry_y = pre_on && (st_bits & MPNL_STAGE_DETECT) && !qhy_on;
         int st = check_dims(ctx, d, true, mqr ? kNrAugmented : kNrTall);
         if (st == MPNL_OK) st = check_sigma2(ctx, it.sigma2);
-        if (st == MPNL_OK &&
-            (it.flags & ~(MPNL_ITEM_MMSE_QR | MPNL_ITEM_LINEAR_MMSE | MPNL_ITEM_FP16)))
+        if (st == MPNL_OK && (it.flags & ~(MPNL_ITEM_MMSE_QR | MPNL_ITEM_LINEAR_MMSE |
+                                           MPNL_ITEM_FP16 | MPNL_ITEM_REFINE_QR)))
             st = fail(ctx, MPNL_ERR_INVALID_ARG, "unknown flags 0x%x", it.flags);
         if (st == MPNL_OK && (st_bits & ~(MPNL_STAGES_ALL)))
             st = fail(ctx, MPNL_ERR_INVALID_ARG, "unknown stage bits 0x%x", st_bits);
@@ -255,6 +261,8 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
         h.mmse = (st_bits & MPNL_STAGE_MMSE) ? 1 : 0;
         h.f16 = (it.flags & MPNL_ITEM_FP16) ? 1 : 0;
         h.factor_sym = carry_y ? d->n_sym : 0;
+        refine[i] = pre_on && (it.flags & MPNL_ITEM_REFINE_QR) ? 1 : 0;
+        h.refine_threshold = refine[i] ? kBatchRefineThreshold : 0.f;
         h.Q = (float2 *)it.Q;
         h.H = (const float2 *)it.H;
         h.Y = (const float2 *)it.Y;
@@ -271,6 +279,7 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
         if (pre_on) {
             const int rows = mqr ? d->nr + d->nt : d->nr;
             pre = std::max(pre, mpnl::preprocess_warp_bytes(h.factor_sym, rows, d->nt));
+            if (refine[i]) ref = std::max(ref, mpnl::refine_warp_bytes(rows, d->nt, h.factor_sym));
         }
         if (st_bits & MPNL_STAGE_SELECT) sel = std::max(sel, mpnl::select_group_bytes(d->n_pe));
         if (qhy_on) qhy = std::max(qhy, mpnl::qhy_warp_bytes(d->n_sym, d->nr, d->nt));
@@ -287,6 +296,7 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
     int det_ctas = ctx->tuning.persistent_ctas_per_sm ? ctx->tuning.persistent_ctas_per_sm : 3;
     while (det_ctas > 1 && (size_t)det_ctas * det > (size_t)dev_smem) --det_ctas;
     if (det > (size_t)dev_smem || pre * 4 > (size_t)dev_smem || mm * 4 > (size_t)dev_smem ||
+        ref * 2 > (size_t)dev_smem ||
         qhy * 4 > (size_t)dev_smem || sel * (4 / sel_warps) > (size_t)dev_smem)
         return fail(ctx, MPNL_ERR_UNSUPPORTED, "a unit needs more shared memory than one SM has");
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
@@ -302,8 +312,10 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
     for (int k = 0; k < n_items; ++k) {
         sorted[k] = host[order[k]];
         const int bits = stg[order[k]];
-        for (int q = 0; q < kBStages; ++q)
-            start[q * cap1 + k + 1] = start[q * cap1 + k] + ((bits & kStageBit[q]) ? sorted[k].n_sc : 0);
+        for (int q = 0; q < kBStages; ++q) {
+            const bool in = (bits & kStageBit[q]) && (q != kBRef || refine[order[k]]);
+            start[q * cap1 + k + 1] = start[q * cap1 + k] + (in ? sorted[k].n_sc : 0);
+        }
     }
     for (int q = 0; q < kBStages; ++q) {
         b->stage_units[q] = start[q * cap1 + n_items];
@@ -313,6 +325,7 @@ int fill_batch(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_batch_item *items, int n
     b->dirty = true;  // uploaded by the next run, on its stream
     b->n_items = n_items;
     b->pre_warp_bytes = (int)pre;
+    b->ref_warp_bytes = (int)ref;
     b->sel_group_bytes = (int)sel;
     b->qhy_warp_bytes = (int)qhy;
     b->mmse_warp_bytes = (int)mm;
@@ -359,6 +372,11 @@ int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st, boo
         e = mpnl::launch_preprocess_batch(b->d_items, start[kBPre], n, b->d_counters + kBPre,
                                           b->pre_warp_bytes, workers, st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch preprocess launch", e);
+    }
+    if ((stages & MPNL_STAGE_PREPROCESS) && b->stage_units[kBRef]) {
+        e = mpnl::launch_refine_batch(b->d_items, start[kBRef], n, b->d_counters + kBRef,
+                                      b->ref_warp_bytes, workers, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "batch refine launch", e);
     }
     if ((stages & MPNL_STAGE_SELECT) && b->stage_units[kBSel]) {
         e = mpnl::launch_select_batch(b->d_items, start[kBSel], n, b->d_counters + kBSel,

@@ -111,6 +111,7 @@ struct BatchItem {
     int mmse;             // also run the linear MMSE baseline
     int f16;              // walks with FP16 residuals (mpnl_detect_mixed's arithmetic)
     int factor_sym;       // symbols the sorted-QR stage carries along (n_sym or 0)
+    float refine_threshold;  // FP64 re-factorisation stage: max R_ll / min R_ll threshold
     float2 *Q;            // antenna rows of Q (nullable; required by the Q^H y stage)
     const float2 *H, *Y;
     float2 *R;
@@ -152,6 +153,9 @@ cudaError_t launch_select_batch(const BatchItem *items, const int *start, int n_
 cudaError_t launch_detect_batch(const BatchItem *items, const int *start, int n_items,
                                 int *counter, unsigned *status, size_t smem, int grid,
                                 cudaStream_t stream);
+size_t refine_warp_bytes(int rows, int nt, int n_sym);
+cudaError_t launch_refine_batch(const BatchItem *items, const int *start, int n_items,
+                                int *counter, int warp_bytes, int grid, cudaStream_t stream);
 size_t mmse_warp_bytes(int n_sym, int nr, int nt);
 cudaError_t launch_mmse_batch(const BatchItem *items, const int *start, int n_items,
                               int *counter, int warp_bytes, int grid, cudaStream_t stream);

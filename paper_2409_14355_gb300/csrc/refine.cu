@@ -35,17 +35,18 @@ __host__ __device__ inline size_t ref_warp_bytes(int rows, int nt, int n_sym)
     return (b + 15) & ~(size_t)15;
 }
 
-__global__ void __launch_bounds__(kRefWarps * 32)
-refine_kernel(int n_sc, int n_sym, int nr, int nt, double sigma, float threshold,
-              const float2 *__restrict__ H, const float2 *__restrict__ Y, float2 *__restrict__ Rp,
-              float *__restrict__ inv_diag, uint8_t *__restrict__ perm_out,
-              float2 *__restrict__ Z, float2 *__restrict__ Qout, int *__restrict__ n_refined,
-              int warp_bytes)
+// One subcarrier by one warp, in its shared-memory region `base` (at least
+// ref_warp_bytes(rows, nt, n_sym)); Y and Z NULL (n_sym 0) when z is not
+// formed here, Qout and n_refined nullable.
+__device__ __forceinline__ void refine_warp(int sc, int n_sym, int nr, int nt, double sigma,
+                                            float threshold, const float2 *__restrict__ H,
+                                            const float2 *__restrict__ Y, float2 *__restrict__ Rp,
+                                            float *__restrict__ inv_diag,
+                                            uint8_t *__restrict__ perm_out,
+                                            float2 *__restrict__ Z, float2 *__restrict__ Qout,
+                                            int *__restrict__ n_refined, unsigned char *base)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int sc = blockIdx.x * kRefWarps + warp;
-    if (sc >= n_sc) return;  // warp-local work only
+    const int lane = threadIdx.x & 31;
     const int P = nt * (nt + 1) / 2;
     float2 *gR = Rp + (size_t)sc * P;
 
@@ -68,7 +69,6 @@ refine_kernel(int n_sc, int n_sym, int nr, int nt, double sigma, float threshold
 
     const int rows = sigma > 0.0 ? nr + nt : nr;
     const int cols = ref_cols(nt, n_sym);
-    unsigned char *base = smem_raw + (size_t)warp * warp_bytes;
     double2 *sM = reinterpret_cast<double2 *>(base);  // [rows][cols]
     double2 *sQ = sM + (size_t)rows * cols;
     double2 *sRt = sQ + rows;                          // [i][user column]
@@ -179,7 +179,61 @@ refine_kernel(int n_sc, int n_sym, int nr, int nt, double sigma, float threshold
     }
 }
 
+__global__ void __launch_bounds__(kRefWarps * 32)
+refine_kernel(int n_sc, int n_sym, int nr, int nt, double sigma, float threshold,
+              const float2 *__restrict__ H, const float2 *__restrict__ Y, float2 *__restrict__ Rp,
+              float *__restrict__ inv_diag, uint8_t *__restrict__ perm_out,
+              float2 *__restrict__ Z, float2 *__restrict__ Qout, int *__restrict__ n_refined,
+              int warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5;
+    const int sc = blockIdx.x * kRefWarps + warp;
+    if (sc >= n_sc) return;  // warp-local work only
+    refine_warp(sc, n_sym, nr, nt, sigma, threshold, H, Y, Rp, inv_diag, perm_out, Z, Qout,
+                n_refined, smem_raw + (size_t)warp * warp_bytes);
+}
+
+// The refinement stage of a batch (units with MPNL_ITEM_REFINE_QR, right
+// after their sorted QR): warps take (unit, subcarrier) items from a global
+// counter; z is redone only where the QR stage formed it.
+__global__ void __launch_bounds__(kRefWarps * 32)
+refine_batch_kernel(const BatchItem *__restrict__ items, const int *__restrict__ start,
+                    int n_items, int *__restrict__ counter, int warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *base = smem_raw + (size_t)warp * warp_bytes;
+    const int total = start[n_items];
+    for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(counter, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= total) break;
+        const int i = find_item(start, n_items, w);
+        const BatchItem &it = items[i];
+        const bool z = it.factor_sym > 0;
+        refine_warp(w - start[i], z ? it.factor_sym : 0, it.nr, it.nt, (double)it.sigma,
+                    it.refine_threshold, it.H, z ? it.Y : nullptr, it.R, it.inv_diag, it.perm,
+                    z ? it.Z : nullptr, it.Q, nullptr, base);
+        __syncwarp();  // the region is reused for the warp's next item
+    }
+}
+
 }  // namespace
+
+size_t refine_warp_bytes(int rows, int nt, int n_sym) { return ref_warp_bytes(rows, nt, n_sym); }
+
+cudaError_t launch_refine_batch(const BatchItem *items, const int *start, int n_items,
+                                int *counter, int warp_bytes, int grid, cudaStream_t stream)
+{
+    const size_t smem = (size_t)warp_bytes * kRefWarps;
+    cudaError_t e = allow_dynamic_smem(refine_batch_kernel, smem);
+    if (e != cudaSuccess) return e;
+    refine_batch_kernel<<<grid, kRefWarps * 32, smem, stream>>>(items, start, n_items, counter,
+                                                                 warp_bytes);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_refine(int n_sc, int n_sym, int nr, int nt, float sigma, float threshold,
                           const float2 *H, const float2 *Y, float2 *R, float *inv_diag,

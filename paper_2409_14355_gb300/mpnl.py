@@ -43,7 +43,7 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs",
             "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd", "mpnl_qhy_mixed",
             "mpnl_detect_units_noalloc")
-ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16 = 1, 2, 4
+ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16, ITEM_REFINE_QR = 1, 2, 4, 8
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
 RUN_GRAPH = 16
@@ -736,8 +736,8 @@ def batch_item(dims, sigma2: float, flags: int = 0, stages: int = 0, **arrays) -
 class Batch:
     """A mixed-size batch of radio units' slots run by the persistent
     launches (mpnl_batch_*).  Units are SlotBuffers given as (buffers,
-    sigma2, mmse_qr, mmse[, precision]) tuples ("fp32" when precision is
-    left out), whose H and Y the caller fills; ``run``
+    sigma2, mmse_qr, mmse[, precision[, refine]]) tuples ("fp32" and no FP64
+    re-factorisation when left out), whose H and Y the caller fills; ``run``
     writes their R/perm/Z/paths state and results.  Alternatively pass
     ready-made BatchItemC items (``items=``) that reference tensors the
     caller keeps alive."""
@@ -760,10 +760,11 @@ class Batch:
     def _unit_item(unit) -> BatchItemC:
         buf, sigma2, mmse_qr, mmse = unit[:4]
         precision = unit[4] if len(unit) > 4 else "fp32"
+        refine = bool(unit[5]) if len(unit) > 5 else False
         if precision not in ("fp32", "fp16"):
             raise ValueError(f"precision must be fp32 or fp16, not {precision!r}")
         flags = (ITEM_MMSE_QR if mmse_qr else 0) | (ITEM_LINEAR_MMSE if mmse else 0) \
-            | (ITEM_FP16 if precision == "fp16" else 0)
+            | (ITEM_FP16 if precision == "fp16" else 0) | (ITEM_REFINE_QR if refine else 0)
         names = ("H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard", "llr", "ped2")
         arrays = {n: getattr(buf, n) for n in names}
         if mmse:

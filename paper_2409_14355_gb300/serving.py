@@ -8,7 +8,9 @@ N_pe position vectors, all computed from the channel alone when the RU
 reports a new channel (§II: the candidate positions are found before the
 data arrives) -- and serves two kinds of requests:
 
-  channel  new H for an RU: sorted QR keeping Q, then the path selection;
+  channel  new H for an RU: sorted QR keeping Q (FP16 units: re-factorised
+           in FP64 where the channel is ill-conditioned), then the path
+           selection;
   slot     the received symbols Y of one slot: z = Q^H y, the N_pe walks,
            hard decisions and max-log LLRs.
 
@@ -42,6 +44,10 @@ import torch
 from . import inputs, mpnl
 
 DEADLINE_S = 0.5e-3
+# FP16 units' channels whose FP32 factor has max R_ll / min R_ll above this
+# are re-factorised in FP64 (the threshold the mixed-precision path is
+# stated for; the batch stage uses the same)
+REFINE_COND = 1e3
 
 
 @dataclass
@@ -208,6 +214,9 @@ class Server:
         Hd = H.to(dev)
         mpnl.factor(Hd, ru.sigma2 if ru.mmse_qr else None,
                     out=(st["Q"], st["R"], st["inv_diag"], st["perm"]))
+        if ru.precision == "fp16":
+            mpnl.refine_qr(Hd, None, st["R"], st["inv_diag"], st["perm"], Q=st["Q"],
+                           sigma2=ru.sigma2 if ru.mmse_qr else None, cond_threshold=REFINE_COND)
         mpnl.select_paths(st["R"], ru.sigma2, ru.qam, ru.n_pe, nt, out=st["paths"])
         torch.cuda.synchronize(dev)
         self.rus[ru.ru_id] = ru
@@ -367,7 +376,7 @@ class Server:
                 it.dims = mpnl.Dims(*ru.dims)
                 it.sigma2 = ru.sigma2
                 it.flags = (mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0) \
-                    | (mpnl.ITEM_FP16 if ru.precision == "fp16" else 0)
+                    | (mpnl.ITEM_FP16 | mpnl.ITEM_REFINE_QR if ru.precision == "fp16" else 0)
                 it.Q, it.R = s_["Q"].data_ptr(), s_["R"].data_ptr()
                 it.inv_diag, it.perm = s_["inv_diag"].data_ptr(), s_["perm"].data_ptr()
                 it.paths = s_["paths"].data_ptr()

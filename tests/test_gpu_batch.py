@@ -182,3 +182,42 @@ def test_autotuner_picks_valid_knobs(dev):
     assert report["classes"] and report["batch_ms"]
     # the tuner leaves the built-in knobs installed
     assert autotune.to_dict(mpnl.get_tuning()) == autotune.to_dict(mpnl.Tuning())
+
+
+def test_refine_stage_equals_the_per_call_refinement(dev):
+    # units flagged MPNL_ITEM_REFINE_QR get the FP64 re-factorisation right
+    # after their sorted QR in the batch: the results equal the per-call path
+    # with mpnl_refine_qr at the same threshold; ill-conditioned channels
+    # make sure the stage changes something
+    from tests.test_gpu_refine import _ill_slot
+
+    mpnl = _mpnl()
+    units, plain = [], []
+    for k, (nr, nt, qam, n_pe, mmse_qr, prec) in enumerate(
+            [(8, 8, 16, 64, False, "fp16"), (16, 16, 64, 128, False, "fp32"),
+             (12, 6, 16, 32, False, "fp16"), (8, 8, 4, 64, True, "fp16")]):
+        H, Y, sigma2 = _ill_slot(nr, nt, qam, 21 + k, 1e5, 40 + k)
+        sigma2 = max(sigma2, 1e-3)
+        for lst, refine in ((units, True), (plain, False)):
+            buf = mpnl.SlotBuffers(H.shape[0], 14, nr, nt, qam, n_pe, dev, mmse=False)
+            buf.H.copy_(torch.from_numpy(H))
+            buf.Y.copy_(torch.from_numpy(Y))
+            lst.append((buf, sigma2, mmse_qr, False, prec, refine))
+    for lst in (units, plain):
+        batch = mpnl.Batch(lst, dev)
+        batch.run()
+        torch.cuda.synchronize()
+        batch.close()
+    mpnl.check_status()
+    changed = 0
+    for k, unit in enumerate(units):
+        buf, sigma2, mmse_qr, _, prec, _ = unit
+        n_sc, n_sym, nr, nt, qam, n_pe = buf.dims
+        ref = mpnl.SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, dev, mmse=False)
+        mpnl.run_slot(ref, buf.H, buf.Y, sigma2, mmse=False, mmse_qr=mmse_qr, precision=prec,
+                      refine_threshold=1e3)
+        torch.cuda.synchronize()
+        for name in OUTS:
+            assert torch.equal(getattr(buf, name), getattr(ref, name)), (k, name)
+        changed += int(not torch.equal(buf.R, plain[k][0].R))
+    assert changed >= 3

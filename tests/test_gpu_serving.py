@@ -61,8 +61,12 @@ def test_factor_and_stored_q_match_oracle(dev, nr, nt, qam, n_sc, mmse_qr):
 
 
 def _alone(dev, ru, H, Y):
-    from paper_2409_14355_gb300 import mpnl
-    Q, R, inv_diag, perm = mpnl.factor(H.to(dev), ru.sigma2 if ru.mmse_qr else None)
+    from paper_2409_14355_gb300 import mpnl, serving
+    Hd = H.to(dev)
+    Q, R, inv_diag, perm = mpnl.factor(Hd, ru.sigma2 if ru.mmse_qr else None)
+    if ru.precision == "fp16":
+        mpnl.refine_qr(Hd, None, R, inv_diag, perm, Q=Q, sigma2=ru.sigma2 if ru.mmse_qr else None,
+                       cond_threshold=serving.REFINE_COND)
     paths = mpnl.select_paths(R, ru.sigma2, ru.qam, ru.n_pe, ru.nt)
     Z = mpnl.qhy(Q, Y.to(dev), precision=ru.precision)
     hard, llr, _ = mpnl.detect(R, inv_diag, perm, paths, Z, ru.sigma2, ru.qam,
