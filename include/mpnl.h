@@ -301,6 +301,34 @@ int mpnl_detect_mixed(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const
                       const uint8_t *perm, const uint8_t *paths, const void *Z, float sigma2,
                       uint8_t *hard, float *llr, float *ped2, void *ws, void *stream);
 
+/* End-to-end detection of one slot held in the caller's buffers (the whole
+ * path of §II and the MMSE baseline of §III-B in one call): H and Y are
+ * copied into the workspace, the sorted QR + z, the path selection, the
+ * walks and, with MPNL_SLOT_MMSE, the linear MMSE baseline run there, and the
+ * hard decisions, LLRs and PED pairs (and the baseline's outputs) are copied
+ * back -- all enqueued on `stream` in that order, so the results are in the
+ * caller's buffers once the stream has reached the end of the call.  The
+ * buffers may be host memory (pinned lets the copies run asynchronously;
+ * pageable makes CUDA copy them synchronously) or device memory.
+ *   H, Y                 in   as mpnl_preprocess (nt <= nr, or nr + nt <= MPNL_MAX_NR
+ *                             with MPNL_SLOT_MMSE_QR)
+ *   hard, llr, ped2      out  as mpnl_detect (llr, ped2 nullable)
+ *   mmse_hard, mmse_llr  out  as mpnl_linear_mmse (MPNL_SLOT_MMSE; mmse_llr nullable)
+ *   flags                MPNL_SLOT_MMSE, MPNL_SLOT_FP16 (the walks of mpnl_detect_mixed),
+ *                        MPNL_SLOT_MMSE_QR (the pre-processing of mpnl_preprocess_mmse)
+ *   ws, ws_bytes         device workspace of at least mpnl_slot_workspace_bytes(dims,
+ *                        flags) bytes, 256-byte aligned, owned by the caller; it holds
+ *                        the slot's intermediates until the stream passes the call, so
+ *                        one call in flight per workspace
+ * Errors: as the per-call steps; a workspace too small or misaligned. */
+#define MPNL_SLOT_MMSE 1
+#define MPNL_SLOT_FP16 2
+#define MPNL_SLOT_MMSE_QR 4
+size_t mpnl_slot_workspace_bytes(const mpnl_dims *dims, int flags);
+int mpnl_detect_slot(mpnl_ctx *ctx, const mpnl_dims *dims, float sigma2, const void *H,
+                     const void *Y, uint8_t *hard, float *llr, float *ped2, uint8_t *mmse_hard,
+                     float *mmse_llr, int flags, void *ws, size_t ws_bytes, void *stream);
+
 /* Linear MMSE baseline (§I, §III-B: "de facto standard linear MMSE"):
  * W = (H^H H + sigma2 I)^{-1} H^H; x = W y; mu_k = (W H)_kk;
  * x~_k = x_k / mu_k, nu_k = (1 - mu_k) / mu_k; hard = nearest point to x~_k;

@@ -50,6 +50,22 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kTopList = 64;  // entries of the first-level neighbour list
 constexpr int kList2 = 128;   // per symbol: entries of all second-level lists together
 
+// A neighbour-list entry in 8 bytes: the squared distance, and the label
+// with the point's two grid indices (the point itself is axis_pos of them).
+__device__ __forceinline__ uint2 list_entry(float d, int lab, int ix, int iy)
+{
+    return make_uint2(__float_as_uint(d), (unsigned)lab | ((unsigned)ix << 8) | ((unsigned)iy << 16));
+}
+
+template <int QAM>
+__device__ __forceinline__ void list_point(uint2 e, float &x, float &y, float &d, int &lab)
+{
+    d = __uint_as_float(e.x);
+    lab = (int)(e.y & 0xffu);
+    x = axis_pos<QAM>((int)((e.y >> 8) & 0xffu));
+    y = axis_pos<QAM>((int)((e.y >> 16) & 0xffu));
+}
+
 // --------------------------------------------------------------------------
 // ranking
 // --------------------------------------------------------------------------
@@ -255,9 +271,9 @@ __device__ __noinline__ float kth_point_slow(float bx, float by, int p, int ire,
 // The first detected level sees the same b = z_{nt-1} / R for every row, so
 // its ordered neighbour list is built once per symbol by one warp: lane j
 // holds points j and j + 32, and a bitonic sort of their (distance, label)
-// keys over the warp orders them.  Entry r: (x, y, distance, label).
+// keys over the warp orders them.  Entry r: distance, label, grid indices.
 template <int QAM>
-__device__ __forceinline__ void top_list(float bx, float by, int kmax, float4 *list)
+__device__ __forceinline__ void top_list(float bx, float by, int kmax, uint2 *list)
 {
     // keys (distance bits, label, grid index): as unsigned 64-bit integers
     // they order by (distance, label); a bitonic sort over the warp puts the
@@ -307,17 +323,17 @@ __device__ __forceinline__ void top_list(float bx, float by, int kmax, float4 *l
         if (e < kmax && e < M) {
             const int q = (int)(key[k] & 0xffu);
             const float dq = __uint_as_float((unsigned)(key[k] >> 32));
-            list[e] = make_float4(axis_pos<QAM>(q % Qam<QAM>::L), axis_pos<QAM>(q / Qam<QAM>::L), dq,
-                                  __int_as_float((int)((key[k] >> 8) & 0xffu)));
+            list[e] = list_entry(dq, (int)((key[k] >> 8) & 0xffu), q % Qam<QAM>::L,
+                                 q / Qam<QAM>::L);
         }
     }
 }
 
 // The len nearest points to b in order, by one thread: the staircase
-// enumeration of kth_point_slow, emitting every pop.  Entry r: (x, y,
-// distance, label).
+// enumeration of kth_point_slow, emitting every pop.  Entry r: distance,
+// label, grid indices.
 template <int QAM>
-__device__ __forceinline__ void nearest_list(float bx, float by, int len, float4 *out)
+__device__ __forceinline__ void nearest_list(float bx, float by, int len, uint2 *out)
 {
     constexpr int L = Qam<QAM>::L;
     float d0;
@@ -344,7 +360,7 @@ __device__ __forceinline__ void nearest_list(float bx, float by, int len, float4
                 blab = lv;
             }
         }
-        out[pop] = make_float4(axis_pos<QAM>(bi), axis_pos<QAM>(bj), bd, __int_as_float(blab));
+        out[pop] = list_entry(bd, blab, bi, bj);
         const int bc = (cols >> (4 * ba)) & 0xF;
         if (bc == 0 && ba == na - 1 && na < L) ++na;
         cols += 1u << (4 * ba);
@@ -464,9 +480,9 @@ __host__ __device__ inline DetSmem det_layout(int NT, int B, int n_pe, int n_sym
     s.off_blab = o;
     o = a16(o + n_sym * chunks * WORDS * 4);
     s.off_top = o;
-    o = a16(o + (n_sym + 1) * kTopList * 16);
+    o = a16(o + (n_sym + 1) * kTopList * 8);
     s.off_l2 = o;
-    o = a16(o + (n_sym + 1) * kList2 * 16);
+    o = a16(o + (n_sym + 1) * kList2 * 8);
     s.off_lut = o;  // 2-D label of grid point (ire, iim) at ire * 8 + iim
     o = a16(o + 64);
     s.off_rh = s.off_rd = s.off_pt = s.off_rp = o;
@@ -768,8 +784,8 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
     unsigned *sWmin = reinterpret_cast<unsigned *>(smem + S.off_wmin);
     unsigned *sSecond = reinterpret_cast<unsigned *>(smem + S.off_second);
     uint32_t *sBlab = reinterpret_cast<uint32_t *>(smem + S.off_blab);
-    float4 *sTop = reinterpret_cast<float4 *>(smem + S.off_top);
-    float4 *sL2 = reinterpret_cast<float4 *>(smem + S.off_l2);
+    uint2 *sTop = reinterpret_cast<uint2 *>(smem + S.off_top);
+    uint2 *sL2 = reinterpret_cast<uint2 *>(smem + S.off_l2);
     int *sScr = reinterpret_cast<int *>(smem + S.off_scr);
     int *s_k1 = sScr + kScrK1, *s_off1 = sScr + kScrOff1;  // QAM + 1 entries each
     int &s_use2 = sScr[kScrUse2];
@@ -981,10 +997,12 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
             const int s = it / kmx, a = 1 + it - s * kmx;
             const int len = s_k1[a];
             if (len == 0) continue;
-            const float4 q = sTop[s * kTopList + a - 1];
+            float qx, qy, qd;
+            int qlab;
+            list_point<QAM>(sTop[s * kTopList + a - 1], qx, qy, qd, qlab);
             const float2 z = sZ[s * NT + l];
-            const float ex = z.x - (r.x * q.x - r.y * q.y);
-            const float ey = z.y - (r.x * q.y + r.y * q.x);
+            const float ex = z.x - (r.x * qx - r.y * qy);
+            const float ey = z.y - (r.x * qy + r.y * qx);
             nearest_list<QAM>(ex * iv, ey * iv, len, sL2 + s * kList2 + s_off1[a]);
         }
         __syncthreads();
@@ -1027,7 +1045,7 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
                 float sx[SYM], sy[SYM], dist[SYM];
                 int lb[SYM];
                 if (l >= l_list) {  // list-served levels (warp-uniform branch)
-                    const float4 *lst;
+                    const uint2 *lst;
                     int stride;
                     if (l == nt - 1) {
                         p_top = p;
@@ -1038,13 +1056,8 @@ __device__ __forceinline__ void detect_body(const DetArgs &args, int sc, unsigne
                         stride = kList2;
                     }
 #pragma unroll
-                    for (int k = 0; k < SYM; ++k) {
-                        const float4 q = lst[k * stride];
-                        sx[k] = q.x;
-                        sy[k] = q.y;
-                        dist[k] = q.z;
-                        lb[k] = __float_as_int(q.w);
-                    }
+                    for (int k = 0; k < SYM; ++k)
+                        list_point<QAM>(lst[k * stride], sx[k], sy[k], dist[k], lb[k]);
                 } else {
                     const float iv = sInvd[l];
                     int ire[SYM], iim[SYM];

@@ -966,3 +966,136 @@ int mpnl_probe_ffma(mpnl_ctx *ctx, int n_blocks, int iters, float *out, double *
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// End-to-end slot call on caller buffers (host or device) with a workspace
+// ---------------------------------------------------------------------------
+namespace {
+
+struct SlotLayout {
+    size_t H, Y, R, invd, perm, Z, paths, hard, llr, ped2, mhard, mllr, bytes;
+};
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+SlotLayout slot_layout(const mpnl_dims *d, int flags)
+{
+    const size_t sc = (size_t)d->n_sc, ns = (size_t)d->n_sym, nr = (size_t)d->nr,
+                 nt = (size_t)d->nt, B = (size_t)bits_of(d->qam);
+    SlotLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    L.H = take(sc * nr * nt * 8);
+    L.Y = take(sc * ns * nr * 8);
+    L.R = take(sc * (nt * (nt + 1) / 2) * 8);
+    L.invd = take(sc * nt * 4);
+    L.perm = take(sc * nt);
+    L.Z = take(sc * ns * nt * 8);
+    L.paths = take(sc * (size_t)d->n_pe * nt);
+    L.hard = take(sc * ns * nt);
+    L.llr = take(sc * ns * nt * B * 4);
+    L.ped2 = take(sc * ns * 2 * 4);
+    const bool mm = flags & MPNL_SLOT_MMSE;
+    L.mhard = take(mm ? sc * ns * nt : 0);
+    L.mllr = take(mm ? sc * ns * nt * B * 4 : 0);
+    L.bytes = o;
+    return L;
+}
+
+// non-NULL and aligned; host memory of any kind is fine for a copy
+int check_buf(mpnl_ctx *ctx, const void *p, size_t align, const char *name, bool nullable)
+{
+    if (!p) return nullable ? MPNL_OK : fail(ctx, MPNL_ERR_INVALID_ARG, "%s is NULL", name);
+    if ((uintptr_t)p % align)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "%s is not %zu-byte aligned", name, align);
+    return MPNL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mpnl_slot_workspace_bytes(const mpnl_dims *dims, int flags)
+{
+    if (!dims || dims->n_sc < 0 || dims->n_sym < 0 || dims->nr < 0 || dims->nt < 0 ||
+        dims->n_pe < 0 || !bits_of(dims->qam))
+        return 0;
+    return slot_layout(dims, flags).bytes;
+}
+
+int mpnl_detect_slot(mpnl_ctx *ctx, const mpnl_dims *d, float sigma2, const void *H,
+                     const void *Y, uint8_t *hard, float *llr, float *ped2, uint8_t *mmse_hard,
+                     float *mmse_llr, int flags, void *ws, size_t ws_bytes, void *stream)
+{
+    MPNL_TRY(begin(ctx));
+    if (flags & ~(MPNL_SLOT_MMSE | MPNL_SLOT_FP16 | MPNL_SLOT_MMSE_QR))
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "unknown slot flags 0x%x", flags);
+    const bool mqr = flags & MPNL_SLOT_MMSE_QR;
+    MPNL_TRY(check_dims(ctx, d, true, mqr ? kNrAugmented : kNrTall));
+    MPNL_TRY(check_sigma2(ctx, sigma2));
+    if (d->n_sc == 0) return MPNL_OK;
+    const SlotLayout L = slot_layout(d, flags);
+    if (ws_bytes < L.bytes)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "workspace of %zu bytes, need %zu", ws_bytes,
+                    L.bytes);
+    MPNL_TRY(check_ptr(ctx, ws, 256, "ws", false));
+    MPNL_TRY(check_buf(ctx, H, 8, "H", false));
+    MPNL_TRY(check_buf(ctx, Y, 8, "Y", false));
+    MPNL_TRY(check_buf(ctx, hard, 1, "hard", false));
+    MPNL_TRY(check_buf(ctx, llr, 4, "llr", true));
+    MPNL_TRY(check_buf(ctx, ped2, 4, "ped2", true));
+    const bool mm = flags & MPNL_SLOT_MMSE;
+    MPNL_TRY(check_buf(ctx, mmse_hard, 1, "mmse_hard", !mm));
+    MPNL_TRY(check_buf(ctx, mmse_llr, 4, "mmse_llr", true));
+    unsigned char *w = (unsigned char *)ws;
+    float2 *dH = (float2 *)(w + L.H), *dY = (float2 *)(w + L.Y), *dR = (float2 *)(w + L.R);
+    float2 *dZ = (float2 *)(w + L.Z);
+    float *dInv = (float *)(w + L.invd), *dLlr = (float *)(w + L.llr);
+    float *dPed = (float *)(w + L.ped2), *dMllr = (float *)(w + L.mllr);
+    uint8_t *dPerm = w + L.perm, *dPaths = w + L.paths, *dHard = w + L.hard, *dMhard = w + L.mhard;
+    const size_t sc = (size_t)d->n_sc, ns = (size_t)d->n_sym, nt = (size_t)d->nt;
+    const size_t B = (size_t)bits_of(d->qam);
+    cudaStream_t st = (cudaStream_t)stream;
+    const char *what = "slot input copy";
+    cudaError_t e = cudaMemcpyAsync(dH, H, sc * d->nr * nt * 8, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dY, Y, sc * ns * d->nr * 8, cudaMemcpyDefault, st);
+    if (e == cudaSuccess) {
+        what = "preprocess launch";
+        e = mpnl::launch_preprocess(d->n_sc, d->n_sym, d->nr, d->nt, mqr ? sqrtf(sigma2) : 0.f, dH,
+                                    dY, dR, dInv, dPerm, dZ, nullptr, st);
+    }
+    if (e == cudaSuccess && mm) {
+        what = "mmse launch";
+        e = mpnl::launch_mmse(d->n_sc, d->n_sym, d->nr, d->nt, d->qam, sigma2, dH, dY, dMhard,
+                              mmse_llr ? dMllr : nullptr, st);
+    }
+    if (e == cudaSuccess) {
+        what = "select_paths launch";
+        e = mpnl::launch_select_paths(d->n_sc, d->nt, d->qam, d->n_pe, sigma2, dR, dPaths,
+                                      tuned_select_warps(ctx, d), st);
+    }
+    if (e == cudaSuccess) {
+        what = "detect launch";
+        e = mpnl::launch_detect(d->n_sc, d->n_sym, d->nt, d->qam, d->n_pe, sigma2, dR, dInv, dPerm,
+                                dPaths, dZ, dHard, llr ? dLlr : nullptr, ped2 ? dPed : nullptr,
+                                ctx->status, (flags & MPNL_SLOT_FP16) != 0, tuned_sym(ctx, d), st);
+    }
+    if (e == cudaSuccess) {
+        what = "slot output copy";
+        e = cudaMemcpyAsync(hard, dHard, sc * ns * nt, cudaMemcpyDefault, st);
+    }
+    if (e == cudaSuccess && llr)
+        e = cudaMemcpyAsync(llr, dLlr, sc * ns * nt * B * 4, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && ped2) e = cudaMemcpyAsync(ped2, dPed, sc * ns * 8, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && mm) e = cudaMemcpyAsync(mmse_hard, dMhard, sc * ns * nt, cudaMemcpyDefault, st);
+    if (e == cudaSuccess && mm && mmse_llr)
+        e = cudaMemcpyAsync(mmse_llr, dMllr, sc * ns * nt * B * 4, cudaMemcpyDefault, st);
+    if (e != cudaSuccess) return cuda_fail(ctx, what, e);
+    return MPNL_OK;
+}
+
+}  // extern "C"

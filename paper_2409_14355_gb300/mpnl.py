@@ -42,7 +42,7 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr",
             "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs",
             "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd", "mpnl_qhy_mixed",
-            "mpnl_detect_units_noalloc")
+            "mpnl_detect_units_noalloc", "mpnl_detect_slot", "mpnl_slot_workspace_bytes")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16, ITEM_REFINE_QR = 1, 2, 4, 8
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
@@ -50,6 +50,7 @@ RUN_GRAPH = 16
 RUN_SHARE_SMS = 64
 RESET_TRUSTED_POINTERS = 1
 NOALLOC_MAX_UNITS = 64
+SLOT_MMSE, SLOT_FP16, SLOT_MMSE_QR = 1, 2, 4
 PRECISIONS = ("fp32", "fp16")
 
 
@@ -165,6 +166,10 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_batch_destroy.restype = None
         lib.mpnl_detect_units_noalloc.argtypes = [ctypes.POINTER(BatchItemC), I, P]
         lib.mpnl_detect_units_noalloc.restype = I
+        lib.mpnl_slot_workspace_bytes.argtypes = [D, I]
+        lib.mpnl_slot_workspace_bytes.restype = S
+        lib.mpnl_detect_slot.argtypes = [P, D, F, P, P, P, P, P, P, P, I, P, S, P]
+        lib.mpnl_detect_slot.restype = I
         lib.mpnl_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
         lib.mpnl_set_tuning.restype = I
         lib.mpnl_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
@@ -603,46 +608,100 @@ def run_slot(buf: SlotBuffers, H, Y, sigma2: float, mmse: bool = True,
         linear_mmse(H, Y, sigma2, qam, out=(buf.mmse_hard, buf.mmse_llr))
 
 
+def slot_flags(mmse: bool, precision: str, mmse_qr: bool) -> int:
+    if precision not in PRECISIONS:
+        raise MpnlError(ERR_INVALID_ARG, f"precision {precision!r} not in {PRECISIONS}")
+    return (SLOT_MMSE if mmse else 0) | (SLOT_FP16 if precision == "fp16" else 0) \
+        | (SLOT_MMSE_QR if mmse_qr else 0)
+
+
+def slot_workspace_bytes(n_sc, n_sym, nr, nt, qam, n_pe, flags: int = 0) -> int:
+    d = Dims(n_sc, n_sym, nr, nt, qam, n_pe)
+    return int(load_library().mpnl_slot_workspace_bytes(ctypes.byref(d), flags))
+
+
+class SlotOutputs:
+    """Result buffers of one slot (host, pinned when `pin`), as mpnl_detect_slot writes them."""
+
+    def __init__(self, n_sc, n_sym, nt, qam, mmse: bool, pin: bool = True):
+        B = BITS[qam]
+        kw = dict(pin_memory=pin)
+        self.hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, **kw)
+        self.llr = torch.empty((n_sc, n_sym, nt, B), dtype=torch.float32, **kw)
+        self.ped2 = torch.empty((n_sc, n_sym, 2), dtype=torch.float32, **kw)
+        self.mmse_hard = torch.empty((n_sc, n_sym, nt), dtype=torch.uint8, **kw) if mmse else None
+        self.mmse_llr = (torch.empty((n_sc, n_sym, nt, B), dtype=torch.float32, **kw)
+                         if mmse else None)
+
+    def as_dict(self) -> dict:
+        out = dict(hard=self.hard, llr=self.llr, ped2=self.ped2)
+        if self.mmse_hard is not None:
+            out["mmse_hard"] = self.mmse_hard
+            out["mmse_llr"] = self.mmse_llr
+        return out
+
+
+def detect_slot_into(H, Y, sigma2: float, qam: int, n_pe: int, out: SlotOutputs,
+                     workspace: torch.Tensor, flags: int = 0, stream=None) -> None:
+    """mpnl_detect_slot: the whole path of one slot on the caller's buffers
+    (host or device tensors), enqueued on `stream` (default: the current
+    stream of the workspace's device); `workspace` is a device uint8 tensor of
+    at least slot_workspace_bytes(...) bytes, one call in flight per workspace."""
+    n_sc, nr, nt = H.shape
+    n_sym = Y.shape[1]
+    _need(H, torch.complex64, (n_sc, nr, nt), "H")
+    _need(Y, torch.complex64, (n_sc, n_sym, nr), "Y")
+    dev = _dev_of(workspace)
+    ctx = context(dev.index)
+    d = Dims(n_sc, n_sym, nr, nt, qam, n_pe)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    _raise(load_library().mpnl_detect_slot(
+        ctx, ctypes.byref(d), float(sigma2), _ptr(H), _ptr(Y), _ptr(out.hard), _ptr(out.llr),
+        _ptr(out.ped2), _ptr(out.mmse_hard), _ptr(out.mmse_llr), int(flags), _ptr(workspace),
+        workspace.numel(), ctypes.c_void_p(st.cuda_stream)), ctx)
+
+
 def detect_slot(H, Y, sigma2: float, qam: int, n_pe: int, mmse: bool = False,
                 buffers: SlotBuffers | None = None, device=None, precision: str = "fp32",
                 mmse_qr: bool = False):
     """End-to-end call a user makes: accepts host (ideally pinned) or device
-    tensors.  Host inputs are copied to the device, the path runs, and the
-    hard decisions and LLRs (and MMSE outputs with ``mmse``) come back as host
-    tensors.  Returns a dict."""
+    tensors.  Host inputs go through mpnl_detect_slot (copies in, the path,
+    copies out, one C-ABI call) and the results come back as host tensors;
+    device inputs run the per-call steps into `buffers`.  Returns a dict."""
     host = H.device.type == "cpu"
     if device is None:
         device = torch.device("cuda", torch.cuda.current_device()) if host else H.device
     n_sc, nr, nt = H.shape
     n_sym = Y.shape[1]
-    buf = buffers or SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, device, mmse)
     if host:
-        buf.H.copy_(H, non_blocking=True)
-        buf.Y.copy_(Y, non_blocking=True)
-        Hd, Yd = buf.H, buf.Y
-    else:
-        Hd, Yd = H, Y
-    run_slot(buf, Hd, Yd, sigma2, mmse, precision, mmse_qr)
+        device = torch.device(device)
+        flags = slot_flags(mmse, precision, mmse_qr)
+        ws = torch.empty(slot_workspace_bytes(n_sc, n_sym, nr, nt, qam, n_pe, flags),
+                         dtype=torch.uint8, device=device)
+        out = SlotOutputs(n_sc, n_sym, nt, qam, mmse, pin=True)
+        st = torch.cuda.current_stream(device)
+        detect_slot_into(H, Y, sigma2, qam, n_pe, out, ws, flags, stream=st)
+        st.synchronize()
+        return out.as_dict()
+    buf = buffers or SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, device, mmse)
+    run_slot(buf, H, Y, sigma2, mmse, precision, mmse_qr)
     out = dict(hard=buf.hard, llr=buf.llr, ped2=buf.ped2)
     if mmse:
         out["mmse_hard"] = buf.mmse_hard
         out["mmse_llr"] = buf.mmse_llr
-    if host:
-        out = {k: v.to("cpu", non_blocking=True) for k, v in out.items()}
-        torch.cuda.current_stream(device).synchronize()
     return out
 
 
 class SlotPipeline:
     """End-to-end detection of a stream of slots held in host memory, with
-    `depth` slots in flight.  A slot's host-to-device copies, the path and
-    the device-to-host copies of its results run on the slot's own stream
-    (the MMSE baseline, which needs only H and Y, on a side stream), so the
-    copies of one slot overlap the kernels of another.  Inputs should be
-    pinned host tensors (pageable ones are copied synchronously).  Results
-    land in pinned host buffers owned by the pipeline: ``result(ticket)``
-    waits for that slot and returns views that stay valid until the same
-    buffers are reused, `depth` submissions later."""
+    `depth` slots in flight.  Each slot is one mpnl_detect_slot call on the
+    slot's own stream and workspace: the copies of H and Y in, the path (and
+    the MMSE baseline), the copies of the results out -- so one slot's copies
+    overlap another slot's kernels.  Inputs should be pinned host tensors
+    (pageable ones are copied synchronously).  Results land in pinned host
+    buffers owned by the pipeline: ``result(ticket)`` waits for that slot and
+    returns views that stay valid until the same buffers are reused, `depth`
+    submissions later."""
 
     def __init__(self, n_sc, n_sym, nr, nt, qam, n_pe, device=None, depth: int = 2,
                  mmse: bool = True, precision: str = "fp32", mmse_qr: bool = False):
@@ -651,27 +710,25 @@ class SlotPipeline:
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None
                                    else torch.device(device).index or 0)
         self.dims = (n_sc, n_sym, nr, nt, qam, n_pe)
-        self.mmse, self.precision, self.mmse_qr = mmse, precision, mmse_qr
+        self.flags = slot_flags(mmse, precision, mmse_qr)
+        self.mmse = mmse
+        nbytes = slot_workspace_bytes(n_sc, n_sym, nr, nt, qam, n_pe, self.flags)
         self._lanes = []
         for _ in range(depth):
-            buf = SlotBuffers(n_sc, n_sym, nr, nt, qam, n_pe, self.device, mmse)
-            names = ("hard", "llr", "ped2") + (("mmse_hard", "mmse_llr") if mmse else ())
-            host = {k: torch.empty(getattr(buf, k).shape, dtype=getattr(buf, k).dtype,
-                                   pin_memory=True) for k in names}
-            self._lanes.append(dict(buf=buf, host=host, ticket=-1,
-                                    stream=torch.cuda.Stream(self.device),
-                                    side=torch.cuda.Stream(self.device),
-                                    done=torch.cuda.Event()))
+            self._lanes.append(dict(
+                ws=torch.empty(nbytes, dtype=torch.uint8, device=self.device),
+                out=SlotOutputs(n_sc, n_sym, nt, qam, mmse, pin=True), ticket=-1,
+                stream=torch.cuda.Stream(self.device), done=torch.cuda.Event()))
         self._next = 0
 
     @property
     def h2d_bytes(self) -> int:
-        b = self._lanes[0]["buf"]
-        return b.H.numel() * b.H.element_size() + b.Y.numel() * b.Y.element_size()
+        n_sc, n_sym, nr, nt, _, _ = self.dims
+        return n_sc * nr * nt * 8 + n_sc * n_sym * nr * 8
 
     @property
     def d2h_bytes(self) -> int:
-        return sum(v.numel() * v.element_size() for v in self._lanes[0]["host"].values())
+        return sum(v.numel() * v.element_size() for v in self._lanes[0]["out"].as_dict().values())
 
     def submit(self, H, Y, sigma2: float) -> int:
         """Enqueue one slot (host H [n_sc][nr][nt], Y [n_sc][n_sym][nr],
@@ -683,25 +740,10 @@ class SlotPipeline:
         if lane["ticket"] >= 0:
             lane["done"].synchronize()
         lane["ticket"] = ticket
-        buf, st, side, host = lane["buf"], lane["stream"], lane["side"], lane["host"]
-        qam = self.dims[4]
-        with torch.cuda.stream(st):
-            buf.H.copy_(H, non_blocking=True)
-            buf.Y.copy_(Y, non_blocking=True)
-        if self.mmse:
-            side.wait_stream(st)
-            with torch.cuda.stream(side):
-                linear_mmse(buf.H, buf.Y, sigma2, qam, out=(buf.mmse_hard, buf.mmse_llr))
-                host["mmse_hard"].copy_(buf.mmse_hard, non_blocking=True)
-                host["mmse_llr"].copy_(buf.mmse_llr, non_blocking=True)
-        with torch.cuda.stream(st):
-            run_slot(buf, buf.H, buf.Y, sigma2, mmse=False, precision=self.precision,
-                     mmse_qr=self.mmse_qr)
-            for k in ("hard", "llr", "ped2"):
-                host[k].copy_(getattr(buf, k), non_blocking=True)
-            if self.mmse:
-                st.wait_stream(side)
-            lane["done"].record(st)
+        qam, n_pe = self.dims[4], self.dims[5]
+        detect_slot_into(H, Y, sigma2, qam, n_pe, lane["out"], lane["ws"], self.flags,
+                         stream=lane["stream"])
+        lane["done"].record(lane["stream"])
         return ticket
 
     def result(self, ticket: int) -> dict:
@@ -710,7 +752,7 @@ class SlotPipeline:
         if lane["ticket"] != ticket:
             raise ValueError(f"ticket {ticket} is no longer held (buffers reused)")
         lane["done"].synchronize()
-        return lane["host"]
+        return lane["out"].as_dict()
 
     def check_status(self) -> None:
         """Raise on device-side errors recorded by the slots' launches."""

@@ -59,3 +59,50 @@ def test_pipeline_equals_each_slot_alone(dev, name, n_pe, n_sc, depth, precision
         with pytest.raises(ValueError):
             pipe.result(t1)
         torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("mmse_qr,precision,pinned", [(False, "fp32", False), (True, "fp16", True)])
+def test_c_abi_slot_call_with_host_buffers(dev, mmse_qr, precision, pinned):
+    # mpnl_detect_slot straight through ctypes: host H and Y (pageable or
+    # pinned), host outputs, a caller workspace; bit-identical to the
+    # per-call steps on device copies
+    import ctypes
+
+    import numpy as np
+    from paper_2409_14355_gb300 import mpnl
+    lib = mpnl.load_library()
+    sl = inputs.make_slot(6, 8 if mmse_qr else 6, 16, 53, 14, 17.0, "iid", 0.3, 9)
+    n_pe = 48
+    flags = mpnl.SLOT_MMSE | (mpnl.SLOT_FP16 if precision == "fp16" else 0) \
+        | (mpnl.SLOT_MMSE_QR if mmse_qr else 0)
+    H, Y = torch.from_numpy(sl.H), torch.from_numpy(sl.Y)
+    if pinned:
+        H, Y = H.pin_memory(), Y.pin_memory()
+    out = mpnl.SlotOutputs(sl.n_sc, 14, sl.nt, sl.qam, mmse=True, pin=pinned)
+    d = mpnl.Dims(sl.n_sc, 14, sl.nr, sl.nt, sl.qam, n_pe)
+    nbytes = lib.mpnl_slot_workspace_bytes(ctypes.byref(d), flags)
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    ctx = mpnl.context(dev.index)
+    st = torch.cuda.current_stream(dev)
+    P = ctypes.c_void_p
+    args = [P(H.data_ptr()), P(Y.data_ptr()), P(out.hard.data_ptr()), P(out.llr.data_ptr()),
+            P(out.ped2.data_ptr()), P(out.mmse_hard.data_ptr()), P(out.mmse_llr.data_ptr()),
+            flags]
+    assert lib.mpnl_detect_slot(ctx, ctypes.byref(d), ctypes.c_float(sl.sigma2), *args,
+                                P(ws.data_ptr()), nbytes, P(st.cuda_stream)) == mpnl.OK
+    st.synchronize()
+    mpnl.check_status()
+    ref = mpnl.SlotBuffers(sl.n_sc, 14, sl.nr, sl.nt, sl.qam, n_pe, dev, mmse=True)
+    mpnl.run_slot(ref, H.to(dev), Y.to(dev), sl.sigma2, mmse=True, precision=precision,
+                  mmse_qr=mmse_qr)
+    torch.cuda.synchronize()
+    for name, v in out.as_dict().items():
+        assert torch.equal(v, getattr(ref, name).cpu()), name
+    # a workspace too small, or not 256-byte aligned, is refused before anything runs
+    assert lib.mpnl_detect_slot(ctx, ctypes.byref(d), ctypes.c_float(sl.sigma2), *args,
+                                P(ws.data_ptr()), nbytes - 1, P(st.cuda_stream)) \
+        == mpnl.ERR_INVALID_ARG
+    assert lib.mpnl_detect_slot(ctx, ctypes.byref(d), ctypes.c_float(sl.sigma2), *args,
+                                P(ws.data_ptr() + 16), nbytes, P(st.cuda_stream)) \
+        == mpnl.ERR_INVALID_ARG
+    assert np.all(out.hard.numpy() < sl.qam)
