@@ -388,6 +388,19 @@ def run_mpnl(args):
     mpnl.check_status(local)
     lat = sorted(a.elapsed_time(b) for a, b in step_ev)
 
+    # ---- one slot in flight: the latency of a single slot through the whole
+    # path (QR + z, selection, walks; the MMSE baseline beside them on a side
+    # stream), nothing else on the device -- the figure to hold against the
+    # 0.5 ms slot
+    lat1 = []
+    b0, st0, sm0 = lanes[0]
+    for i in range(max(20, min(K, 100))):
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        lane_step(i, ev)  # lane 0 when nf == 1; else the lanes in turn, each alone
+        ev[1].synchronize()
+        lat1.append(ev[0].elapsed_time(ev[1]))
+    lat1.sort()
+
     # ---- end to end through the public host API (pinned host buffers)
     e2e_value = None
     h2d = d2h = 0
@@ -512,6 +525,7 @@ def run_mpnl(args):
             kept = []
             v, thr, n_used, dt = time_oracle(sl0, qam, n_pe, args.cpu_seconds, keep=kept)
             accuracy = accuracy_vs_oracle(sl0, kept[0], n_used, qam, n_pe, dev)
+            accuracy["per_snr"] = accuracy_per_snr(args.workload, n_pe, dev)
             v1, _, n1, dt1 = time_oracle(sl0, qam, n_pe, args.cpu_seconds / 3, n_threads=1)
             cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{n_used} of {n_sc} subcarriers x 14 symbols of one slot "
@@ -530,7 +544,12 @@ def run_mpnl(args):
                               f"H+Y > 129 MB L2"),
             "gb_per_s": value * nt * B / 1e9,
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                           "max": lat[-1], "deadline": 0.5},
+                           "max": lat[-1], "deadline": 0.5,
+                           "note": f"per step with {nf} slots in flight (throughput mode)"},
+            "latency_one_in_flight_ms": {
+                "p50": lat1[len(lat1) // 2], "p99": lat1[min(len(lat1) - 1, int(0.99 * len(lat1)))],
+                "max": lat1[-1], "deadline": 0.5, "slots": len(lat1),
+                "note": "one slot at a time through the whole path, synchronised after each"},
             "roofline": {"bound": "alu", "kernel": "detect_walk_kernel",
                          "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
                          "frac": achieved_tflops / peak_tflops, "traffic": traffic,
@@ -550,7 +569,9 @@ def run_mpnl(args):
             "cpu_baseline": cpu,
             "e2e": None if e2e_value is None else
                    {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+                    "d2h_bytes_per_step": d2h,
+                    "path": f"mpnl_detect_slot (C ABI) on pinned host buffers, {nf} slots in "
+                            f"flight on their own streams and workspaces"},
             "gpu_launches": 4 * K,
             "clocks": clk,
         }
@@ -696,6 +717,39 @@ def accuracy_vs_oracle(sl, ref, n_used, qam, n_pe, dev):
         if prec == "fp32":
             out["ber_mmse_gpu"] = ber(g["mmse_hard"].cpu().numpy()[:n_used])
     return out
+
+
+def accuracy_per_snr(name, n_pe, dev, n_sc: int = 96):
+    """BER of the oracle, the FP32 path and the mixed-precision walks, and the
+    two forms' decision mismatch against the oracle, at every SNR point of
+    the workload (the first n_sc subcarriers of each point's slot)."""
+    import oracle
+    from paper_2409_14355_gb300 import mpnl
+
+    import torch
+
+    w = inputs.WORKLOADS[name]
+    B = BITS[w["qam"]]
+    rows = []
+    for k, snr in enumerate(w["snrs"]):
+        sl = inputs.workload_slot(name, k, n_sc=min(n_sc, w["n_sc"]))
+        ref = oracle.detect_slot(sl.H, sl.Y, sl.sigma2, sl.qam, n_pe)
+
+        def ber(h):
+            e = sum(np.sum(((h >> (B - 1 - b)) & 1) != ((sl.labels >> (B - 1 - b)) & 1))
+                    for b in range(B))
+            return float(e / (sl.labels.size * B))
+
+        row = {"snr_db": snr, "ber_oracle": ber(ref["hard"])}
+        H = torch.from_numpy(sl.H).to(dev)
+        Y = torch.from_numpy(sl.Y).to(dev)
+        for prec in ("fp32", "fp16"):
+            g = mpnl.detect_slot(H, Y, sl.sigma2, sl.qam, n_pe, precision=prec)
+            h = g["hard"].cpu().numpy()
+            row[prec] = {"ber": ber(h), "ber_delta": ber(h) - row["ber_oracle"],
+                         "decision_mismatch": float(np.mean(np.any(h != ref["hard"], axis=-1)))}
+        rows.append(row)
+    return {"subcarriers_per_point": min(n_sc, w["n_sc"]), "points": rows}
 
 
 def run_mixed(args, dev, rank):
