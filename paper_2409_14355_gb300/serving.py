@@ -165,7 +165,7 @@ class Server:
                  max_inflight: int = 4, llr: bool = True, starve_s: float = 5e-3,
                  slots_per_ru: int = 2, keep_results: bool = False,
                  big_cost: float = 936 * 14 * 64 * 16 * 20, max_large_rounds: int | None = None,
-                 share_sms: bool = False):
+                 share_sms: bool = False, large_per_unit: bool = True):
         self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
                        else torch.device(device))
         self.mem_budget = int(mem_budget)
@@ -183,6 +183,9 @@ class Server:
         # on the serving mix it slowed the large units more than it sped up
         # the small ones
         self.share_sms = share_sms
+        # large units' rounds as per-call launches (short CTAs the small units'
+        # high-priority rounds can slip between) rather than persistent ones
+        self.large_per_unit = large_per_unit
         self.keep_results = keep_results  # copy each result out (else a view valid
         # until the RU's pool buffer is reused)
         self.rus: dict[int, RU] = {}
@@ -363,6 +366,10 @@ class Server:
         big = any(self.rus[q.ru].cost >= self.big_cost for q in reqs)
         r.big = big
         st = r.stream_for(big)
+        if big and self.large_per_unit:
+            self._launch_per_unit(r, reqs, st, t_adm)
+            self._finish_launch(r, reqs, nbytes)
+            return True
         n = 0
         with torch.cuda.stream(st):
             # channel updates first in the item list (the batch runs stages in
@@ -410,6 +417,43 @@ class Server:
                         q.bufs.llr_host.copy_(q.bufs.llr, non_blocking=True)
             r.event = torch.cuda.Event()
             r.event.record(st)
+        self._finish_launch(r, reqs, nbytes)
+        return True
+
+    def _launch_per_unit(self, r: _Round, reqs, st, t_adm: float) -> None:
+        """A large units' round as plain per-call launches (one CTA per
+        subcarrier in the walks) instead of the persistent batch kernels:
+        their CTAs are short, so the small units' rounds on the high-priority
+        streams take SMs as the large units' CTAs retire instead of waiting
+        for a persistent launch to drain."""
+        with torch.cuda.stream(st):
+            for q in sorted(reqs, key=lambda q: q.kind != "channel"):
+                ru = self.rus[q.ru]
+                s_ = ru.state
+                q.admitted = t_adm
+                s2 = ru.sigma2 if ru.mmse_qr else None
+                if q.kind == "channel":
+                    ru.H_dev.copy_(q.payload, non_blocking=True)
+                    mpnl.factor(ru.H_dev, s2, out=(s_["Q"], s_["R"], s_["inv_diag"], s_["perm"]))
+                    if ru.precision == "fp16":
+                        mpnl.refine_qr(ru.H_dev, None, s_["R"], s_["inv_diag"], s_["perm"],
+                                       Q=s_["Q"], sigma2=s2, cond_threshold=REFINE_COND)
+                    mpnl.select_paths(s_["R"], ru.sigma2, ru.qam, ru.n_pe, ru.nt, out=s_["paths"])
+                else:
+                    b = ru.pool.pop()
+                    q.bufs = b
+                    b.Y.copy_(q.payload, non_blocking=True)
+                    mpnl.qhy(s_["Q"], b.Y, out=b.Z, precision=ru.precision)
+                    mpnl.detect(s_["R"], s_["inv_diag"], s_["perm"], s_["paths"], b.Z, ru.sigma2,
+                                ru.qam, want_llr=b.llr is not None, want_ped2=False,
+                                out=(b.hard, b.llr, None), precision=ru.precision)
+                    b.hard_host.copy_(b.hard, non_blocking=True)
+                    if b.llr is not None:
+                        b.llr_host.copy_(b.llr, non_blocking=True)
+            r.event = torch.cuda.Event()
+            r.event.record(st)
+
+    def _finish_launch(self, r: _Round, reqs, nbytes: int) -> None:
         self.n_rounds += 1
         r.round_id = self.n_rounds
         for q in reqs:
@@ -421,7 +465,6 @@ class Server:
         self.in_use += nbytes
         self.peak_in_use = max(self.peak_in_use, self.in_use)
         self.round_sizes.append(len(reqs))
-        return True
 
     def step(self) -> None:
         self.poll()
