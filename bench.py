@@ -492,21 +492,8 @@ def run_mpnl(args):
         serving_res = run_serving(args, dev)
 
     # ---- measured FP32 FMA throughput (probe kernel), beside the derived peak
-    probe_tflops = None
     props = torch.cuda.get_device_properties(dev)
-    n_blk = props.multi_processor_count * 8
-    pout = torch.empty(n_blk * 256, dtype=torch.float32, device=dev)
-    best = None
-    for _ in range(6):
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        fl = mpnl.probe_ffma(n_blk, 8192, pout)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        t = a0.elapsed_time(a1) / 1e3
-        best = t if best is None else min(best, t)
-    probe_tflops = fl / best / 1e12
+    probe_tflops = ffma_probe_tflops(dev, stream, props.multi_processor_count * 8)
 
     # ---- roofline of the dominant kernel (walk kernel, FP32 ALU bound)
     sm_max = clk.get("sm_max_mhz") or 2070.0
@@ -580,6 +567,37 @@ def run_mpnl(args):
         dist.barrier()
         dist.destroy_process_group()
     return 0
+
+
+def ffma_probe_tflops(dev, stream, n_blk: int, iters: int = 8192, reps: int = 6) -> float:
+    """FP32 FMA rate of the probe kernel of libmpnl_bench.so (8 independent
+    fmaf chains per thread), best of `reps` launches timed with CUDA events."""
+    import ctypes
+
+    import torch
+
+    from paper_2409_14355_gb300 import build as cuda_build
+
+    lib = ctypes.CDLL(cuda_build.BENCH_LIB)
+    lib.mpnl_bench_ffma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                          ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    lib.mpnl_bench_ffma_probe.restype = ctypes.c_int
+    out = torch.empty(n_blk * 256, dtype=torch.float32, device=dev)
+    fl = ctypes.c_double(0.0)
+    best = None
+    for _ in range(reps):
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        st = lib.mpnl_bench_ffma_probe(n_blk, iters, ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.byref(fl), ctypes.c_void_p(stream.cuda_stream))
+        a1.record(stream)
+        torch.cuda.synchronize()
+        if st != 0:
+            raise RuntimeError(f"FMA probe failed ({st})")
+        t = a0.elapsed_time(a1) / 1e3
+        best = t if best is None else min(best, t)
+    return fl.value / best / 1e12
 
 
 def run_rank_lut(args, dev, n_pe):

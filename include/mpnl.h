@@ -499,18 +499,6 @@ int mpnl_set_tuning(mpnl_ctx *ctx, const mpnl_tuning *tuning);
 /* Copy this context's knobs to *tuning (zeros for built-in choices). */
 int mpnl_get_tuning(mpnl_ctx *ctx, mpnl_tuning *tuning);
 
-/* Measurement helper, not part of the detector (the paper has no
- * counterpart): enqueue an FP32 FMA throughput kernel of n_blocks CTAs of 256
- * threads, each thread running 8 independent fmaf chains for `iters` rounds,
- * and store the number of floating-point operations it performs (2 per fmaf)
- * in *flops.  `out` is device memory of n_blocks * 256 floats (overwritten
- * with the chain sums).  Timing it with events on `stream` gives the measured
- * FP32 peak beside the one derived from SM count and clock.
- * Errors: MPNL_ERR_INVALID_ARG (n_blocks < 1, iters < 1, NULL or host
- * `out`/`flops`), MPNL_ERR_CUDA. */
-int mpnl_probe_ffma(mpnl_ctx *ctx, int n_blocks, int iters, float *out, double *flops,
-                    void *stream);
-
 #ifdef __cplusplus
 }
 #endif

@@ -2,7 +2,8 @@
 
 Each .cu file is compiled in parallel to an object under ``_build/`` and the
 objects are linked into ``paper_2409_14355_gb300/libmpnl.so`` (in-tree, not
-installed).  ``python -m paper_2409_14355_gb300.build [-v]`` rebuilds it;
+installed); the benchmark's FP32 FMA probe (``bench/``) goes into a library
+of its own, ``libmpnl_bench.so``.  ``python -m paper_2409_14355_gb300.build [-v]`` rebuilds it;
 ``-v`` also prints ptxas register / shared-memory usage.
 """
 from __future__ import annotations
@@ -17,6 +18,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OBJ = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmpnl.so")
+# the benchmark's measurement helpers, kept out of the detector's library
+BENCH_SRC = os.path.join(PKG, "bench")
+BENCH_LIB = os.path.join(PKG, "libmpnl_bench.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,6 +43,10 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def bench_sources() -> list[str]:
+    return sorted(os.path.join(BENCH_SRC, f) for f in os.listdir(BENCH_SRC) if f.endswith(".cu"))
+
+
 def _deps() -> list[str]:
     out = [os.path.join(INCLUDE, "mpnl.h")]
     out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
@@ -57,10 +65,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     deps = _deps()
     jobs = []
-    objs = []
-    for src in sources():
+    objs, bench_objs = [], []
+    for src in sources() + bench_sources():
         obj = os.path.join(OBJ, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
+        (bench_objs if os.path.dirname(src) == BENCH_SRC else objs).append(obj)
         if force or verbose or _stale(obj, [src] + deps):
             cmd = [nvcc, *ARCH, *FLAGS, "-c", src, "-o", obj]
             if verbose:
@@ -78,10 +86,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed: {' '.join(cmd)}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
-        subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-        os.replace(tmp, LIB)
+    for lib, ob in ((LIB, objs), (BENCH_LIB, bench_objs)):
+        if force or jobs or _stale(lib, ob):
+            tmp = lib + f".tmp{os.getpid()}"
+            subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *ob], check=True)
+            os.replace(tmp, lib)
     return LIB
 
 

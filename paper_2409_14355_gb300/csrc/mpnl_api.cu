@@ -948,22 +948,6 @@ int mpnl_get_tuning(mpnl_ctx *ctx, mpnl_tuning *t)
     return MPNL_OK;
 }
 
-int mpnl_probe_ffma(mpnl_ctx *ctx, int n_blocks, int iters, float *out, double *flops,
-                    void *stream)
-{
-    MPNL_TRY(begin(ctx));
-    if (!flops) return fail(ctx, MPNL_ERR_INVALID_ARG, "flops is NULL");
-    if (n_blocks < 1 || iters < 1)
-        return fail(ctx, MPNL_ERR_INVALID_ARG, "n_blocks=%d, iters=%d must be >= 1", n_blocks, iters);
-    // at most ~1e13 flop (about a tenth of a second): the probe never runs long
-    const double f = mpnl::ffma_probe_flops(n_blocks, iters);
-    if (f > 1e13) return fail(ctx, MPNL_ERR_INVALID_ARG, "probe of %.3g flop exceeds 1e13", f);
-    MPNL_TRY(check_ptr(ctx, out, 4, "out", false));
-    cudaError_t e = mpnl::launch_ffma_probe(n_blocks, iters, out, (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(ctx, "ffma probe launch", e);
-    *flops = f;
-    return MPNL_OK;
-}
 
 }  // extern "C"
 

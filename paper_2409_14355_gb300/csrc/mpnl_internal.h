@@ -96,10 +96,6 @@ cudaError_t launch_mmse(int n_sc, int n_sym, int nr, int nt, int qam, float sigm
                         const float2 *H, const float2 *Y, uint8_t *hard, float *llr,
                         cudaStream_t stream);
 
-// FP32 FMA throughput probe (mpnl_probe_ffma): 256-thread CTAs.
-cudaError_t launch_ffma_probe(int n_blocks, int iters, float *out, cudaStream_t stream);
-double ffma_probe_flops(int n_blocks, int iters);
-
 // One radio unit's slot in a batch (mpnl_batch_*), as the persistent kernels
 // read it from device memory.  The work items of a stage are the
 // subcarriers of the units taking part in it; the stage's start[] holds

@@ -37,7 +37,7 @@ ERR_TIMEOUT = -4
 EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_bytes",
             "mpnl_preprocess", "mpnl_preprocess_mmse", "mpnl_select_paths", "mpnl_detect",
             "mpnl_detect_mixed",
-            "mpnl_linear_mmse", "mpnl_check_status", "mpnl_probe_ffma", "mpnl_set_tuning",
+            "mpnl_linear_mmse", "mpnl_check_status", "mpnl_set_tuning",
             "mpnl_get_tuning", "mpnl_batch_create", "mpnl_batch_run", "mpnl_batch_destroy",
             "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr",
             "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs",
@@ -145,8 +145,6 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_linear_mmse.restype = I
         lib.mpnl_check_status.argtypes = [P, P]
         lib.mpnl_check_status.restype = I
-        lib.mpnl_probe_ffma.argtypes = [P, I, I, P, ctypes.POINTER(ctypes.c_double), P]
-        lib.mpnl_probe_ffma.restype = I
         lib.mpnl_batch_create.argtypes = [P, ctypes.POINTER(BatchItemC), I,
                                           ctypes.POINTER(ctypes.c_void_p)]
         lib.mpnl_batch_create.restype = I
@@ -554,18 +552,6 @@ def get_tuning(device: int | None = None) -> Tuning:
     t = Tuning()
     _raise(load_library().mpnl_get_tuning(ctx, ctypes.byref(t)), ctx)
     return t
-
-
-def probe_ffma(n_blocks: int, iters: int, out: torch.Tensor) -> float:
-    """Enqueue the FP32 FMA throughput probe on the current stream (measurement
-    helper, not part of the detector); returns the flops it performs."""
-    dev = out.device
-    _need(out, torch.float32, (n_blocks * 256,), "out")
-    ctx = context(dev.index)
-    f = ctypes.c_double(0.0)
-    _raise(load_library().mpnl_probe_ffma(ctx, int(n_blocks), int(iters), _ptr(out),
-                                          ctypes.byref(f), _stream(dev)), ctx)
-    return f.value
 
 
 class SlotBuffers:

@@ -48,8 +48,6 @@ def test_host_side_errors_without_gpu(lib):
                            ctypes.c_float(1.0), None, None, None, None, None) == mpnl.ERR_INVALID_ARG
     assert lib.mpnl_create(None, 0) == mpnl.ERR_INVALID_ARG
     assert lib.mpnl_workspace_bytes(ctypes.byref(d)) == 0
-    f = ctypes.c_double(0.0)
-    assert lib.mpnl_probe_ffma(None, 1, 1, None, ctypes.byref(f), None) == mpnl.ERR_INVALID_ARG
     lib.mpnl_destroy(None)
 
 
@@ -108,3 +106,15 @@ def test_header_is_plain_c():
         r = subprocess.run([cc, "-fsyntax-only", "-Wall", "-Wextra", "-Werror", *std, hdr],
                            capture_output=True, text=True)
         assert r.returncode == 0, r.stderr
+
+
+def test_bench_probe_lives_outside_the_detector_library(lib):
+    # the FP32 FMA probe is a benchmark helper in libmpnl_bench.so; the
+    # detector's library does not export it
+    assert not hasattr(lib, "mpnl_probe_ffma")
+    b = ctypes.CDLL(cuda_build.BENCH_LIB)
+    b.mpnl_bench_ffma_probe.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_double), ctypes.c_void_p]
+    f = ctypes.c_double(0.0)
+    assert b.mpnl_bench_ffma_probe(0, 1, None, ctypes.byref(f), None) == -1
+

@@ -154,18 +154,3 @@ def test_mixed_and_fp32_agree_on_most_decisions(dev):
     h16, _, _ = mpnl.detect(R, inv_diag, perm, paths, Z, sl.sigma2, 64, precision="fp16")
     agree = torch.all(h32 == h16, dim=-1).float().mean().item()
     assert agree >= 0.95, agree
-
-
-def test_ffma_probe_runs_and_counts_its_flops(dev):
-    # measurement helper used for the roofline's measured FP32 peak
-    from paper_2409_14355_gb300 import mpnl
-    out = torch.empty(3 * 256, dtype=torch.float32, device=dev)
-    fl = mpnl.probe_ffma(3, 100, out)
-    torch.cuda.synchronize()
-    assert fl == 2 * 8 * 256 * 3 * 100
-    v = out.cpu().numpy()
-    assert np.all(np.isfinite(v)) and np.all(v > 0)
-    with pytest.raises(mpnl.MpnlError):
-        mpnl.probe_ffma(0, 100, torch.empty(0, dtype=torch.float32, device=dev))
-    with pytest.raises(mpnl.MpnlError):
-        mpnl.probe_ffma(3, 10 ** 9, out)            # more than 1e13 flop
