@@ -138,3 +138,31 @@ def test_geometric_costs_in_a_table_reproduce_the_geometric_model(nt, M, n_pe):
     ok = np.concatenate([[True], sep]) & np.concatenate([sep, [True]])
     assert ok.mean() > 0.8
     np.testing.assert_array_equal(paths_t[ok], paths_g[ok])
+
+
+def test_unseen_rank_tail_recovers_a_halving_law_truncated_by_sampling():
+    # A source whose rank probabilities halve from rank to rank (P(k) =
+    # 2^-k, renormalised over 16 ranks) sampled with few trials: the deep
+    # ranks are never seen.  The true costs are c(k) = (k - 1) ln 2 at every
+    # rank; the histogram gives them (up to sampling noise) where it saw
+    # ranks, and the tail rule must give them where it did not -- checked
+    # against the law itself, not against the rule's own formula.  Counts
+    # drawn from the law by the inverse-CDF of a seeded generator.
+    rng = np.random.default_rng(17)
+    M, trials = 16, 4000
+    p = 0.5 ** np.arange(1, M + 1)
+    p /= p.sum()
+    draws = rng.choice(M, size=trials, p=p)
+    counts = np.bincount(draws, minlength=M).astype(np.int64)[None, :]
+    seen = int(np.max(np.nonzero(counts[0])[0])) + 1
+    assert seen < M - 2                      # the tail really is unseen
+    cost = oracle.rank_costs(counts, trials)[0]
+    true = np.arange(M) * math.log(2.0)
+    # seen ranks: within the sampling error of the true cost (rank counts of a
+    # few hundred: a few tenths in log)
+    first = [k for k in range(seen) if counts[0, k] >= 30]
+    np.testing.assert_allclose(cost[first], true[first], atol=0.35)
+    # unseen ranks: the law's step, exactly, from the last seen rank on
+    np.testing.assert_allclose(np.diff(cost[seen - 1:]), np.diff(true[seen - 1:]), rtol=1e-12)
+    # and the extrapolated costs stay within the sampling error of the truth
+    assert np.all(np.abs(cost[seen:] - true[seen:]) <= 1.5)
