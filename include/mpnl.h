@@ -397,6 +397,12 @@ typedef struct {
  * launches): the walk stage runs one CTA per SM fewer than tuned (at least
  * one), the other stages half their workers; results are unchanged */
 #define MPNL_RUN_SHARE_SMS 64
+/* every CTA of every stage takes one work item (as many CTAs as items)
+ * instead of a persistent grid drawing items until they run out: short CTAs
+ * that the hardware spreads over whatever SMs free up, for a latency-bound
+ * batch that shares the GPU with longer work (a serving loop's small units
+ * beside a large unit's walks); results are unchanged */
+#define MPNL_RUN_SHORT_CTAS 128
 #define MPNL_STAGE_QHY 32
 #define MPNL_STAGES_ALL 47
 
@@ -427,7 +433,7 @@ int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *batch, const mpnl_batch_item *it
                      int n_items, int flags);
 
 /* Enqueue the stages in `stages` (MPNL_STAGE_* bits, in pipeline order,
- * optionally with MPNL_RUN_GRAPH and MPNL_RUN_SHARE_SMS) on `stream`; with
+ * optionally with MPNL_RUN_GRAPH, MPNL_RUN_SHARE_SMS, MPNL_RUN_SHORT_CTAS) on `stream`; with
  * MPNL_RUN_GRAPH the stream must not be the legacy default stream (NULL).  Device-side argument errors go to mpnl_check_status. */
 int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *batch, int stages, void *stream);
 

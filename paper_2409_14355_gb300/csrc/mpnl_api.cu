@@ -144,7 +144,7 @@ int begin(mpnl_ctx *ctx)
 // Stage slots of a batch, in execution order.
 // The FP64 refinement (units with MPNL_ITEM_REFINE_QR) runs with the QR stage.
 enum BatchStage { kBPre, kBRef, kBSel, kBQhy, kBDet, kBMmse, kBStages };
-constexpr int kGraphSlots = 2 * (MPNL_STAGES_ALL + 1);
+constexpr int kGraphSlots = 4 * (MPNL_STAGES_ALL + 1);
 static const int kStageBit[kBStages] = {MPNL_STAGE_PREPROCESS, MPNL_STAGE_PREPROCESS,
                                         MPNL_STAGE_SELECT,     MPNL_STAGE_QHY,
                                         MPNL_STAGE_DETECT,     MPNL_STAGE_MMSE};
@@ -168,7 +168,7 @@ struct mpnl_batch {
     size_t det_smem;
     int sel_warps, det_ctas;
     int sms;
-    cudaGraphExec_t graph[kGraphSlots];  // by stage mask, and MPNL_RUN_SHARE_SMS
+    cudaGraphExec_t graph[kGraphSlots];  // by stage mask, MPNL_RUN_SHARE_SMS, MPNL_RUN_SHORT_CTAS
 };
 
 namespace {
@@ -358,10 +358,21 @@ int upload_batch(mpnl_ctx *ctx, mpnl_batch *b, cudaStream_t st)
 // share: leave room on every SM for other work (MPNL_RUN_SHARE_SMS): the walk
 // stage runs one CTA per SM fewer than tuned (at least one), the warp- and
 // group-worker stages half their workers.
-int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st, bool share)
+// shorts: one item per walk CTA and per warp worker (MPNL_RUN_SHORT_CTAS).
+int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st, bool share,
+                  bool shorts = false)
 {
     const int workers = share ? b->sms * 2 : b->sms * 4;
     const int det_ctas = share && b->det_ctas > 1 ? b->det_ctas - 1 : b->det_ctas;
+    // CTAs of each stage: persistent (a fixed number per SM, drawing items
+    // from the counter until it runs out), or with MPNL_RUN_SHORT_CTAS as many
+    // as the stage has items (warp stages: 4 warps per CTA), so that every
+    // CTA is short and the hardware spreads them over whatever SMs free up
+    auto grid_of = [&](int q, int persistent, int per_cta) {
+        if (!shorts) return persistent;
+        const long long g = ((long long)b->stage_units[q] + per_cta - 1) / per_cta;
+        return (int)std::min<long long>(std::max<long long>(g, 1), 1 << 24);
+    };
     cudaError_t e = cudaMemsetAsync(b->d_counters, 0, kBStages * sizeof(int), st);
     if (e != cudaSuccess) return cuda_fail(ctx, "batch counter reset", e);
     const int cap1 = b->capacity + 1;
@@ -370,32 +381,34 @@ int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st, boo
     const int n = b->n_items;
     if ((stages & MPNL_STAGE_PREPROCESS) && b->stage_units[kBPre]) {
         e = mpnl::launch_preprocess_batch(b->d_items, start[kBPre], n, b->d_counters + kBPre,
-                                          b->pre_warp_bytes, workers, st);
+                                          b->pre_warp_bytes, grid_of(kBPre, workers, 4), st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch preprocess launch", e);
     }
     if ((stages & MPNL_STAGE_PREPROCESS) && b->stage_units[kBRef]) {
         e = mpnl::launch_refine_batch(b->d_items, start[kBRef], n, b->d_counters + kBRef,
-                                      b->ref_warp_bytes, workers, st);
+                                      b->ref_warp_bytes, grid_of(kBRef, workers, 2), st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch refine launch", e);
     }
     if ((stages & MPNL_STAGE_SELECT) && b->stage_units[kBSel]) {
         e = mpnl::launch_select_batch(b->d_items, start[kBSel], n, b->d_counters + kBSel,
-                                      b->sel_group_bytes, b->sel_warps, workers, st);
+                                      b->sel_group_bytes, b->sel_warps,
+                                      grid_of(kBSel, workers, 4 / b->sel_warps), st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch select launch", e);
     }
     if ((stages & MPNL_STAGE_QHY) && b->stage_units[kBQhy]) {
         e = mpnl::launch_qhy_batch(b->d_items, start[kBQhy], n, b->d_counters + kBQhy,
-                                   b->qhy_warp_bytes, workers, st);
+                                   b->qhy_warp_bytes, grid_of(kBQhy, workers, 4), st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch qhy launch", e);
     }
     if ((stages & MPNL_STAGE_DETECT) && b->stage_units[kBDet]) {
         e = mpnl::launch_detect_batch(b->d_items, start[kBDet], n, b->d_counters + kBDet,
-                                      ctx->status, b->det_smem, b->sms * det_ctas, st);
+                                      ctx->status, b->det_smem, grid_of(kBDet, b->sms * det_ctas, 1),
+                                      st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch detect launch", e);
     }
     if ((stages & MPNL_STAGE_MMSE) && b->stage_units[kBMmse]) {
         e = mpnl::launch_mmse_batch(b->d_items, start[kBMmse], n, b->d_counters + kBMmse,
-                                    b->mmse_warp_bytes, workers, st);
+                                    b->mmse_warp_bytes, grid_of(kBMmse, workers, 4), st);
         if (e != cudaSuccess) return cuda_fail(ctx, "batch mmse launch", e);
     }
     return MPNL_OK;
@@ -460,19 +473,20 @@ int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *b, int stages, void *stream)
     if (b->device != ctx->device)
         return fail(ctx, MPNL_ERR_INVALID_ARG, "batch lives on device %d, context on %d", b->device,
                     ctx->device);
-    if (stages & ~(MPNL_STAGES_ALL | MPNL_RUN_GRAPH | MPNL_RUN_SHARE_SMS))
+    if (stages & ~(MPNL_STAGES_ALL | MPNL_RUN_GRAPH | MPNL_RUN_SHARE_SMS | MPNL_RUN_SHORT_CTAS))
         return fail(ctx, MPNL_ERR_INVALID_ARG, "unknown stage bits 0x%x", stages);
     const int mask = stages & MPNL_STAGES_ALL;
     const bool share = (stages & MPNL_RUN_SHARE_SMS) != 0;
-    const int slot = mask + (share ? MPNL_STAGES_ALL + 1 : 0);
+    const bool shorts = (stages & MPNL_RUN_SHORT_CTAS) != 0;
+    const int slot = mask + (share ? MPNL_STAGES_ALL + 1 : 0) + (shorts ? 2 * (MPNL_STAGES_ALL + 1) : 0);
     cudaStream_t st = (cudaStream_t)stream;
     MPNL_TRY(upload_batch(ctx, b, st));
-    if (!(stages & MPNL_RUN_GRAPH)) return enqueue_batch(ctx, b, mask, st, share);
+    if (!(stages & MPNL_RUN_GRAPH)) return enqueue_batch(ctx, b, mask, st, share, shorts);
     if (!st) return fail(ctx, MPNL_ERR_INVALID_ARG, "graph capture needs a non-default stream");
     if (!b->graph[slot]) {
         cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return cuda_fail(ctx, "graph capture begin", e);
-        const int rc = enqueue_batch(ctx, b, mask, st, share);
+        const int rc = enqueue_batch(ctx, b, mask, st, share, shorts);
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(st, &g);
         if (rc != MPNL_OK) {

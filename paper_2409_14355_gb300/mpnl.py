@@ -48,6 +48,7 @@ STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8
 STAGES_ALL = 47
 RUN_GRAPH = 16
 RUN_SHARE_SMS = 64
+RUN_SHORT_CTAS = 128
 RESET_TRUSTED_POINTERS = 1
 NOALLOC_MAX_UNITS = 64
 SLOT_MMSE, SLOT_FP16, SLOT_MMSE_QR = 1, 2, 4
@@ -808,12 +809,15 @@ class Batch:
                self._ctx)
 
     def run(self, stages: int = STAGES_ALL, graph: bool = False, stream=None,
-            share_sms: bool = False) -> None:
+            share_sms: bool = False, short_ctas: bool = False) -> None:
         """Enqueue the stages on `stream` (default: the current stream; a
         graph needs a non-default stream).  share_sms leaves room on every SM
-        for other streams' work (MPNL_RUN_SHARE_SMS)."""
+        for other streams' work (MPNL_RUN_SHARE_SMS); short_ctas launches one
+        CTA (or warp) per work item instead of persistent ones
+        (MPNL_RUN_SHORT_CTAS)."""
         st = stream if stream is not None else torch.cuda.current_stream(self.device)
-        flags = stages | (RUN_GRAPH if graph else 0) | (RUN_SHARE_SMS if share_sms else 0)
+        flags = stages | (RUN_GRAPH if graph else 0) | (RUN_SHARE_SMS if share_sms else 0) \
+            | (RUN_SHORT_CTAS if short_ctas else 0)
         _raise(load_library().mpnl_batch_run(self._ctx, self._h, flags,
                                              ctypes.c_void_p(st.cuda_stream)), self._ctx)
 

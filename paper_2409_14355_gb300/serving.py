@@ -165,7 +165,8 @@ class Server:
                  max_inflight: int = 4, llr: bool = True, starve_s: float = 5e-3,
                  slots_per_ru: int = 2, keep_results: bool = False,
                  big_cost: float = 936 * 14 * 64 * 16 * 20, max_large_rounds: int | None = None,
-                 share_sms: bool = False, large_per_unit: bool = True):
+                 share_sms: bool = False, large_per_unit: bool = True,
+                 small_short_ctas: bool = True):
         self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
                        else torch.device(device))
         self.mem_budget = int(mem_budget)
@@ -186,6 +187,10 @@ class Server:
         # large units' rounds as per-call launches (short CTAs the small units'
         # high-priority rounds can slip between) rather than persistent ones
         self.large_per_unit = large_per_unit
+        # small units' rounds with one CTA per work item (MPNL_RUN_SHORT_CTAS):
+        # a persistent round would do all its items on the few CTAs that find
+        # an SM free beside the large units' walks
+        self.small_short_ctas = small_short_ctas
         self.keep_results = keep_results  # copy each result out (else a view valid
         # until the RU's pool buffer is reused)
         self.rus: dict[int, RU] = {}
@@ -409,7 +414,8 @@ class Server:
                 r.batch = mpnl.Batch(items=list(items), device=dev)
             r.batch.reset((mpnl.BatchItemC * n).from_buffer(items), trusted_pointers=True)
             r.batch.run(mpnl.STAGE_PREPROCESS | mpnl.STAGE_SELECT | mpnl.STAGE_QHY |
-                        mpnl.STAGE_DETECT, stream=st, share_sms=big and self.share_sms)
+                        mpnl.STAGE_DETECT, stream=st, share_sms=big and self.share_sms,
+                        short_ctas=not big and self.small_short_ctas)
             for q in reqs:
                 if q.bufs is not None:
                     q.bufs.hard_host.copy_(q.bufs.hard, non_blocking=True)

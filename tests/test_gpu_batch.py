@@ -84,13 +84,16 @@ def test_sharing_sms_leaves_results_unchanged(dev):
     batch = mpnl.Batch(units, dev)
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
+    # leaving room on the SMs, or one CTA per work item (short CTAs) instead
+    # of persistent ones, changes how the work is spread, never the results
     for graph in (False, True):
-        with torch.cuda.stream(side):
-            batch.run(graph=graph, stream=side, share_sms=True)
-        side.synchronize()
-        mpnl.check_status()
-        for k, unit in enumerate(units):
-            _assert_same(unit, _alone(dev, unit), k)
+        for share, short in ((True, False), (False, True), (True, True)):
+            with torch.cuda.stream(side):
+                batch.run(graph=graph, stream=side, share_sms=share, short_ctas=short)
+            side.synchronize()
+            mpnl.check_status()
+            for k, unit in enumerate(units):
+                _assert_same(unit, _alone(dev, unit), k)
     batch.close()
 
 
