@@ -443,7 +443,7 @@ def run_mpnl(args):
     sweep = None
     if not args.no_sweep:
         sweep = []
-        points = [(p, args.precision) for p in (64, 128, 256) if p != n_pe and p <= qam ** nt]
+        points = [(p, args.precision) for p in (32, 64, 128, 256) if p != n_pe and p <= qam ** nt]
         points.append((n_pe, "fp16" if args.precision == "fp32" else "fp32"))
         ks = max(10, K // 4)
         for npe, prec in points:
@@ -465,9 +465,24 @@ def run_mpnl(args):
             dms = sum(x.elapsed_time(y) for x, y in ev) / ks
             v, _ = whole_job_rate(ks * dets_per_step, t, dev)
             fl = npe * (4 * nt * nt + 4 * nt) * dets_per_step
+            # one slot alone through the whole path (QR + z, selection, walks,
+            # MMSE baseline), synchronised after each: the latency against
+            # the 0.5 ms slot at this N_pe
+            one = []
+            for i in range(20):
+                x0 = torch.cuda.Event(enable_timing=True)
+                x1 = torch.cuda.Event(enable_timing=True)
+                x0.record(stream)
+                run_step(b2, npe, prec, i)
+                x1.record(stream)
+                x1.synchronize()
+                one.append(x0.elapsed_time(x1))
+            one.sort()
             sweep.append({"n_pe": npe, "precision": prec, "steps": ks, "value": v,
                           "ms_per_step": 1e3 * t / ks, "detect_ms": dms,
-                          "detect_tflops": fl / (dms / 1e3) / 1e12})
+                          "detect_tflops": fl / (dms / 1e3) / 1e12,
+                          "one_slot_ms": {"p50": one[len(one) // 2], "p99": one[-1],
+                                          "note": "20 slots, one at a time, MMSE in the same stream"}})
             del b2
 
     # ---- the table-driven rank model beside the geometric one: the table's
@@ -766,6 +781,10 @@ def accuracy_per_snr(name, n_pe, dev, n_sc: int = 96):
             h = g["hard"].cpu().numpy()
             row[prec] = {"ber": ber(h), "ber_delta": ber(h) - row["ber_oracle"],
                          "decision_mismatch": float(np.mean(np.any(h != ref["hard"], axis=-1)))}
+        # beside them: the paper's own N_p = 32 and the linear MMSE baseline
+        g32 = mpnl.detect_slot(H, Y, sl.sigma2, sl.qam, min(32, n_pe), mmse=True)
+        row["ber_n_pe_32"] = ber(g32["hard"].cpu().numpy())
+        row["ber_mmse"] = ber(g32["mmse_hard"].cpu().numpy())
         rows.append(row)
     return {"subcarriers_per_point": min(n_sc, w["n_sc"]), "points": rows}
 
