@@ -437,6 +437,38 @@ int mpnl_batch_reset(mpnl_ctx *ctx, mpnl_batch *batch, const mpnl_batch_item *it
  * MPNL_RUN_GRAPH the stream must not be the legacy default stream (NULL).  Device-side argument errors go to mpnl_check_status. */
 int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *batch, int stages, void *stream);
 
+/* One round of a serving loop in one call (a DU serving many RUs, §I and
+ * §IV): the requests' inputs copied from host buffers into device staging,
+ * the batch reset with one item per request (trusted pointers, as
+ * MPNL_RESET_TRUSTED_POINTERS), the stages run, and the slots' decisions and
+ * LLRs copied back to host buffers -- all enqueued on `stream`.  A request
+ * refers to its unit's resident state through `unit` (an mpnl_batch_item
+ * with dims, sigma2, flags and the device arrays Q, R, inv_diag, perm,
+ * paths; its other fields are ignored).  A channel update runs the sorted QR
+ * (keeping Q; with MPNL_ITEM_REFINE_QR in the unit's flags also the FP64
+ * re-factorisation) and the selection from H; a slot runs Q^H y and the
+ * walks on Y.  Channel updates are ordered before slots, so a slot of the
+ * same unit in the round sees the new state.  The batch must have room for
+ * n_reqs items and its previous round must have completed (as
+ * mpnl_batch_reset).  run_flags: 0, MPNL_RUN_SHARE_SMS, MPNL_RUN_SHORT_CTAS.
+ * Errors: as mpnl_batch_reset / mpnl_batch_run; a request without a unit,
+ * a bad kind, or a slot without its buffers. */
+#define MPNL_ROUND_SLOT 0
+#define MPNL_ROUND_CHANNEL 1
+typedef struct {
+    const mpnl_batch_item *unit;  /* the unit's state (device arrays) and sizes */
+    int kind;                     /* MPNL_ROUND_SLOT or MPNL_ROUND_CHANNEL */
+    const void *payload;          /* host (pinned) Y [n_sc][n_sym][nr], or H [n_sc][nr][nt] */
+    void *staging;                /* device buffer the payload is copied to */
+    void *Z;                      /* device c64 [n_sc][n_sym][nt] (slots) */
+    uint8_t *hard;                /* device u8 [n_sc][n_sym][nt] (slots) */
+    float *llr;                   /* device f32 [n_sc][n_sym][nt][log2 qam] (slots; nullable) */
+    uint8_t *hard_host;           /* host copy of hard (slots) */
+    float *llr_host;              /* host copy of llr (slots; nullable) */
+} mpnl_round_req;
+int mpnl_serve_round(mpnl_ctx *ctx, mpnl_batch *batch, const mpnl_round_req *reqs, int n_reqs,
+                     int run_flags, void *stream);
+
 /* Release a batch (NULL is ignored); its work must have completed. */
 void mpnl_batch_destroy(mpnl_batch *batch);
 

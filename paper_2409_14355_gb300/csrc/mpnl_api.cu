@@ -506,6 +506,84 @@ int mpnl_batch_run(mpnl_ctx *ctx, mpnl_batch *b, int stages, void *stream)
     return MPNL_OK;
 }
 
+int mpnl_serve_round(mpnl_ctx *ctx, mpnl_batch *b, const mpnl_round_req *reqs, int n_reqs,
+                     int run_flags, void *stream)
+{
+    MPNL_TRY(begin(ctx));
+    if (!b) return fail(ctx, MPNL_ERR_INVALID_ARG, "batch is NULL");
+    if (b->device != ctx->device)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "batch lives on device %d, context on %d", b->device,
+                    ctx->device);
+    if (!reqs || n_reqs < 1 || n_reqs > b->capacity)
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "n_reqs=%d outside 1..%d", n_reqs, b->capacity);
+    if (run_flags & ~(MPNL_RUN_SHARE_SMS | MPNL_RUN_SHORT_CTAS))
+        return fail(ctx, MPNL_ERR_INVALID_ARG, "unknown run flags 0x%x", run_flags);
+    // channel updates first (stable): the stages run in order, so a slot of
+    // the same unit in this round reads the new state
+    std::vector<int> order;
+    order.reserve(n_reqs);
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < n_reqs; ++i)
+            if ((reqs[i].kind == MPNL_ROUND_CHANNEL) == (pass == 0)) order.push_back(i);
+    std::vector<mpnl_batch_item> items(n_reqs);
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int k = 0; k < n_reqs; ++k) {
+        const mpnl_round_req &q = reqs[order[k]];
+        if (!q.unit || (q.kind != MPNL_ROUND_SLOT && q.kind != MPNL_ROUND_CHANNEL) || !q.payload ||
+            !q.staging)
+            return fail(ctx, MPNL_ERR_INVALID_ARG, "request %d: bad unit, kind or buffers",
+                        order[k]);
+        const mpnl_dims &d = q.unit->dims;
+        if (d.n_sc < 0 || d.n_sym < 0 || d.nr < 1 || d.nt < 1)
+            return fail(ctx, MPNL_ERR_INVALID_ARG, "request %d: bad sizes", order[k]);
+        mpnl_batch_item it = *q.unit;
+        it.H = it.Y = nullptr;
+        it.Z = nullptr;
+        it.hard = it.mmse_hard = nullptr;
+        it.llr = it.ped2 = it.mmse_llr = nullptr;
+        if (q.kind == MPNL_ROUND_CHANNEL) {
+            it.stages = MPNL_STAGE_PREPROCESS | MPNL_STAGE_SELECT;
+            it.H = q.staging;
+        } else {
+            if (!q.Z || !q.hard || !q.hard_host || (q.llr_host && !q.llr))
+                return fail(ctx, MPNL_ERR_INVALID_ARG, "request %d: slot buffers missing",
+                            order[k]);
+            it.stages = MPNL_STAGE_QHY | MPNL_STAGE_DETECT;
+            it.Y = q.staging;
+            it.Z = q.Z;
+            it.hard = q.hard;
+            it.llr = q.llr;
+        }
+        items[k] = it;
+    }
+    // everything validated: now enqueue (inputs in, the stages, results out)
+    MPNL_TRY(fill_batch(ctx, b, items.data(), n_reqs, false));
+    for (int k = 0; k < n_reqs; ++k) {
+        const mpnl_round_req &q = reqs[order[k]];
+        const mpnl_dims &d = q.unit->dims;
+        const size_t bytes = q.kind == MPNL_ROUND_CHANNEL
+                                 ? (size_t)d.n_sc * d.nr * d.nt * 8
+                                 : (size_t)d.n_sc * d.n_sym * d.nr * 8;
+        cudaError_t e = cudaMemcpyAsync(q.staging, q.payload, bytes, cudaMemcpyDefault, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "round input copy", e);
+    }
+    MPNL_TRY(upload_batch(ctx, b, st));
+    MPNL_TRY(enqueue_batch(ctx, b, MPNL_STAGES_ALL, st, (run_flags & MPNL_RUN_SHARE_SMS) != 0,
+                           (run_flags & MPNL_RUN_SHORT_CTAS) != 0));
+    for (int k = 0; k < n_reqs; ++k) {
+        const mpnl_round_req &q = reqs[order[k]];
+        if (q.kind != MPNL_ROUND_SLOT) continue;
+        const mpnl_dims &d = q.unit->dims;
+        const size_t det = (size_t)d.n_sc * d.n_sym;
+        cudaError_t e = cudaMemcpyAsync(q.hard_host, q.hard, det * d.nt, cudaMemcpyDefault, st);
+        if (e == cudaSuccess && q.llr_host)
+            e = cudaMemcpyAsync(q.llr_host, q.llr, det * d.nt * bits_of(d.qam) * 4,
+                                cudaMemcpyDefault, st);
+        if (e != cudaSuccess) return cuda_fail(ctx, "round output copy", e);
+    }
+    return MPNL_OK;
+}
+
 void mpnl_batch_destroy(mpnl_batch *b)
 {
     if (!b) return;

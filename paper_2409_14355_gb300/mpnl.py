@@ -42,7 +42,8 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_batch_reset", "mpnl_factor", "mpnl_qhy", "mpnl_refine_qr",
             "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs",
             "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd", "mpnl_qhy_mixed",
-            "mpnl_detect_units_noalloc", "mpnl_detect_slot", "mpnl_slot_workspace_bytes")
+            "mpnl_detect_units_noalloc", "mpnl_detect_slot", "mpnl_slot_workspace_bytes",
+            "mpnl_serve_round")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16, ITEM_REFINE_QR = 1, 2, 4, 8
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
@@ -86,12 +87,22 @@ class Tuning(ctypes.Structure):
                 ("persistent_select_warps", ctypes.c_uint8)]
 
 
+ROUND_SLOT, ROUND_CHANNEL = 0, 1
+
+
 class BatchItemC(ctypes.Structure):
     """mpnl_batch_item."""
     _fields_ = [("dims", Dims), ("sigma2", ctypes.c_float), ("flags", ctypes.c_int),
                 ("stages", ctypes.c_int), ("Q", ctypes.c_void_p)] + [
         (n, ctypes.c_void_p) for n in ("H", "Y", "R", "inv_diag", "perm", "Z", "paths", "hard",
                                        "llr", "ped2", "mmse_hard", "mmse_llr")]
+
+
+class RoundReqC(ctypes.Structure):
+    """mpnl_round_req: one request of a serving round (mpnl_serve_round)."""
+    _fields_ = [("unit", ctypes.POINTER(BatchItemC)), ("kind", ctypes.c_int)] + [
+        (n, ctypes.c_void_p) for n in ("payload", "staging", "Z", "hard", "llr", "hard_host",
+                                       "llr_host")]
 
 
 def problem_class(nt: int, qam: int, n_pe: int) -> tuple[int, int, int]:
@@ -165,6 +176,8 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_batch_destroy.restype = None
         lib.mpnl_detect_units_noalloc.argtypes = [ctypes.POINTER(BatchItemC), I, P]
         lib.mpnl_detect_units_noalloc.restype = I
+        lib.mpnl_serve_round.argtypes = [P, P, ctypes.POINTER(RoundReqC), I, I, P]
+        lib.mpnl_serve_round.restype = I
         lib.mpnl_slot_workspace_bytes.argtypes = [D, I]
         lib.mpnl_slot_workspace_bytes.restype = S
         lib.mpnl_detect_slot.argtypes = [P, D, F, P, P, P, P, P, P, P, I, P, S, P]
@@ -820,6 +833,13 @@ class Batch:
             | (RUN_SHORT_CTAS if short_ctas else 0)
         _raise(load_library().mpnl_batch_run(self._ctx, self._h, flags,
                                              ctypes.c_void_p(st.cuda_stream)), self._ctx)
+
+    def serve_round(self, reqs, n: int, run_flags: int = 0, stream=None) -> None:
+        """One serving round in one C call (mpnl_serve_round): `reqs` is a
+        RoundReqC array whose first n entries are this round's requests."""
+        st = stream if stream is not None else torch.cuda.current_stream(self.device)
+        _raise(load_library().mpnl_serve_round(self._ctx, self._h, reqs, int(n), int(run_flags),
+                                               ctypes.c_void_p(st.cuda_stream)), self._ctx)
 
     def close(self) -> None:
         if getattr(self, "_h", None):

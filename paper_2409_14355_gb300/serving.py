@@ -35,6 +35,7 @@ kernels behind the C ABI (mpnl.py).
 from __future__ import annotations
 
 import collections
+import ctypes
 import time
 from dataclasses import dataclass, field
 
@@ -67,6 +68,7 @@ class RU:
     busy_rounds: set = field(default_factory=set)
     update_round: int = -1    # round of the RU's channel update in flight (-1: none)
     gone: bool = False        # deregistered; state released when its rounds retire
+    item: object = None       # the resident state as an mpnl_batch_item (rounds refer to it)
     pool: list = field(default_factory=list)    # free per-slot buffer sets
     H_dev: torch.Tensor | None = None           # device staging of a channel update
 
@@ -166,7 +168,7 @@ class Server:
                  slots_per_ru: int = 2, keep_results: bool = False,
                  big_cost: float = 936 * 14 * 64 * 16 * 20, max_large_rounds: int | None = None,
                  share_sms: bool = False, large_per_unit: bool = True,
-                 small_short_ctas: bool = True):
+                 small_short_ctas: bool = True, native_rounds: bool = True):
         self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
                        else torch.device(device))
         self.mem_budget = int(mem_budget)
@@ -191,6 +193,8 @@ class Server:
         # a persistent round would do all its items on the few CTAs that find
         # an SM free beside the large units' walks
         self.small_short_ctas = small_short_ctas
+        # rounds after a batch's first as one native call (mpnl_serve_round)
+        self.native_rounds = native_rounds
         self.keep_results = keep_results  # copy each result out (else a view valid
         # until the RU's pool buffer is reused)
         self.rus: dict[int, RU] = {}
@@ -219,6 +223,9 @@ class Server:
         ru.state = st
         ru.pool = [SlotBuffers(ru, dev, self.llr) for _ in range(self.slots_per_ru)]
         ru.H_dev = torch.empty((n_sc, nr, nt), dtype=torch.complex64, device=dev)
+        # the unit's resident state as a batch item: what a round's request refers to
+        ru.item = mpnl.batch_item(ru.dims, ru.sigma2, self._unit_flags(ru), 0, Q=st["Q"], R=st["R"],
+                                  inv_diag=st["inv_diag"], perm=st["perm"], paths=st["paths"])
         Hd = H.to(dev)
         mpnl.factor(Hd, ru.sigma2 if ru.mmse_qr else None,
                     out=(st["Q"], st["R"], st["inv_diag"], st["perm"]))
@@ -229,6 +236,11 @@ class Server:
         torch.cuda.synchronize(dev)
         self.rus[ru.ru_id] = ru
         self.state_bytes += ru.state_bytes()
+
+    @staticmethod
+    def _unit_flags(ru: RU) -> int:
+        return (mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0) \
+            | (mpnl.ITEM_FP16 | mpnl.ITEM_REFINE_QR if ru.precision == "fp16" else 0)
 
     def now(self) -> float:
         return time.perf_counter() - self.t0
@@ -375,6 +387,10 @@ class Server:
             self._launch_per_unit(r, reqs, st, t_adm)
             self._finish_launch(r, reqs, nbytes)
             return True
+        if r.batch is not None and self.native_rounds:
+            self._launch_native(r, reqs, st, t_adm, big)
+            self._finish_launch(r, reqs, nbytes)
+            return True
         n = 0
         with torch.cuda.stream(st):
             # channel updates first in the item list (the batch runs stages in
@@ -387,8 +403,7 @@ class Server:
                 n += 1
                 it.dims = mpnl.Dims(*ru.dims)
                 it.sigma2 = ru.sigma2
-                it.flags = (mpnl.ITEM_MMSE_QR if ru.mmse_qr else 0) \
-                    | (mpnl.ITEM_FP16 | mpnl.ITEM_REFINE_QR if ru.precision == "fp16" else 0)
+                it.flags = self._unit_flags(ru)
                 it.Q, it.R = s_["Q"].data_ptr(), s_["R"].data_ptr()
                 it.inv_diag, it.perm = s_["inv_diag"].data_ptr(), s_["perm"].data_ptr()
                 it.paths = s_["paths"].data_ptr()
@@ -425,6 +440,37 @@ class Server:
             r.event.record(st)
         self._finish_launch(r, reqs, nbytes)
         return True
+
+    def _launch_native(self, r: _Round, reqs, st, t_adm: float, big: bool) -> None:
+        """A round as one mpnl_serve_round call: the inputs' copies, the
+        batch's descriptors, the stages and the results' copies are all
+        enqueued by the library; this side only names each request's buffers."""
+        if getattr(r, "reqs_c", None) is None:
+            r.reqs_c = (mpnl.RoundReqC * self.max_units)()
+        rc = r.reqs_c
+        for k, q in enumerate(reqs):
+            ru = self.rus[q.ru]
+            q.admitted = t_adm
+            c = rc[k]
+            c.unit = ctypes.pointer(ru.item)
+            c.payload = q.payload.data_ptr()
+            if q.kind == "channel":
+                c.kind = mpnl.ROUND_CHANNEL
+                c.staging = ru.H_dev.data_ptr()
+                c.Z = c.hard = c.llr = c.hard_host = c.llr_host = None
+            else:
+                b = ru.pool.pop()
+                q.bufs = b
+                c.kind = mpnl.ROUND_SLOT
+                c.staging, c.Z, c.hard = b.Y.data_ptr(), b.Z.data_ptr(), b.hard.data_ptr()
+                c.hard_host = b.hard_host.data_ptr()
+                c.llr = b.llr.data_ptr() if b.llr is not None else None
+                c.llr_host = b.llr_host.data_ptr() if b.llr is not None else None
+        flags = (mpnl.RUN_SHARE_SMS if big and self.share_sms else 0) \
+            | (mpnl.RUN_SHORT_CTAS if not big and self.small_short_ctas else 0)
+        r.batch.serve_round(rc, len(reqs), flags, stream=st)
+        r.event = torch.cuda.Event()
+        r.event.record(st)
 
     def _launch_per_unit(self, r: _Round, reqs, st, t_adm: float) -> None:
         """A large units' round as plain per-call launches (one CTA per
