@@ -128,3 +128,34 @@ def test_memory_budget_limits_rounds(dev):
     reqs = serving.run_trace(server, trace, payloads, t_limit_s=0.2)
     assert reqs[0].done < 0 and server.n_rounds == 0
     server.close()
+
+
+def test_serve_round_refuses_bad_requests(dev):
+    # mpnl_serve_round checks every request before it enqueues anything
+    import ctypes
+
+    from paper_2409_14355_gb300 import mpnl, serving
+    u = inputs.mixed_units(1, seed=5, sc_scale=0.02)[0]
+    sl = inputs.unit_slot(u)
+    server = serving.Server(dev, mem_budget=64 << 20, max_units_per_round=4, max_inflight=1)
+    ru = serving.RU(0, u.nr, u.nt, u.qam, u.n_sc, u.n_pe, sl.sigma2)
+    server.register(ru, torch.from_numpy(sl.H))
+    reqs = [(0.0, 0, "slot")]
+    payloads = {0: {"slot": [torch.from_numpy(sl.Y).pin_memory()], "channel": []}}
+    serving.run_trace(server, reqs, payloads)            # creates the round's batch
+    r = server.rounds[0]
+    assert r.batch is not None
+    rc = (mpnl.RoundReqC * 4)()
+    lib = mpnl.load_library()
+    st = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    b = ru.pool[0]
+    rc[0].unit = ctypes.pointer(ru.item)
+    rc[0].kind = 7                                        # no such kind
+    rc[0].payload, rc[0].staging = payloads[0]["slot"][0].data_ptr(), b.Y.data_ptr()
+    assert lib.mpnl_serve_round(r.batch._ctx, r.batch._h, rc, 1, 0, st) == mpnl.ERR_INVALID_ARG
+    rc[0].kind = mpnl.ROUND_SLOT                          # a slot without its output buffers
+    assert lib.mpnl_serve_round(r.batch._ctx, r.batch._h, rc, 1, 0, st) == mpnl.ERR_INVALID_ARG
+    assert lib.mpnl_serve_round(r.batch._ctx, r.batch._h, rc, 5, 0, st) == mpnl.ERR_INVALID_ARG
+    assert lib.mpnl_serve_round(r.batch._ctx, r.batch._h, rc, 1, 1 << 20, st) \
+        == mpnl.ERR_INVALID_ARG
+    server.close()
