@@ -785,6 +785,13 @@ def accuracy_per_snr(name, n_pe, dev, n_sc: int = 96):
         g32 = mpnl.detect_slot(H, Y, sl.sigma2, sl.qam, min(32, n_pe), mmse=True)
         row["ber_n_pe_32"] = ber(g32["hard"].cpu().numpy())
         row["ber_mmse"] = ber(g32["mmse_hard"].cpu().numpy())
+        # the walks over the MMSE-extended sorted QR ([H; sigma I]), against
+        # the oracle's same pre-processing
+        ref_q = oracle.detect_slot(sl.H, sl.Y, sl.sigma2, sl.qam, n_pe, mmse_qr=True)
+        gq = mpnl.detect_slot(H, Y, sl.sigma2, sl.qam, n_pe, mmse_qr=True)
+        hq = gq["hard"].cpu().numpy()
+        row["mmse_qr"] = {"ber": ber(hq), "ber_oracle": ber(ref_q["hard"]),
+                          "decision_mismatch": float(np.mean(np.any(hq != ref_q["hard"], axis=-1)))}
         rows.append(row)
     return {"subcarriers_per_point": min(n_sc, w["n_sc"]), "points": rows}
 

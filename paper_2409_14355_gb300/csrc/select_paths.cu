@@ -25,7 +25,21 @@
 // output (N_pe / (32 G) entries) starts by one co-rank binary search and
 // merges from there.  G = 1 (a warp, no barrier) for short lists; G = 2 for
 // N_pe >= 256, where halving the serial slice outweighs a two-warp named
-// barrier per merge.  A CTA holds several independent groups.
+// barrier per merge.  A CTA holds several independent groups.  Shifts whose
+// cost exceeds an upper bound on the final N_pe-th cost are skipped; for
+// N_pe >= 64 the bound comes from the vectors that deviate at one or two
+// levels (about 1.1 times the true N_pe-th cost on 16 levels, against about
+// 6 times from single deviations alone), so most shifts never start.  (Not
+// for a cost table: counting its pairs takes a binary search per row lookup
+// and cost more than it saved.)
+//
+// Costs are 32-bit fixed point (units of 2^-17): each shift cost j w_m is
+// rounded once, and list costs are exact integer sums.  So a shifted list is
+// as sorted as the list it came from -- in float, two costs a ulp apart can
+// round to one value after the shift and swap places under the tie rule,
+// and a merge path over an unsorted input can drop or repeat an entry.  A
+// shift cost is taken as at most 2047 (16 levels of it stay below 2^32); the
+// geometric model's costs stay below 1742 (63 times -log of the Pe floor).
 //
 // A vector is keyed by 16 bytes (two u64, level nt-1 in the most significant
 // byte): comparing keys as unsigned integers is the lexicographic order from
@@ -36,8 +50,8 @@
 namespace mpnl {
 namespace {
 
-__device__ __forceinline__ bool before(float ca, unsigned long long ha, unsigned long long la,
-                                       float cb, unsigned long long hb, unsigned long long lb)
+__device__ __forceinline__ bool before(unsigned ca, unsigned long long ha, unsigned long long la,
+                                       unsigned cb, unsigned long long hb, unsigned long long lb)
 {
     return ca < cb || (ca == cb && (ha < hb || (ha == hb && la < lb)));
 }
@@ -51,10 +65,15 @@ __device__ __forceinline__ void level_shift(int nt, int l, bool &in_hi, int &shi
 }
 
 constexpr int kSelMaxWarps = 4;
+constexpr int kBoundIters = 10;    // bisection steps of the pair-count bound
+constexpr int kBoundMinPe = 64;    // shorter lists keep the single-deviation bound
+constexpr float kCostScale = 131072.f;  // fixed-point units per unit of cost (2^17)
+constexpr float kCostMax = 2047.f;      // largest shift cost represented
 
 __host__ __device__ inline size_t sel_group_bytes(int n_pe)
 {
-    // 3 lists x (8 + 8 + 4) bytes, then w[] and the bound; 16-byte multiple
+    // 3 lists x (8 + 8 + 4) bytes (keys, fixed-point costs), then w[] and the
+    // bound; 16-byte multiple
     // so that the next group's 8-byte keys stay aligned
     return ((size_t)n_pe * 60 + kMaxNt * 4 + 4 + 15) & ~(size_t)15;
 }
@@ -110,8 +129,8 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     // the list index stays arithmetic (no pointer arrays in local memory)
     unsigned long long *HI = reinterpret_cast<unsigned long long *>(base);
     unsigned long long *LO = HI + 3 * n_pe;
-    float *CO = reinterpret_cast<float *>(LO + 3 * n_pe);
-    float *w = CO + 3 * n_pe;
+    unsigned *CO = reinterpret_cast<unsigned *>(LO + 3 * n_pe);
+    float *w = reinterpret_cast<float *>(CO + 3 * n_pe);
     unsigned *s_bound = reinterpret_cast<unsigned *>(w + kMaxNt);
 #define hi(b) (HI + (size_t)(b) * n_pe)
 #define lo(b) (LO + (size_t)(b) * n_pe)
@@ -146,6 +165,67 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     auto shift_cost = [&](int m, int j) -> float {
         if constexpr (LUT) return __ldg(lut.cost + (size_t)__float_as_int(w[m]) * QAM + j);
         else return (float)j * w[m];
+    };
+    // the same in fixed point (rounded to nearest, clamped to kCostMax)
+    auto shift_q = [&](int m, int j) -> unsigned {
+        return __float2uint_rn(fminf(shift_cost(m, j), kCostMax) * kCostScale);
+    };
+    // Number of deviations j >= 1 at level m whose shift cost j w_m is at
+    // most r (linear costs; conservative: r w_m^-1 in float, and callers pass
+    // an r already shaded below the value they test).
+    auto count_upto = [&](int m, float r) -> int {
+        if (!(r >= 0.f)) return 0;
+        const int c = (int)floorf(r * __frcp_rn(w[m]));
+        return c < 0 ? 0 : (c > RK - 1 ? RK - 1 : c);
+    };
+    // Tightening of the single-deviation bound v1 (bits of a float, +inf for
+    // none; the first warp, all lanes): the vectors that deviate at one or
+    // two levels are valid vectors too, so the smallest v at which N_pe of
+    // those cost at most v is also an upper bound on the final N_pe-th cost
+    // -- about 1.1 times it on 16 levels, where v1 is about 6 times it.  A
+    // bisection over (0, v1] with the count split over the lanes: lane
+    // (a, h) takes level a's single deviations (h = 0) and its pairs (a, a +
+    // k mod nt) for k = 1 + h, 3 + h, ... <= nt / 2 (the pair at k = nt / 2
+    // only from a < nt / 2), each pair as a loop over the deviations of the
+    // level with the larger first shift cost and a count at the other.  The
+    // count is conservative: it is taken at v (1 - 1e-5), far below the
+    // rounding of any two-term cost, so every vector counted costs less than
+    // v in float; the result is padded upward and returned in fixed point
+    // (0xffffffff: no bound).
+    auto tighten_bound = [&](unsigned v1bits) -> unsigned {
+        if (v1bits == 0x7f800000u) return 0xffffffffu;
+        float hi_v = __uint_as_float(v1bits);
+        if (!LUT && nt >= 2 && n_pe >= kBoundMinPe) {  // linear costs only
+            const int lane = tid & 31, a = lane & 15, h = lane >> 4;
+            float lo_v = 0.f;
+            for (int it = 0; it < kBoundIters; ++it) {
+                const float mid = 0.5f * (lo_v + hi_v);
+                const float vp = mid * (1.0f - 1e-5f);
+                int cnt = 0;
+                if (a < nt) {
+                    if (h == 0) cnt += count_upto(a, vp);
+                    for (int k = 1 + h; 2 * k <= nt; k += 2) {
+                        if (2 * k == nt && a >= k) continue;
+                        const int b = a + k < nt ? a + k : a + k - nt;
+                        const bool ao = shift_cost(a, 1) >= shift_cost(b, 1);
+                        const int o = ao ? a : b, q = ao ? b : a;
+                        for (int j = 1; j < RK; ++j) {
+                            const float r = vp - shift_cost(o, j);
+                            if (!(r >= 0.f)) break;
+                            cnt += count_upto(q, r);
+                        }
+                    }
+                }
+                cnt = (int)__reduce_add_sync(FULL, (unsigned)cnt) + 1;
+                if (cnt >= n_pe) hi_v = mid;
+                else lo_v = mid;
+            }
+        }
+        // in fixed point: a vector counted costs less than hi_v, and its
+        // fixed-point cost exceeds its float cost times kCostScale by at most
+        // half a unit per level
+        const float b = ceilf((hi_v * (1.0f + 1e-4f) + 1e-6f) * kCostScale) + 16.f;
+        return b >= 4294967040.f ? 0xffffffffu : (unsigned)b;
     };
     // Upper bound on the final N_pe-th cost: the vectors that deviate from
     // all-ones at a single level (cost j w_l) plus all-ones itself are valid
@@ -185,11 +265,11 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
                     if (count(shift_cost(l, mid)) >= n_pe) hi_j = mid;
                     else lo_j = mid + 1;
                 }
-                const float v = shift_cost(l, lo_j);
-                bbits = __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f);
+                bbits = __float_as_uint(shift_cost(l, lo_j));
             }
         }
         bbits = __reduce_min_sync(FULL, bbits);
+        bbits = tighten_bound(bbits);
         if (tid == 0) *s_bound = bbits;
     } else if (!LUT && tid < 32) {
         unsigned bbits = 0x7f800000u;  // +inf
@@ -215,15 +295,15 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
                     if (count(mid) >= n_pe) hi_j = mid;
                     else lo_j = mid + 1;
                 }
-                const float v = (float)lo_j * wl;
-                bbits = __float_as_uint(v * (1.0f + 1e-4f) + 1e-6f);
+                bbits = __float_as_uint((float)lo_j * wl);
             }
         }
         bbits = __reduce_min_sync(FULL, bbits);
+        bbits = tighten_bound(bbits);
         if (tid == 0) *s_bound = bbits;
     }
     group_sync<G>(group);
-    const float bound = __uint_as_float(*s_bound);
+    const unsigned bound = *s_bound;  // fixed point; 0xffffffff: none
     // The first level processed (nt-1) in closed form: starting from the
     // all-ones vector, its list is the arithmetic sequence j * w (rank j + 1
     // at that level), already sorted, cut at N_pe, at M and at the bound --
@@ -231,7 +311,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     int li = 0, nL = 1;
     {
         const int mt = nt - 1;
-        while (nL < RK && nL < n_pe && shift_cost(mt, nL) <= bound) ++nL;
+        while (nL < RK && nL < n_pe && shift_q(mt, nL) <= bound) ++nL;
         unsigned long long h = 0, o = 0;
         for (int l = 0; l < nt; ++l) {
             bool in_hi;
@@ -247,7 +327,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
             const unsigned long long add = (unsigned long long)j << sh;
             hi(0)[j] = h + (in_hi ? add : 0ull);
             lo(0)[j] = o + (in_hi ? 0ull : add);
-            cost(0)[j] = shift_cost(mt, j);
+            cost(0)[j] = shift_q(mt, j);
         }
     }
     group_sync<G>(group);
@@ -259,11 +339,11 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         int oi = (li + 1) % 3;         // first output buffer
         for (int j = 1; j < RK; ++j) {
             const unsigned long long add = (unsigned long long)j << sh;
-            const float cj = shift_cost(m, j);
+            const unsigned cj = shift_q(m, j);
             if (cj > bound) break;
             // first entry of the shifted list vs the last entry of B
             {
-                const float c0 = cost(li)[0] + cj;
+                const unsigned c0 = cost(li)[0] + cj;
                 const unsigned long long h0 = hi(li)[0] + (in_hi ? add : 0ull);
                 const unsigned long long l0 = lo(li)[0] + (in_hi ? 0ull : add);
                 if (nB == n_pe &&
@@ -280,7 +360,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
                 int lo_i = max(0, k0 - nL), hi_i = min(k0, nB);
                 while (lo_i < hi_i) {
                     const int i = (lo_i + hi_i) >> 1, jj = k0 - i;  // jj >= 1, i < nB
-                    const float cc = cost(li)[jj - 1] + cj;
+                    const unsigned cc = cost(li)[jj - 1] + cj;
                     const unsigned long long hc = hi(li)[jj - 1] + (in_hi ? add : 0ull);
                     const unsigned long long lc = lo(li)[jj - 1] + (in_hi ? 0ull : add);
                     if (before(cost(bi)[i], hi(bi)[i], lo(bi)[i], cc, hc, lc)) lo_i = i + 1;
@@ -288,7 +368,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
                 }
                 int i = lo_i, jj = k0 - lo_i;
                 for (int k = k0; k < k1; ++k) {
-                    float ca = 0.f, cc = 0.f;
+                    unsigned ca = 0u, cc = 0u;
                     unsigned long long ha = 0, la = 0, hc = 0, lc = 0;
                     if (i < nB) {
                         ca = cost(bi)[i];
