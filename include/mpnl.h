@@ -173,10 +173,9 @@ int mpnl_refine_qr(mpnl_ctx *ctx, const mpnl_dims *dims, const void *H, const vo
  * symbol is the k-th closest.  The N_pe vectors of largest prod_l P_l(p_l)
  * are written best first (ties: lexicographically smaller from level nt-1
  * down); row 0 is the all-ones vector (plain SIC).  The ranking uses the
- * cost -log of that product relative to all-ones, sum_l (p_l - 1)(-log Pe_l),
- * with each level's term rounded to a multiple of 2^-17 (so vectors whose
- * costs differ by less than about 4e-6 per deviated level may come in either
- * order).
+ * cost -log of that product relative to all-ones, sum_l (p_l - 1)(-log Pe_l):
+ * each level's term in float, the sum exact (64-bit fixed point, units of
+ * 2^-32).
  *   R      in  c64 [n_sc][nt(nt+1)/2]  as written by mpnl_preprocess (only
  *              the diagonal is read)
  *   paths  out u8  [n_sc][n_pe][nt]     ranks 1..qam, level index last */
@@ -194,8 +193,8 @@ int mpnl_select_paths(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, float
  *   edges  in  f32 [n_bins - 1]     ascending linear SNRs (device)
  *   cost   in  f32 [n_bins][qam]    c(k) at k - 1: c(1) = 0, nondecreasing in
  *                                   k, finite (device; mpnl_rank_costs);
- *                                   costs above 2047 are taken as 2047 and
- *                                   each term is rounded as in
+ *                                   costs above 2^20 are taken as 2^20, and
+ *                                   the terms are summed as in
  *                                   mpnl_select_paths  */
 typedef struct {
     int qam, n_bins;

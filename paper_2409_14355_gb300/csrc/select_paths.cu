@@ -33,13 +33,13 @@
 // for a cost table: counting its pairs takes a binary search per row lookup
 // and cost more than it saved.)
 //
-// Costs are 32-bit fixed point (units of 2^-17): each shift cost j w_m is
-// rounded once, and list costs are exact integer sums.  So a shifted list is
-// as sorted as the list it came from -- in float, two costs a ulp apart can
-// round to one value after the shift and swap places under the tie rule,
-// and a merge path over an unsorted input can drop or repeat an entry.  A
-// shift cost is taken as at most 2047 (16 levels of it stay below 2^32); the
-// geometric model's costs stay below 1742 (63 times -log of the Pe floor).
+// Costs are 64-bit fixed point (units of 2^-32): each float shift cost j w_m
+// converts exactly (or to within 2^-33 below 2^-9), and list costs are exact
+// integer sums of them.  So a shifted list is as sorted as the list it came
+// from -- in float, two costs a ulp apart can round to one value after the
+// shift and swap places under the tie rule, and a merge path over an
+// unsorted input can drop or repeat an entry.  A shift cost is taken as at
+// most 2^20 (16 levels of it stay below 2^57).
 //
 // A vector is keyed by 16 bytes (two u64, level nt-1 in the most significant
 // byte): comparing keys as unsigned integers is the lexicographic order from
@@ -50,8 +50,9 @@
 namespace mpnl {
 namespace {
 
-__device__ __forceinline__ bool before(unsigned ca, unsigned long long ha, unsigned long long la,
-                                       unsigned cb, unsigned long long hb, unsigned long long lb)
+__device__ __forceinline__ bool before(unsigned long long ca, unsigned long long ha,
+                                       unsigned long long la, unsigned long long cb,
+                                       unsigned long long hb, unsigned long long lb)
 {
     return ca < cb || (ca == cb && (ha < hb || (ha == hb && la < lb)));
 }
@@ -67,15 +68,15 @@ __device__ __forceinline__ void level_shift(int nt, int l, bool &in_hi, int &shi
 constexpr int kSelMaxWarps = 4;
 constexpr int kBoundIters = 10;    // bisection steps of the pair-count bound
 constexpr int kBoundMinPe = 64;    // shorter lists keep the single-deviation bound
-constexpr float kCostScale = 131072.f;  // fixed-point units per unit of cost (2^17)
-constexpr float kCostMax = 2047.f;      // largest shift cost represented
+constexpr float kCostScale = 4294967296.f;  // fixed-point units per unit of cost (2^32)
+constexpr float kCostMax = 1048576.f;       // largest shift cost represented (2^20)
+constexpr unsigned long long kNoBound = ~0ull;
 
 __host__ __device__ inline size_t sel_group_bytes(int n_pe)
 {
-    // 3 lists x (8 + 8 + 4) bytes (keys, fixed-point costs), then w[] and the
-    // bound; 16-byte multiple
-    // so that the next group's 8-byte keys stay aligned
-    return ((size_t)n_pe * 60 + kMaxNt * 4 + 4 + 15) & ~(size_t)15;
+    // 3 lists x (8 + 8 + 8) bytes (keys, fixed-point costs), then the bound
+    // and w[]; 16-byte multiple so that the next group's keys stay aligned
+    return ((size_t)n_pe * 72 + 8 + kMaxNt * 4 + 15) & ~(size_t)15;
 }
 
 template <int G>
@@ -129,9 +130,9 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     // the list index stays arithmetic (no pointer arrays in local memory)
     unsigned long long *HI = reinterpret_cast<unsigned long long *>(base);
     unsigned long long *LO = HI + 3 * n_pe;
-    unsigned *CO = reinterpret_cast<unsigned *>(LO + 3 * n_pe);
-    float *w = reinterpret_cast<float *>(CO + 3 * n_pe);
-    unsigned *s_bound = reinterpret_cast<unsigned *>(w + kMaxNt);
+    unsigned long long *CO = LO + 3 * n_pe;
+    unsigned long long *s_bound = CO + 3 * n_pe;
+    float *w = reinterpret_cast<float *>(s_bound + 1);
 #define hi(b) (HI + (size_t)(b) * n_pe)
 #define lo(b) (LO + (size_t)(b) * n_pe)
 #define cost(b) (CO + (size_t)(b) * n_pe)
@@ -167,8 +168,8 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         else return (float)j * w[m];
     };
     // the same in fixed point (rounded to nearest, clamped to kCostMax)
-    auto shift_q = [&](int m, int j) -> unsigned {
-        return __float2uint_rn(fminf(shift_cost(m, j), kCostMax) * kCostScale);
+    auto shift_q = [&](int m, int j) -> unsigned long long {
+        return __float2ull_rn(fminf(shift_cost(m, j), kCostMax) * kCostScale);
     };
     // Number of deviations j >= 1 at level m whose shift cost j w_m is at
     // most r (linear costs; conservative: r w_m^-1 in float, and callers pass
@@ -191,9 +192,9 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     // count is conservative: it is taken at v (1 - 1e-5), far below the
     // rounding of any two-term cost, so every vector counted costs less than
     // v in float; the result is padded upward and returned in fixed point
-    // (0xffffffff: no bound).
-    auto tighten_bound = [&](unsigned v1bits) -> unsigned {
-        if (v1bits == 0x7f800000u) return 0xffffffffu;
+    // (kNoBound: none).
+    auto tighten_bound = [&](unsigned v1bits) -> unsigned long long {
+        if (v1bits == 0x7f800000u) return kNoBound;
         float hi_v = __uint_as_float(v1bits);
         if (!LUT && nt >= 2 && n_pe >= kBoundMinPe) {  // linear costs only
             const int lane = tid & 31, a = lane & 15, h = lane >> 4;
@@ -222,10 +223,10 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
             }
         }
         // in fixed point: a vector counted costs less than hi_v, and its
-        // fixed-point cost exceeds its float cost times kCostScale by at most
-        // half a unit per level
-        const float b = ceilf((hi_v * (1.0f + 1e-4f) + 1e-6f) * kCostScale) + 16.f;
-        return b >= 4294967040.f ? 0xffffffffu : (unsigned)b;
+        // fixed-point cost is the exact sum of its float shift costs (each
+        // to within half a unit), far inside the padding
+        const float b = fminf(hi_v * (1.0f + 1e-4f) + 1e-6f, kCostMax * (float)kMaxNt);
+        return __float2ull_ru(b * kCostScale) + 16ull;
     };
     // Upper bound on the final N_pe-th cost: the vectors that deviate from
     // all-ones at a single level (cost j w_l) plus all-ones itself are valid
@@ -269,8 +270,8 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
             }
         }
         bbits = __reduce_min_sync(FULL, bbits);
-        bbits = tighten_bound(bbits);
-        if (tid == 0) *s_bound = bbits;
+        const unsigned long long bq = tighten_bound(bbits);
+        if (tid == 0) *s_bound = bq;
     } else if (!LUT && tid < 32) {
         unsigned bbits = 0x7f800000u;  // +inf
         if (tid < nt) {
@@ -299,11 +300,11 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
             }
         }
         bbits = __reduce_min_sync(FULL, bbits);
-        bbits = tighten_bound(bbits);
-        if (tid == 0) *s_bound = bbits;
+        const unsigned long long bq = tighten_bound(bbits);
+        if (tid == 0) *s_bound = bq;
     }
     group_sync<G>(group);
-    const unsigned bound = *s_bound;  // fixed point; 0xffffffff: none
+    const unsigned long long bound = *s_bound;  // fixed point; kNoBound: none
     // The first level processed (nt-1) in closed form: starting from the
     // all-ones vector, its list is the arithmetic sequence j * w (rank j + 1
     // at that level), already sorted, cut at N_pe, at M and at the bound --
@@ -339,11 +340,11 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         int oi = (li + 1) % 3;         // first output buffer
         for (int j = 1; j < RK; ++j) {
             const unsigned long long add = (unsigned long long)j << sh;
-            const unsigned cj = shift_q(m, j);
+            const unsigned long long cj = shift_q(m, j);
             if (cj > bound) break;
             // first entry of the shifted list vs the last entry of B
             {
-                const unsigned c0 = cost(li)[0] + cj;
+                const unsigned long long c0 = cost(li)[0] + cj;
                 const unsigned long long h0 = hi(li)[0] + (in_hi ? add : 0ull);
                 const unsigned long long l0 = lo(li)[0] + (in_hi ? 0ull : add);
                 if (nB == n_pe &&
@@ -360,7 +361,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
                 int lo_i = max(0, k0 - nL), hi_i = min(k0, nB);
                 while (lo_i < hi_i) {
                     const int i = (lo_i + hi_i) >> 1, jj = k0 - i;  // jj >= 1, i < nB
-                    const unsigned cc = cost(li)[jj - 1] + cj;
+                    const unsigned long long cc = cost(li)[jj - 1] + cj;
                     const unsigned long long hc = hi(li)[jj - 1] + (in_hi ? add : 0ull);
                     const unsigned long long lc = lo(li)[jj - 1] + (in_hi ? 0ull : add);
                     if (before(cost(bi)[i], hi(bi)[i], lo(bi)[i], cc, hc, lc)) lo_i = i + 1;
@@ -368,7 +369,7 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
                 }
                 int i = lo_i, jj = k0 - lo_i;
                 for (int k = k0; k < k1; ++k) {
-                    unsigned ca = 0u, cc = 0u;
+                    unsigned long long ca = 0ull, cc = 0ull;
                     unsigned long long ha = 0, la = 0, hc = 0, lc = 0;
                     if (i < nB) {
                         ca = cost(bi)[i];

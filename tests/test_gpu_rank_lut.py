@@ -135,3 +135,68 @@ def test_select_paths_lut_rejects_bad_tables(dev):
     p = mpnl.select_paths_lut(R, 0.1, lut, 8, 3)
     torch.cuda.synchronize()
     assert p.shape == (3, 8, 3) and p[:, 0].eq(1).all()
+
+
+def _exact_fixed_point_top(bins, cost, nt, qam, n_pe):
+    """The N_pe vectors of smallest fixed-point cost (each level's term the
+    float32 table value, capped at 2^20, in units of 2^-32, rounded to the
+    nearest unit; integer sums), ties lexicographically smaller from level
+    nt-1 down: level by level, all candidates sorted, exact truncation."""
+    def q(m, j):
+        v = float(min(np.float32(cost[bins[m], j]), np.float32(2.0 ** 20))) * 2.0 ** 32
+        return int(np.rint(v))
+    cur = [(q(nt - 1, j), (j,)) for j in range(min(qam, n_pe))]
+    cur.sort()
+    for m in range(nt - 2, -1, -1):
+        qs = [q(m, j) for j in range(qam)]
+        cur = sorted((v + qs[j], k + (j,)) for v, k in cur for j in range(qam))[:n_pe]
+    return np.array([[k[nt - 1 - l] + 1 for l in range(nt)] for _, k in cur], np.uint8)
+
+
+@pytest.mark.parametrize("nt,qam,n_pe,n_sc,scale", [
+    (16, 64, 256, 8, 1.0), (8, 16, 100, 12, 1.0), (4, 4, 64, 12, 1.0), (16, 64, 1024, 3, 1.0),
+    (5, 64, 300, 8, 1.0), (3, 16, 200, 8, 3.0e5),
+])
+def test_select_paths_lut_exact_under_near_ties(dev, nt, qam, n_pe, n_sc, scale):
+    """Tables built to make near-ties: rows a few float32 ulps apart, a flat
+    step, equal rows.  In float, adding a shift cost can round two list costs
+    a ulp apart to one value and swap them under the tie rule; the selection
+    ranks by fixed-point terms instead, and must equal the exact top-N_pe of
+    that order row for row.  With scale 3e5 the costs run past the 2^20 cap
+    (capped terms tie and fall back to the key order)."""
+    mpnl = _mpnl()
+    rng = np.random.default_rng(1000 + nt * qam + n_pe)
+    n_bins = 6
+    base = (np.concatenate([[0.0], np.cumsum(rng.uniform(0.05, 0.9, qam - 1))])
+            * scale).astype(np.float32)
+    cost = np.empty((n_bins, qam), np.float32)
+    for b in range(n_bins):
+        row = base.copy()
+        row[1:] = np.nextafter(row[1:], np.float32(np.inf)) if b % 2 else row[1:]
+        if b >= 2:
+            row[1:] = row[1:] * np.float32(1.0 + 1e-7 * b)
+        if b == 4:
+            row[3] = row[2]           # a flat step
+        if b == 5:
+            row = cost[0].copy()      # a row equal to another
+        cost[b] = np.maximum.accumulate(row)
+        cost[b, 0] = 0.0
+    edges = np.arange(1, n_bins, dtype=np.float32)          # bin b: gamma in [b, b + 1)
+    lut = mpnl.RankLut(qam, torch.from_numpy(edges).to(dev), torch.from_numpy(cost).to(dev))
+    P_ = nt * (nt + 1) // 2
+    bins = rng.integers(0, n_bins, size=(n_sc, nt))
+    gamma = bins + 0.5
+    R = np.zeros((n_sc, P_), np.complex64)
+    for l in range(nt):
+        R[:, l * nt - l * (l - 1) // 2] = np.sqrt(gamma[:, l]).astype(np.float32)
+    paths = mpnl.select_paths_lut(torch.from_numpy(R).to(dev), 1.0, lut, n_pe, nt)
+    torch.cuda.synchronize()
+    G = paths.cpu().numpy()
+    for c in range(n_sc):
+        # the bin the kernel sees: gamma from the float32 diagonal
+        rll = R[c, [l * nt - l * (l - 1) // 2 for l in range(nt)]].real.astype(np.float32)
+        b_dev = np.array([int(np.sum((rll[l] * rll[l]) / np.float32(1.0) >= edges))
+                          for l in range(nt)])
+        assert np.array_equal(b_dev, bins[c])
+        want = _exact_fixed_point_top(b_dev, cost, nt, qam, n_pe)
+        assert np.array_equal(G[c], want), (c, np.nonzero(np.any(G[c] != want, axis=1))[0][:5])
