@@ -848,13 +848,17 @@ def run_mixed(args, dev, rank):
             "tuning_batch_ms": report["batch_ms"], "tuning_choice": report["batch_choice"]}
 
 
-def run_serving(args, dev):
+def run_serving(args, dev, sm_split: int = 0, capacity: float | None = None):
+    """The serving loop on the RU mix: its capacity (or the one given, so
+    that two configurations see the same offered loads), then latency at 50,
+    75 and 100% of it.  sm_split > 0: the small units' rounds on a group of
+    that many SMs of their own."""
     import torch
 
     from paper_2409_14355_gb300 import serving
 
     units = serving.serving_units(args.serving_rus)
-    server = serving.Server(dev, mem_budget=4 << 30, max_units_per_round=64)
+    server = serving.Server(dev, mem_budget=4 << 30, max_units_per_round=64, sm_split=sm_split)
     payloads = {}
     for k, u in enumerate(units):
         sl = inputs.unit_slot(u)
@@ -871,7 +875,9 @@ def run_serving(args, dev):
     serving.run_trace(server, sat, payloads)
     reqs = serving.run_trace(server, sat, payloads)
     span = max(q.done for q in reqs) - min(q.arrival for q in reqs)
-    capacity = sum(dets[q.ru] for q in reqs) / span
+    own_capacity = sum(dets[q.ru] for q in reqs) / span
+    if capacity is None:
+        capacity = own_capacity
     loads = {}
     for rho in (0.5, 0.75, 1.0):
         rate = rho * capacity / mean_dets
@@ -886,13 +892,15 @@ def run_serving(args, dev):
             rounds=len(server.round_sizes),
             host_ms_per_round=1e3 * server.host_launch_s / max(1, len(server.round_sizes)))
         loads[str(rho)] = st
+    sms = list(server.split_sms) if server.split_sms is not None else None
     server.close()
     n_big = sum(1 for u in units if (u.nr, u.nt, u.qam, u.n_sc) == (16, 16, 64, 3276))
     return {"workload": f"{len(units)} radio units ({n_big} of them 16x16 64-QAM 3276 sc), "
                         f"sizes as the mixed batch, Poisson slot requests, channel update every "
                         f"8th slot of a unit; large units: walk work >= a 16x16 936-sc N_pe 64 "
                         f"slot", "deadline_ms": 0.5,
-            "capacity_detections_per_s": capacity, "seconds_per_load": args.serving_seconds,
+            "capacity_detections_per_s": capacity, "own_capacity_detections_per_s": own_capacity,
+            "sm_split": sms, "seconds_per_load": args.serving_seconds,
             "resident_state_MB": server.state_bytes / 1e6, "loads": loads}
 
 

@@ -478,6 +478,38 @@ int mpnl_serve_round(mpnl_ctx *ctx, mpnl_batch *batch, const mpnl_round_req *req
 /* Release a batch (NULL is ignored); its work must have completed. */
 void mpnl_batch_destroy(mpnl_batch *batch);
 
+/* SM partition for serving (§I, §IV: a distributed unit allocates its
+ * compute to the radio units where the load is).  Splits the SMs of the
+ * context's device into two disjoint groups with CUDA green contexts: group
+ * 0 of at least sms_first SMs (rounded up to the device's partition
+ * granularity, 8 SMs on this GPU), group 1 the rest.  Kernels enqueued on a
+ * stream of a group run on that group's SMs only; everything else about the
+ * stream is as for any stream of the device (a green context is the primary
+ * context with fewer SMs): device memory, every call of this library,
+ * events, CUDA graphs.  The serving loop puts its small radio units' rounds
+ * on group 0, so they never wait for an SM behind a large unit's walks.
+ *   sms    out int[2]: the SMs of group 0 and group 1
+ * Errors: MPNL_ERR_INVALID_ARG for a NULL pointer or sms_first outside
+ * 1..SMs-1 (or a split the device cannot make), MPNL_ERR_UNSUPPORTED when
+ * the driver has no green contexts, MPNL_ERR_CUDA. */
+typedef struct mpnl_sm_split mpnl_sm_split;
+int mpnl_sm_split_create(mpnl_ctx *ctx, int sms_first, mpnl_sm_split **split, int *sms);
+
+/* A new non-blocking stream (a cudaStream_t) in group `part` (0 or 1), at
+ * `priority` as for cudaStreamCreateWithPriority.  The split owns it:
+ * mpnl_sm_split_destroy destroys it. */
+int mpnl_sm_split_stream(mpnl_ctx *ctx, mpnl_sm_split *split, int part, int priority,
+                         void **stream);
+
+/* Waits for the work queued on the split's streams, destroys them and the
+ * green contexts, frees the split.  NULL is a no-op.  Destroy only a split
+ * whose streams nothing will touch again: events that other code recorded
+ * on them (a framework's caching allocators do, for the copies and
+ * allocations they see on a stream) stay bound to the green contexts, and
+ * using them afterwards is undefined.  A split can instead be kept for the
+ * life of the process, as frameworks keep their own streams. */
+int mpnl_sm_split_destroy(mpnl_ctx *ctx, mpnl_sm_split *split);
+
 /* Walks of up to MPNL_NOALLOC_MAX_UNITS radio units in one persistent launch,
  * without allocating anything.  The paper has no counterpart: this is an
  * interface for callers that must not allocate device memory once they are

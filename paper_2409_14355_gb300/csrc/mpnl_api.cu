@@ -416,6 +416,16 @@ int enqueue_batch(mpnl_ctx *ctx, mpnl_batch *b, int stages, cudaStream_t st, boo
 
 }  // namespace
 
+// for the calls defined in other translation units (sm_split.cu)
+namespace mpnl {
+int api_begin(mpnl_ctx *ctx) { return begin(ctx); }
+int api_device(const mpnl_ctx *ctx) { return ctx->device; }
+int api_fail(mpnl_ctx *ctx, int code, const char *what, const char *detail)
+{
+    return detail && detail[0] ? fail(ctx, code, "%s: %s", what, detail) : fail(ctx, code, "%s", what);
+}
+}  // namespace mpnl
+
 extern "C" {
 
 int mpnl_batch_create(mpnl_ctx *ctx, const mpnl_batch_item *items, int n_items,
@@ -639,6 +649,7 @@ void mpnl_destroy(mpnl_ctx *ctx)
 }
 
 const char *mpnl_last_error(const mpnl_ctx *ctx) { return ctx ? ctx->err : "context is NULL"; }
+
 
 size_t mpnl_workspace_bytes(const mpnl_dims *dims)
 {

@@ -6,7 +6,16 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct mpnl_ctx;
+
 namespace mpnl {
+
+// Context plumbing for the calls defined outside mpnl_api.cu: begin (checks
+// the context, makes its device current, clears the message), its device,
+// and an error return with the message "what: detail" (detail may be empty).
+int api_begin(mpnl_ctx *ctx);
+int api_device(const mpnl_ctx *ctx);
+int api_fail(mpnl_ctx *ctx, int code, const char *what, const char *detail);
 
 // Arguments of one detection problem (one radio unit's slot): sizes and the
 // caller's device arrays, indexed by subcarrier inside the walk kernel.

@@ -43,7 +43,8 @@ EXPORTED = ("mpnl_create", "mpnl_destroy", "mpnl_last_error", "mpnl_workspace_by
             "mpnl_select_paths_lut", "mpnl_rank_counts", "mpnl_rank_costs",
             "mpnl_rvd_embed", "mpnl_select_paths_pam", "mpnl_detect_rvd", "mpnl_qhy_mixed",
             "mpnl_detect_units_noalloc", "mpnl_detect_slot", "mpnl_slot_workspace_bytes",
-            "mpnl_serve_round")
+            "mpnl_serve_round", "mpnl_sm_split_create", "mpnl_sm_split_stream",
+            "mpnl_sm_split_destroy")
 ITEM_MMSE_QR, ITEM_LINEAR_MMSE, ITEM_FP16, ITEM_REFINE_QR = 1, 2, 4, 8
 STAGE_PREPROCESS, STAGE_SELECT, STAGE_DETECT, STAGE_MMSE, STAGE_QHY = 1, 2, 4, 8, 32
 STAGES_ALL = 47
@@ -182,6 +183,13 @@ def load_library(path: str = LIB_PATH):
         lib.mpnl_slot_workspace_bytes.restype = S
         lib.mpnl_detect_slot.argtypes = [P, D, F, P, P, P, P, P, P, P, I, P, S, P]
         lib.mpnl_detect_slot.restype = I
+        lib.mpnl_sm_split_create.argtypes = [P, I, ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.POINTER(I)]
+        lib.mpnl_sm_split_create.restype = I
+        lib.mpnl_sm_split_stream.argtypes = [P, P, I, I, ctypes.POINTER(ctypes.c_void_p)]
+        lib.mpnl_sm_split_stream.restype = I
+        lib.mpnl_sm_split_destroy.argtypes = [P, P]
+        lib.mpnl_sm_split_destroy.restype = I
         lib.mpnl_set_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
         lib.mpnl_set_tuning.restype = I
         lib.mpnl_get_tuning.argtypes = [P, ctypes.POINTER(Tuning)]
@@ -203,6 +211,54 @@ def context(device: int | None = None) -> ctypes.c_void_p:
             raise MpnlError(st, f"mpnl_create(device={dev}) failed")
         _ctxs[dev] = h
     return _ctxs[dev]
+
+
+class SmSplit:
+    """mpnl_sm_split_*: the device's SMs in two disjoint groups (CUDA green
+    contexts), group 0 of at least `sms_first` SMs and group 1 the rest;
+    `stream(part)` gives a torch stream whose kernels run on that group's SMs
+    only.  One split per (device, sms_first) is made per process
+    (`SmSplit.get`) and kept, with its streams, for the life of the process,
+    as torch keeps its own streams: torch records events on the streams it
+    uses (caching allocators, copies from pinned memory) and may touch them
+    long after, so neither the streams nor their green contexts may go away
+    under it.  `sync()` waits for the work on the split's streams."""
+
+    _cache: dict = {}
+
+    def __init__(self, sms_first: int, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self._ctx = context(self.device.index)
+        self._h = ctypes.c_void_p()
+        sms = (ctypes.c_int * 2)()
+        _raise(load_library().mpnl_sm_split_create(self._ctx, int(sms_first),
+                                                   ctypes.byref(self._h), sms), self._ctx)
+        self.sms = (int(sms[0]), int(sms[1]))
+        self._streams: dict = {}
+
+    @classmethod
+    def get(cls, sms_first: int, device=None) -> "SmSplit":
+        dev = torch.cuda.current_device() if device is None else torch.device(device).index or 0
+        key = (dev, int(sms_first))
+        if key not in cls._cache:
+            cls._cache[key] = cls(sms_first, dev)
+        return cls._cache[key]
+
+    def stream(self, part: int, priority: int = 0, index: int = 0) -> torch.cuda.ExternalStream:
+        """The index-th stream of group `part` at `priority` (made on first
+        request, then the same one)."""
+        key = (int(part), int(priority), int(index))
+        if key not in self._streams:
+            p = ctypes.c_void_p()
+            _raise(load_library().mpnl_sm_split_stream(self._ctx, self._h, key[0], key[1],
+                                                       ctypes.byref(p)), self._ctx)
+            self._streams[key] = torch.cuda.ExternalStream(p.value, device=self.device)
+        return self._streams[key]
+
+    def sync(self) -> None:
+        for st in self._streams.values():
+            st.synchronize()
 
 
 def _raise(st: int, ctx) -> None:

@@ -147,12 +147,16 @@ class _Round:
         """The round's stream for its size class, created on first use (the
         loop's logic needs no GPU): small units' rounds run on a
         high-priority stream, so their CTAs are scheduled ahead of a large
-        unit's walks still in flight."""
+        unit's walks still in flight; with an SM split, each class's rounds
+        run on its own group of SMs."""
         if big not in self._streams:
             lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") \
                 else (0, -1)
-            self._streams[big] = torch.cuda.Stream(self.server.device,
-                                                   priority=lo if big else hi)
+            prio = lo if big else hi
+            if self.server.split is not None:
+                self._streams[big] = self.server.split.stream(1 if big else 0, prio, self.index)
+            else:
+                self._streams[big] = torch.cuda.Stream(self.server.device, priority=prio)
         return self._streams[big]
 
     @property
@@ -168,7 +172,8 @@ class Server:
                  slots_per_ru: int = 2, keep_results: bool = False,
                  big_cost: float = 936 * 14 * 64 * 16 * 20, max_large_rounds: int | None = None,
                  share_sms: bool = False, large_per_unit: bool = True,
-                 small_short_ctas: bool = True, native_rounds: bool = True):
+                 small_short_ctas: bool = True, native_rounds: bool = True,
+                 sm_split: int = 0):
         self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
                        else torch.device(device))
         self.mem_budget = int(mem_budget)
@@ -195,6 +200,12 @@ class Server:
         self.small_short_ctas = small_short_ctas
         # rounds after a batch's first as one native call (mpnl_serve_round)
         self.native_rounds = native_rounds
+        # sm_split > 0: the small units' rounds get a group of at least that
+        # many SMs of their own (mpnl_sm_split_*), the large units' the rest;
+        # made on first use of a round stream (one split per size per process)
+        self.sm_split = int(sm_split)
+        self._split = None
+        self.split_sms = None   # (small units' SMs, large units' SMs) once made
         self.keep_results = keep_results  # copy each result out (else a view valid
         # until the RU's pool buffer is reused)
         self.rus: dict[int, RU] = {}
@@ -531,12 +542,22 @@ class Server:
         while (self.waiting or any(not r.free for r in self.rounds)) and time.perf_counter() < t_end:
             self.step()
 
+    @property
+    def split(self):
+        """The SM split of the two size classes (None without one)."""
+        if self.sm_split and self._split is None:
+            self._split = mpnl.SmSplit.get(self.sm_split, self.device)
+            self.split_sms = self._split.sms
+        return self._split
+
     def close(self) -> None:
         torch.cuda.synchronize(self.device)
         for r in self.rounds:
             if r.batch is not None:
                 r.batch.close()
                 r.batch = None
+            r._streams.clear()
+        self._split = None   # kept by the process (mpnl.SmSplit.get)
 
 
 # ---------------------------------------------------------------------------

@@ -75,11 +75,26 @@ def _alone(dev, ru, H, Y):
 
 
 def test_serving_results_equal_each_request_alone(dev):
+    _serve_and_compare(dev)
+
+
+def test_serving_on_an_sm_split_equals_each_request_alone(dev):
+    """The same with the small units' rounds on a group of SMs of their own
+    (green contexts) and the large ones on the rest: the class boundary is
+    set so that both groups serve some of the units."""
+    from paper_2409_14355_gb300 import serving
+    specs = inputs.mixed_units(6, seed=31, sc_scale=0.02)
+    costs = sorted(serving.RU(0, u.nr, u.nt, u.qam, u.n_sc, u.n_pe, 1.0).cost for u in specs)
+    server = _serve_and_compare(dev, sm_split=16, big_cost=costs[len(costs) // 2])
+    assert server.split_sms is not None and server.split_sms[0] >= 16
+
+
+def _serve_and_compare(dev, **server_kw):
     from paper_2409_14355_gb300 import mpnl, serving
     specs = inputs.mixed_units(6, seed=31, sc_scale=0.02)
     specs[1] = inputs.UnitSpec(4, 6, 16, 29, 64, 18.0, "iid", 77)   # more users than antennas
     server = serving.Server(dev, mem_budget=64 << 20, max_units_per_round=8, max_inflight=2,
-                            keep_results=True)
+                            keep_results=True, **server_kw)
     payloads, first_H = {}, {}
     for k, u in enumerate(specs):
         sl = inputs.unit_slot(u)
@@ -111,6 +126,68 @@ def test_serving_results_equal_each_request_alone(dev):
         assert torch.equal(q.llr, llr), (q.rid, q.ru)
         n_cmp += 1
     assert n_cmp > 20
+    if "big_cost" in server_kw:   # both size classes were served
+        assert len({server.rus[q.ru].cost >= server.big_cost for q in reqs}) == 2
+    return server
+
+
+def test_sm_split_streams_run_the_path(dev):
+    """mpnl_sm_split_*: two disjoint SM groups covering at most the device's
+    SMs; the whole path enqueued on a stream of either group gives the
+    results of the default stream; bad arguments are refused."""
+    from paper_2409_14355_gb300 import mpnl
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sl = inputs.make_slot(8, 8, 16, 150, 14, 16.0, "iid", 0.3, 901)
+    H = torch.from_numpy(sl.H).to(dev)
+    Y = torch.from_numpy(sl.Y).to(dev)
+
+    def path():
+        R, inv_diag, perm, Z = mpnl.preprocess(H, Y)
+        paths = mpnl.select_paths(R, sl.sigma2, sl.qam, 64, sl.nt)
+        hard, llr, ped2 = mpnl.detect(R, inv_diag, perm, paths, Z, sl.sigma2, sl.qam)
+        return hard, llr, ped2
+
+    want = [t.cpu() for t in path()]
+    split = mpnl.SmSplit.get(16, dev)
+    assert mpnl.SmSplit.get(16, dev) is split
+    assert split.sms[0] >= 16 and split.sms[1] >= 1 and sum(split.sms) <= n_sm
+    for part in (0, 1):
+        st = split.stream(part)
+        assert split.stream(part) is st
+        st.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(st):
+            got = path()
+        st.synchronize()
+        for a, b in zip(got, want):
+            assert torch.equal(a.cpu(), b)
+    mpnl.check_status()
+    for bad in (0, n_sm, -3):
+        with pytest.raises(mpnl.MpnlError):
+            mpnl.SmSplit(bad, dev)
+
+
+def test_sm_split_create_and_destroy_through_the_abi(dev):
+    """Create, streams, destroy at the C ABI (nothing enqueued: a split
+    whose streams torch has used stays for the life of the process)."""
+    import ctypes
+    from paper_2409_14355_gb300 import mpnl
+    lib = mpnl.load_library()
+    ctx = mpnl.context(dev.index)
+    h = ctypes.c_void_p()
+    sms = (ctypes.c_int * 2)()
+    assert lib.mpnl_sm_split_create(ctx, 24, ctypes.byref(h), sms) == mpnl.OK
+    assert sms[0] >= 24 and sms[1] >= 1
+    streams = []
+    for part in (0, 1, 1):
+        p = ctypes.c_void_p()
+        assert lib.mpnl_sm_split_stream(ctx, h, part, 0, ctypes.byref(p)) == mpnl.OK and p.value
+        streams.append(p.value)
+    assert len(set(streams)) == 3
+    p = ctypes.c_void_p()
+    assert lib.mpnl_sm_split_stream(ctx, h, 2, 0, ctypes.byref(p)) == mpnl.ERR_INVALID_ARG
+    assert lib.mpnl_sm_split_create(ctx, 24, None, sms) == mpnl.ERR_INVALID_ARG
+    assert lib.mpnl_sm_split_destroy(ctx, h) == mpnl.OK
+    assert lib.mpnl_sm_split_destroy(ctx, None) == mpnl.OK
 
 
 def test_memory_budget_limits_rounds(dev):
