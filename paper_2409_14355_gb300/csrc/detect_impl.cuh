@@ -44,8 +44,12 @@ namespace {
 
 constexpr int kThreads = 256;
 // Three CTAs per SM (about 80 registers a thread): measured faster than two
-// with more registers; the shared memory of the bench shape (73 KB) fits.
+// with more registers, and than four (64 registers: the FP32 walks spill,
+// 1.52 against 1.33 ms on the bench slot); the FP16-residual walks keep
+// their shift register in half the registers and run four (1.64 against
+// 1.69 ms).  The shared memory of the bench shape (52 KB) fits either way.
 constexpr int kCtasPerSm = 3;
+constexpr int ctas_per_sm(bool f16) { return f16 ? 4 : kCtasPerSm; }
 constexpr int kWarps = kThreads / 32;
 constexpr int kTopList = 64;  // entries of the first-level neighbour list
 constexpr int kList2 = 128;   // per symbol: entries of all second-level lists together
@@ -1193,7 +1197,7 @@ __device__ __noinline__ void detect_sc(const DetArgs args, int sc)
 }
 
 template <int NT, int QAM, bool F16, int SYM>
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) detect_walk_kernel(DetArgs args)
+__global__ void __launch_bounds__(kThreads, ctas_per_sm(F16)) detect_walk_kernel(DetArgs args)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     detect_body<NT, QAM, F16, SYM>(args, blockIdx.x, smem);
