@@ -201,6 +201,25 @@ def source_hash(paths) -> str:
     return h.hexdigest()[:16]
 
 
+def walk_hbm(n_sc, n_sym, nt, B, n_pe, launch_ms):
+    """The walk kernel against HBM, for completeness (it is ALU-bound):
+    algorithmic bytes of one launch -- reads R (packed), 1/R_ll, perm, the
+    table and z; writes hard decisions, LLRs and the PED pairs -- over its
+    live launch time, against the measured copy bandwidth."""
+    reads = n_sc * (nt * (nt + 1) // 2 * 8 + nt * 4 + nt + n_pe * nt) + n_sc * n_sym * nt * 8
+    writes = n_sc * n_sym * (nt + nt * B * 4 + 8)
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        pass
+    gbs = (reads + writes) / (launch_ms / 1e3) / 1e9
+    return {"bytes_per_launch": reads + writes, "read_bytes": reads, "write_bytes": writes,
+            "achieved_gbs": gbs, "peak_gbs": peak, "peak_note": "measured copy bandwidth",
+            "frac": gbs / peak if peak else None}
+
+
 def load_traffic(kernel_src: list[str]):
     """DRAM bytes per launch of the dominant kernel from the committed ncu
     summary, if it was taken on the current kernel source; else None."""
@@ -562,7 +581,8 @@ def run_mpnl(args):
                          "peak_note": f"{props.multi_processor_count} SMs x 128 FP32 lanes x 2 x "
                                       f"{sm_max:.0f} MHz (max SM clock)",
                          "peak_measured_ffma": probe_tflops,
-                         "frac_of_measured_ffma": achieved_tflops / probe_tflops},
+                         "frac_of_measured_ffma": achieved_tflops / probe_tflops,
+                         "hbm": walk_hbm(n_sc, n_sym, nt, B, n_pe, det_avg)},
             "sweep": sweep,
             "rank_lut": rank_lut,
             "rvd": rvd,
