@@ -314,6 +314,10 @@ int mpnl_detect_mixed(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const
  * hard decisions, LLRs and PED pairs (and the baseline's outputs) are copied
  * back -- all enqueued on `stream` in that order, so the results are in the
  * caller's buffers once the stream has reached the end of the call.  The
+ * baseline (it needs only H and Y) runs beside the path on a side stream of
+ * the context, forked from `stream` after the input copies and joined back
+ * before its outputs are copied; the context makes that stream on first use
+ * and serialises the fork and join of concurrent callers.  The
  * buffers may be host memory (pinned lets the copies run asynchronously;
  * pageable makes CUDA copy them synchronously) or device memory.
  *   H, Y                 in   as mpnl_preprocess (nt <= nr, or nr + nt <= MPNL_MAX_NR

@@ -11,16 +11,25 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <new>
 #include <vector>
 
 #include "mpnl.h"
 #include "mpnl_internal.h"
 
 struct mpnl_ctx {
-    int device;
-    unsigned *status;  // device word of kStatus* bits, cleared by mpnl_check_status
-    mpnl_tuning tuning;
-    char err[512];
+    int device = 0;
+    unsigned *status = nullptr;  // device word of kStatus* bits, cleared by mpnl_check_status
+    mpnl_tuning tuning{};
+    char err[512] = {};
+    // mpnl_detect_slot runs the MMSE baseline on a side stream of the
+    // context (made on first use), forked from and joined back into the
+    // caller's stream with these events; the mutex keeps a fork/join pair
+    // whole when several threads share the context
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    std::mutex side_mu;
 };
 
 namespace {
@@ -626,14 +635,14 @@ int mpnl_create(mpnl_ctx **out, int device)
         return MPNL_ERR_CUDA;
     }
     if (cudaSetDevice(device) != cudaSuccess) return MPNL_ERR_CUDA;
-    mpnl_ctx *ctx = (mpnl_ctx *)calloc(1, sizeof(mpnl_ctx));
+    mpnl_ctx *ctx = new (std::nothrow) mpnl_ctx;
     if (!ctx) return MPNL_ERR_CUDA;
     ctx->device = device;
     if (cudaMalloc(&ctx->status, sizeof(unsigned)) != cudaSuccess ||
         cudaMemset(ctx->status, 0, sizeof(unsigned)) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->status) cudaFree(ctx->status);
-        free(ctx);
+        delete ctx;
         return MPNL_ERR_CUDA;
     }
     *out = ctx;
@@ -644,8 +653,14 @@ void mpnl_destroy(mpnl_ctx *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    if (ctx->side) {
+        cudaStreamSynchronize(ctx->side);
+        cudaStreamDestroy(ctx->side);
+    }
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
     cudaFree(ctx->status);
-    free(ctx);
+    delete ctx;
 }
 
 const char *mpnl_last_error(const mpnl_ctx *ctx) { return ctx ? ctx->err : "context is NULL"; }
@@ -1114,6 +1129,29 @@ size_t mpnl_slot_workspace_bytes(const mpnl_dims *dims, int flags)
     return slot_layout(dims, flags).bytes;
 }
 
+// The context's side stream and fork/join events, made on first use (called
+// with side_mu held); false if CUDA cannot make them (the caller then runs
+// the baseline on its own stream).
+static bool side_ready(mpnl_ctx *ctx)
+{
+    if (ctx->side) return true;
+    cudaStream_t s = nullptr;
+    cudaEvent_t f = nullptr, j = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreateWithFlags(&f, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
+        ctx->side = s;
+        ctx->fork = f;
+        ctx->join = j;
+        return true;
+    }
+    cudaGetLastError();
+    if (s) cudaStreamDestroy(s);
+    if (f) cudaEventDestroy(f);
+    if (j) cudaEventDestroy(j);
+    return false;
+}
+
 int mpnl_detect_slot(mpnl_ctx *ctx, const mpnl_dims *d, float sigma2, const void *H,
                      const void *Y, uint8_t *hard, float *llr, float *ped2, uint8_t *mmse_hard,
                      float *mmse_llr, int flags, void *ws, size_t ws_bytes, void *stream)
@@ -1150,15 +1188,31 @@ int mpnl_detect_slot(mpnl_ctx *ctx, const mpnl_dims *d, float sigma2, const void
     const char *what = "slot input copy";
     cudaError_t e = cudaMemcpyAsync(dH, H, sc * d->nr * nt * 8, cudaMemcpyDefault, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dY, Y, sc * ns * d->nr * 8, cudaMemcpyDefault, st);
+    // the MMSE baseline needs only H and Y: on the context's side stream,
+    // beside the path, joined back before its outputs are copied
+    std::unique_lock<std::mutex> side_lock(ctx->side_mu, std::defer_lock);
+    bool forked = false;
+    if (e == cudaSuccess && mm) {
+        what = "mmse launch";
+        side_lock.lock();
+        if (side_ready(ctx)) {
+            e = cudaEventRecord(ctx->fork, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->fork, 0);
+            if (e == cudaSuccess)
+                e = mpnl::launch_mmse(d->n_sc, d->n_sym, d->nr, d->nt, d->qam, sigma2, dH, dY,
+                                      dMhard, mmse_llr ? dMllr : nullptr, ctx->side);
+            if (e == cudaSuccess) e = cudaEventRecord(ctx->join, ctx->side);
+            forked = e == cudaSuccess;
+        } else {
+            side_lock.unlock();
+            e = mpnl::launch_mmse(d->n_sc, d->n_sym, d->nr, d->nt, d->qam, sigma2, dH, dY, dMhard,
+                                  mmse_llr ? dMllr : nullptr, st);
+        }
+    }
     if (e == cudaSuccess) {
         what = "preprocess launch";
         e = mpnl::launch_preprocess(d->n_sc, d->n_sym, d->nr, d->nt, mqr ? sqrtf(sigma2) : 0.f, dH,
                                     dY, dR, dInv, dPerm, dZ, nullptr, st);
-    }
-    if (e == cudaSuccess && mm) {
-        what = "mmse launch";
-        e = mpnl::launch_mmse(d->n_sc, d->n_sym, d->nr, d->nt, d->qam, sigma2, dH, dY, dMhard,
-                              mmse_llr ? dMllr : nullptr, st);
     }
     if (e == cudaSuccess) {
         what = "select_paths launch";
@@ -1178,6 +1232,13 @@ int mpnl_detect_slot(mpnl_ctx *ctx, const mpnl_dims *d, float sigma2, const void
     if (e == cudaSuccess && llr)
         e = cudaMemcpyAsync(llr, dLlr, sc * ns * nt * B * 4, cudaMemcpyDefault, st);
     if (e == cudaSuccess && ped2) e = cudaMemcpyAsync(ped2, dPed, sc * ns * 8, cudaMemcpyDefault, st);
+    if (forked) {
+        // join even after an error, so that the workspace is not reused
+        // while the baseline still reads it
+        const cudaError_t j = cudaStreamWaitEvent(st, ctx->join, 0);
+        if (e == cudaSuccess) e = j;
+        side_lock.unlock();
+    }
     if (e == cudaSuccess && mm) e = cudaMemcpyAsync(mmse_hard, dMhard, sc * ns * nt, cudaMemcpyDefault, st);
     if (e == cudaSuccess && mm && mmse_llr)
         e = cudaMemcpyAsync(mmse_llr, dMllr, sc * ns * nt * B * 4, cudaMemcpyDefault, st);
