@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--snr-index", type=int, default=2)
     ap.add_argument("--ring", type=int, default=16, help="distinct slots cycled through (> L2)")
     ap.add_argument("--e2e-steps", type=int, default=40)
-    ap.add_argument("--inflight", type=int, default=2,
-                    help="slots in flight on their own streams (MMSE on a side stream each)")
+    ap.add_argument("--inflight", type=int, default=3,
+                    help="slots in flight on their own streams (MMSE on a side stream each); "
+                         "three keep the end-to-end path's copies off the critical path")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--precision", choices=["fp32", "fp16"], default="fp32",
