@@ -485,15 +485,25 @@ def run_mpnl(args):
             dms = sum(x.elapsed_time(y) for x, y in ev) / ks
             v, _ = whole_job_rate(ks * dets_per_step, t, dev)
             fl = npe * (4 * nt * nt + 4 * nt) * dets_per_step
-            # one slot alone through the whole path (QR + z, selection, walks,
-            # MMSE baseline), synchronised after each: the latency against
-            # the 0.5 ms slot at this N_pe
+            # one slot alone through the whole path (QR + z, selection, walks;
+            # the MMSE baseline beside them on a side stream, as in the main
+            # line's one-slot figure and in mpnl_detect_slot), synchronised
+            # after each: the latency against the 0.5 ms slot at this N_pe
             one = []
+            side = torch.cuda.Stream(dev)
             for i in range(20):
                 x0 = torch.cuda.Event(enable_timing=True)
                 x1 = torch.cuda.Event(enable_timing=True)
+                H, Y, s2 = ring[i % len(ring)]
                 x0.record(stream)
-                run_step(b2, npe, prec, i)
+                side.wait_event(x0)
+                with torch.cuda.stream(side):
+                    mpnl.linear_mmse(H, Y, s2, qam, out=(b2.mmse_hard, b2.mmse_llr))
+                mpnl.preprocess(H, Y, out=(b2.R, b2.inv_diag, b2.perm, b2.Z))
+                mpnl.select_paths(b2.R, s2, qam, npe, nt, out=b2.paths)
+                mpnl.detect(b2.R, b2.inv_diag, b2.perm, b2.paths, b2.Z, s2, qam,
+                            out=(b2.hard, b2.llr, b2.ped2), precision=prec)
+                stream.wait_stream(side)
                 x1.record(stream)
                 x1.synchronize()
                 one.append(x0.elapsed_time(x1))
@@ -502,7 +512,7 @@ def run_mpnl(args):
                           "ms_per_step": 1e3 * t / ks, "detect_ms": dms,
                           "detect_tflops": fl / (dms / 1e3) / 1e12,
                           "one_slot_ms": {"p50": one[len(one) // 2], "p99": one[-1],
-                                          "note": "20 slots, one at a time, MMSE in the same stream"}})
+                                          "note": "20 slots, one at a time, the MMSE baseline on a side stream"}})
             del b2
 
     # ---- the table-driven rank model beside the geometric one: the table's
