@@ -106,3 +106,26 @@ def test_c_abi_slot_call_with_host_buffers(dev, mmse_qr, precision, pinned):
                                 P(ws.data_ptr() + 16), nbytes, P(st.cuda_stream)) \
         == mpnl.ERR_INVALID_ARG
     assert np.all(out.hard.numpy() < sl.qam)
+
+
+@pytest.mark.parametrize("precision,mmse", [("fp32", True), ("fp16", False)])
+def test_slot_graph_replays_the_path(dev, precision, mmse):
+    """SlotGraph: a replay gives the per-call path's results on whatever the
+    fixed H and Y hold, slot after slot."""
+    from paper_2409_14355_gb300 import mpnl
+    slots = [inputs.make_slot(8, 8, 16, 61, 14, 15.0, "iid", 0.3, 700 + k) for k in range(3)]
+    sl = slots[0]
+    H = torch.from_numpy(sl.H).to(dev)
+    Y = torch.from_numpy(sl.Y).to(dev)
+    buf = mpnl.SlotBuffers(sl.n_sc, 14, sl.nr, sl.nt, sl.qam, 64, dev, mmse=mmse)
+    g = mpnl.SlotGraph(buf, H, Y, sl.sigma2, mmse=mmse, precision=precision)
+    ref = mpnl.SlotBuffers(sl.n_sc, 14, sl.nr, sl.nt, sl.qam, 64, dev, mmse=mmse)
+    for s in slots:
+        H.copy_(torch.from_numpy(s.H))
+        Y.copy_(torch.from_numpy(s.Y))
+        g.replay()
+        mpnl.run_slot(ref, H, Y, sl.sigma2, mmse=mmse, precision=precision)
+        torch.cuda.synchronize()
+        for name in ("paths", "hard", "llr", "ped2") + (("mmse_hard", "mmse_llr") if mmse else ()):
+            assert torch.equal(getattr(buf, name), getattr(ref, name)), name
+    mpnl.check_status()
