@@ -941,6 +941,7 @@ def run_serving(args, dev, sm_split: int = 0, capacity: float | None = None):
         loads[str(rho)] = st
     sms = list(server.split_sms) if server.split_sms is not None else None
     server.close()
+    realtime = [serving_realtime(dev, n_pe) for n_pe in (32, 64)] if sm_split == 0 else None
     n_big = sum(1 for u in units if (u.nr, u.nt, u.qam, u.n_sc) == (16, 16, 64, 3276))
     return {"workload": f"{len(units)} radio units ({n_big} of them 16x16 64-QAM 3276 sc), "
                         f"sizes as the mixed batch, Poisson slot requests, channel update every "
@@ -948,7 +949,46 @@ def run_serving(args, dev, sm_split: int = 0, capacity: float | None = None):
                         f"slot", "deadline_ms": 0.5,
             "capacity_detections_per_s": capacity, "own_capacity_detections_per_s": own_capacity,
             "sm_split": sms, "seconds_per_load": args.serving_seconds,
-            "resident_state_MB": server.state_bytes / 1e6, "loads": loads}
+            "resident_state_MB": server.state_bytes / 1e6, "loads": loads,
+            "realtime": realtime}
+
+
+def serving_realtime(dev, n_pe: int, slots: int = 2000, warm: int = 200) -> dict:
+    """The real-time load of one 16x16 64-QAM 3276-subcarrier radio unit
+    through the serving loop: a slot request every 0.5 ms (the slot period),
+    a channel update with every 8th, the LLRs computed into the slot's
+    device buffers and left there for a decoder on the device (the hard
+    decisions are copied back).  p50/p99 latency and the deadline-miss rate
+    over `slots` slots after `warm` warm-up slots."""
+    import torch
+
+    from paper_2409_14355_gb300 import serving
+
+    u = inputs.UnitSpec(16, 16, 64, 3276, n_pe, 21.0, "iid", 12345)
+    sl = inputs.unit_slot(u)
+    server = serving.Server(dev, mem_budget=4 << 30, llr_to_host=False)
+    server.register(serving.RU(0, u.nr, u.nt, u.qam, u.n_sc, u.n_pe, sl.sigma2),
+                    torch.from_numpy(sl.H))
+    alts = [inputs.unit_slot(inputs.UnitSpec(**{**u.__dict__, "seed": u.seed + j}))
+            for j in range(1, 4)]
+    payloads = {0: {"slot": [torch.from_numpy(a.Y).pin_memory() for a in [sl] + alts],
+                    "channel": [torch.from_numpy(a.H).pin_memory() for a in alts]}}
+
+    def trace(n):
+        out = []
+        for i in range(n):
+            if i % 8 == 7:
+                out.append((i * serving.DEADLINE_S, 0, "channel"))
+            out.append((i * serving.DEADLINE_S, 0, "slot"))
+        return out
+
+    serving.run_trace(server, trace(warm), payloads)
+    st = serving.latency_stats(serving.run_trace(server, trace(slots), payloads))
+    server.close()
+    return {"workload": "one 16x16 64-QAM 3276-sc radio unit, a slot every 0.5 ms, channel "
+                        "update every 8th slot, LLRs left on the device", "n_pe": n_pe,
+            "slots": st["slots_done"], "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "miss_rate": st["miss_rate"]}
 
 
 def main():

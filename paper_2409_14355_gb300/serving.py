@@ -90,7 +90,7 @@ class SlotBuffers:
     """Device and pinned host buffers of one in-flight slot request of an RU
     (allocated at registration, reused)."""
 
-    def __init__(self, ru: "RU", device, llr: bool):
+    def __init__(self, ru: "RU", device, llr: bool, llr_to_host: bool = True):
         n_sc, n_sym, nr, nt = ru.n_sc, ru.n_sym, ru.nr, ru.nt
         kw = dict(device=device)
         self.Y = torch.empty((n_sc, n_sym, nr), dtype=torch.complex64, **kw)
@@ -100,8 +100,9 @@ class SlotBuffers:
                     if llr else None)
         pin = device.type == "cuda"
         self.hard_host = torch.empty(self.hard.shape, dtype=torch.uint8, pin_memory=pin)
+        # None when the LLRs stay on the device (for a decoder there)
         self.llr_host = (torch.empty(self.llr.shape, dtype=torch.float32, pin_memory=pin)
-                         if llr else None)
+                         if llr and llr_to_host else None)
 
 
 @dataclass
@@ -173,12 +174,16 @@ class Server:
                  big_cost: float = 936 * 14 * 64 * 16 * 20, max_large_rounds: int | None = None,
                  share_sms: bool = False, large_per_unit: bool = True,
                  small_short_ctas: bool = True, native_rounds: bool = True,
-                 sm_split: int = 0):
+                 sm_split: int = 0, llr_to_host: bool = True):
         self.device = (torch.device("cuda", torch.cuda.current_device()) if device is None
                        else torch.device(device))
         self.mem_budget = int(mem_budget)
         self.max_units = int(max_units_per_round)
         self.llr = llr
+        # llr_to_host False: the LLRs are computed into the slot's device
+        # buffer and left there (a decoder on the device reads them); only
+        # the hard decisions are copied back
+        self.llr_to_host = llr_to_host
         self.starve_s = starve_s
         self.slots_per_ru = slots_per_ru
         self.big_cost = big_cost  # units at least this costly form rounds of their own
@@ -232,7 +237,8 @@ class Server:
                   perm=torch.empty((n_sc, nt), dtype=torch.uint8, device=dev),
                   paths=torch.empty((n_sc, ru.n_pe, nt), dtype=torch.uint8, device=dev))
         ru.state = st
-        ru.pool = [SlotBuffers(ru, dev, self.llr) for _ in range(self.slots_per_ru)]
+        ru.pool = [SlotBuffers(ru, dev, self.llr, self.llr_to_host)
+                   for _ in range(self.slots_per_ru)]
         ru.H_dev = torch.empty((n_sc, nr, nt), dtype=torch.complex64, device=dev)
         # the unit's resident state as a batch item: what a round's request refers to
         ru.item = mpnl.batch_item(ru.dims, ru.sigma2, self._unit_flags(ru), 0, Q=st["Q"], R=st["R"],
@@ -307,11 +313,12 @@ class Server:
                     if ru.update_round == r.round_id:
                         ru.update_round = -1
                     if q.bufs is not None:
+                        llr = q.bufs.llr_host if q.bufs.llr_host is not None else q.bufs.llr
                         if self.keep_results:
                             q.hard = q.bufs.hard_host.clone()
-                            q.llr = q.bufs.llr_host.clone() if q.bufs.llr_host is not None else None
+                            q.llr = llr.clone() if llr is not None else None
                         else:
-                            q.hard, q.llr = q.bufs.hard_host, q.bufs.llr_host
+                            q.hard, q.llr = q.bufs.hard_host, llr
                         ru.pool.append(q.bufs)
                         q.bufs = None
                 self.in_use -= r.bytes
@@ -445,7 +452,7 @@ class Server:
             for q in reqs:
                 if q.bufs is not None:
                     q.bufs.hard_host.copy_(q.bufs.hard, non_blocking=True)
-                    if q.bufs.llr is not None:
+                    if q.bufs.llr_host is not None:
                         q.bufs.llr_host.copy_(q.bufs.llr, non_blocking=True)
             r.event = torch.cuda.Event()
             r.event.record(st)
@@ -476,7 +483,7 @@ class Server:
                 c.staging, c.Z, c.hard = b.Y.data_ptr(), b.Z.data_ptr(), b.hard.data_ptr()
                 c.hard_host = b.hard_host.data_ptr()
                 c.llr = b.llr.data_ptr() if b.llr is not None else None
-                c.llr_host = b.llr_host.data_ptr() if b.llr is not None else None
+                c.llr_host = b.llr_host.data_ptr() if b.llr_host is not None else None
         flags = (mpnl.RUN_SHARE_SMS if big and self.share_sms else 0) \
             | (mpnl.RUN_SHORT_CTAS if not big and self.small_short_ctas else 0)
         r.batch.serve_round(rc, len(reqs), flags, stream=st)
@@ -511,7 +518,7 @@ class Server:
                                 ru.qam, want_llr=b.llr is not None, want_ped2=False,
                                 out=(b.hard, b.llr, None), precision=ru.precision)
                     b.hard_host.copy_(b.hard, non_blocking=True)
-                    if b.llr is not None:
+                    if b.llr_host is not None:
                         b.llr_host.copy_(b.llr, non_blocking=True)
             r.event = torch.cuda.Event()
             r.event.record(st)

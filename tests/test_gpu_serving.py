@@ -78,6 +78,13 @@ def test_serving_results_equal_each_request_alone(dev):
     _serve_and_compare(dev)
 
 
+def test_serving_with_llrs_left_on_the_device(dev):
+    """llr_to_host=False: the LLRs are computed into each slot's device
+    buffer and not copied back; they equal the per-call path's."""
+    server = _serve_and_compare(dev, llr_to_host=False)
+    assert all(b.llr_host is None for ru in server.rus.values() for b in ru.pool)
+
+
 def test_serving_on_an_sm_split_equals_each_request_alone(dev):
     """The same with the small units' rounds on a group of SMs of their own
     (green contexts) and the large ones on the rest: the class boundary is
@@ -123,7 +130,8 @@ def _serve_and_compare(dev, **server_kw):
         ru = server.rus[q.ru]
         hard, llr = _alone(dev, ru, current[q.ru], q.payload)
         assert torch.equal(q.hard, hard), (q.rid, q.ru)
-        assert torch.equal(q.llr, llr), (q.rid, q.ru)
+        assert torch.equal(q.llr.cpu(), llr), (q.rid, q.ru)
+        assert q.llr.device.type == ("cpu" if server.llr_to_host else "cuda")
         n_cmp += 1
     assert n_cmp > 20
     if "big_cost" in server_kw:   # both size classes were served
