@@ -1,6 +1,7 @@
 """The bench configuration at full size, and the BER rule at every SNR point.
 
-* Full slot (16x16 64-QAM, 3276 subcarriers x 14 symbols, N_pe = 256): every
+* Full slot (16x16 64-QAM, 3276 subcarriers x 14 symbols, N_pe = 256, and
+  the paper's N_p = 32, the configuration that meets the slot deadline): every
   one of the 45,864 detections is compared with the FP64 oracle, end to end
   and stage-isolated (the walks fed the oracle's own R, z, order and table
   rounded to float32).  A detection is held to bit-exact decisions, and its
@@ -65,11 +66,11 @@ def _report(name, g, ref, sigma2):
     return mism, unexplained
 
 
-def test_full_slot_end_to_end(dev):
+@pytest.mark.parametrize("n_pe", [256, 32])
+def test_full_slot_end_to_end(dev, n_pe):
     from paper_2409_14355_gb300 import mpnl
 
     sl = inputs.workload_slot("16x16-64qam-3276sc", 2)
-    n_pe = 256
     buf = mpnl.SlotBuffers(sl.n_sc, sl.n_sym, sl.nr, sl.nt, sl.qam, n_pe, dev, mmse=True)
     mpnl.run_slot(buf, _t(sl.H, dev), _t(sl.Y, dev), sl.sigma2, mmse=True)
     mpnl.check_status()
@@ -77,7 +78,7 @@ def test_full_slot_end_to_end(dev):
                              with_mmse=True, tie_eps=P.TIE_EPS)
     g = dict(hard=buf.hard.cpu().numpy(), llr=buf.llr.cpu().numpy().astype(np.float64),
              ped2=buf.ped2.cpu().numpy().astype(np.float64))
-    mism, _ = _report("full slot end to end", g, ref, sl.sigma2)
+    mism, _ = _report(f"full slot end to end, N_pe {n_pe}", g, ref, sl.sigma2)
     # end to end R and z carry the float32 QR's error (the near-tie width
     # scales with kappa(H)), so the count is held overall, not per near-tie
     assert mism.mean() <= 0.02
@@ -87,11 +88,11 @@ def test_full_slot_end_to_end(dev):
     assert np.mean(np.all(mh == ref["mmse_hard"], axis=-1)) >= 0.999
 
 
-def test_full_slot_stage_isolated(dev):
+@pytest.mark.parametrize("n_pe", [256, 32])
+def test_full_slot_stage_isolated(dev, n_pe):
     from paper_2409_14355_gb300 import mpnl
 
     sl = inputs.workload_slot("16x16-64qam-3276sc", 2)
-    n_pe = 256
     H64, Y64 = sl.H.astype(np.complex128), sl.Y.astype(np.complex128)
     Rr, pr, Zr, _ = P.oracle_front(H64, Y64)
     R32, Z32, inv32 = P.to_fp32_inputs(Rr, Zr)
@@ -112,7 +113,7 @@ def test_full_slot_stage_isolated(dev):
     with cf.ThreadPoolExecutor(_threads()) as ex:   # the C oracle runs outside the GIL
         outs = list(ex.map(one, range(sl.n_sc)))
     ref = {k: np.stack([o[k] for o in outs]) for k in ("hard", "llr", "ped2", "flip_floor")}
-    mism, unexplained = _report("full slot stage-isolated", g, ref, sl.sigma2)
+    mism, unexplained = _report(f"full slot stage-isolated, N_pe {n_pe}", g, ref, sl.sigma2)
     assert unexplained.sum() == 0
     assert mism.mean() <= 0.02
     # PEDs and LLRs at the float32 tolerances wherever they are unique
@@ -150,3 +151,8 @@ def test_ber_every_snr_point_8x8_16qam(dev, precision):
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
 def test_ber_every_snr_point_16x16_64qam(dev, precision):
     _per_snr(dev, "16x16-64qam-3276sc", 256, 160, precision)
+
+
+def test_ber_every_snr_point_16x16_64qam_at_the_papers_n_p(dev):
+    # the paper's N_p = 32 (its link simulations), FP32
+    _per_snr(dev, "16x16-64qam-3276sc", 32, 160, "fp32")
