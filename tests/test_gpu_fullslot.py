@@ -88,6 +88,29 @@ def test_full_slot_end_to_end(dev, n_pe):
     assert np.mean(np.all(mh == ref["mmse_hard"], axis=-1)) >= 0.999
 
 
+def test_full_slot_mmse_extended_qr(dev):
+    """The walks over the MMSE-extended sorted QR ([H; sigma I], the reading
+    for more users than antennas) on the bench slot in full, end to end,
+    against the oracle with the same pre-processing: the same rule as the
+    plain path (bit-exact decisions outside near-ties, at most 2% explained
+    mismatches) and the BER within 1e-3."""
+    from paper_2409_14355_gb300 import mpnl
+
+    sl = inputs.workload_slot("16x16-64qam-3276sc", 2)
+    n_pe = 256
+    buf = mpnl.SlotBuffers(sl.n_sc, sl.n_sym, sl.nr, sl.nt, sl.qam, n_pe, dev, mmse=False)
+    mpnl.run_slot(buf, _t(sl.H, dev), _t(sl.Y, dev), sl.sigma2, mmse=False, mmse_qr=True)
+    mpnl.check_status()
+    ref = oracle.detect_slot(sl.H, sl.Y, sl.sigma2, sl.qam, n_pe, n_threads=_threads(),
+                             tie_eps=P.TIE_EPS, mmse_qr=True)
+    g = dict(hard=buf.hard.cpu().numpy(), llr=buf.llr.cpu().numpy().astype(np.float64),
+             ped2=buf.ped2.cpu().numpy().astype(np.float64))
+    mism, _ = _report("full slot end to end, MMSE-extended QR", g, ref, sl.sigma2)
+    assert mism.mean() <= 0.02
+    B = oracle.BITS[sl.qam]
+    assert abs(_ber(g["hard"], sl.labels, B) - _ber(ref["hard"], sl.labels, B)) <= 1e-3
+
+
 @pytest.mark.parametrize("n_pe", [256, 32])
 def test_full_slot_stage_isolated(dev, n_pe):
     from paper_2409_14355_gb300 import mpnl
