@@ -1,6 +1,6 @@
 // Linear MMSE baseline, one warp per subcarrier (4 subcarriers per CTA).
 //
-//   A = H^H H + sigma2 I = L L^H        (Cholesky in shared memory)
+//   A = H^H H + sigma2 I = L L^H        (right-looking Cholesky in shared memory)
 //   W = A^{-1} H^H                      (lane r solves for receive column r)
 //   (A^{-1})_kk = || L^{-1} e_k ||^2    (lane k)
 //   mu_k = (W H)_kk = 1 - sigma2 (A^{-1})_kk  (since W H = I - sigma2 A^{-1})
@@ -95,26 +95,32 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
         sL[i * nt + j] = a;
     }
     __syncwarp();
-    // Cholesky, column by column (left-looking)
+    // Cholesky, right-looking: at step j column j is finished (L_jj = the
+    // square root of the updated diagonal, L_ij = the updated entry / L_jj)
+    // and every trailing entry (i, m), i >= m > j, loses L_ij conj(L_mj).  An
+    // entry receives its terms in the order 0, 1, ..., as the left-looking
+    // recurrence subtracts them, in the same arithmetic (the diagonal's real
+    // part loses |L_mj|^2); the trailing updates spread over the lanes.
     for (int j = 0; j < nt; ++j) {
-        if (lane == 0) {
-            float s = sL[j * nt + j].x;
-            for (int k = 0; k < j; ++k) {
-                const float2 v = sL[j * nt + k];
-                s -= v.x * v.x + v.y * v.y;
-            }
-            sL[j * nt + j] = make_float2(sqrtf(s), 0.f);
+        const float ljj = sqrtf(sL[j * nt + j].x);
+        for (int i = j + 1 + lane; i < nt; i += 32) {
+            const float2 t = sL[i * nt + j];
+            sL[i * nt + j] = make_float2(t.x / ljj, t.y / ljj);
         }
         __syncwarp();
-        const float ljj = sL[j * nt + j].x;
-        for (int i = j + 1 + lane; i < nt; i += 32) {
-            float2 t = sL[i * nt + j];
-            for (int k = 0; k < j; ++k) {
-                const float2 p = cmulc(sL[i * nt + k], sL[j * nt + k]);
-                t.x -= p.x;
-                t.y -= p.y;
-            }
-            sL[i * nt + j] = make_float2(t.x / ljj, t.y / ljj);
+        if (lane == 0) sL[j * nt + j] = make_float2(ljj, 0.f);
+        const int w = nt - 1 - j;  // trailing order
+        for (int p = lane; p < w * (w + 1) / 2; p += 32) {
+            // p-th trailing entry, row by row: row ii holds ii + 1 entries
+            int ii = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+            if ((ii + 1) * (ii + 2) / 2 <= p) ++ii;
+            if (ii * (ii + 1) / 2 > p) --ii;
+            const int i = j + 1 + ii, m = j + 1 + (p - ii * (ii + 1) / 2);
+            const float2 q = cmulc(sL[i * nt + j], sL[m * nt + j]);
+            float2 v = sL[i * nt + m];
+            v.x -= q.x;
+            v.y -= q.y;
+            sL[i * nt + m] = v;
         }
         __syncwarp();
     }
@@ -204,15 +210,21 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
             (uint8_t)join_label<QAM>(Qam<QAM>::axis_label(ire), Qam<QAM>::axis_label(iim));
         if (llr != nullptr) {
             const float inu = 1.0f / sNu[k];
+            // squared distances to the axis points, once per axis
+            float dx[LQ], dy[LQ];
+#pragma unroll
+            for (int i = 0; i < LQ; ++i) {
+                const float a = x.x - axis_pos<QAM>(i), c = x.y - axis_pos<QAM>(i);
+                dx[i] = a * a;
+                dy[i] = c * c;
+            }
 #pragma unroll
             for (int b = 0; b < B; ++b) {
-                const float c = (b & 1) ? x.y : x.x;
                 const int tb = b >> 1;  // bit position within the axis label, MSB first
                 float m0 = INFINITY, m1 = INFINITY;
 #pragma unroll
                 for (int i = 0; i < LQ; ++i) {
-                    float dv = c - axis_pos<QAM>(i);
-                    dv *= dv;
+                    const float dv = (b & 1) ? dy[i] : dx[i];
                     if ((Qam<QAM>::axis_label(i) >> (HB - 1 - tb)) & 1) m1 = fminf(m1, dv);
                     else m0 = fminf(m0, dv);
                 }
