@@ -27,13 +27,13 @@ __host__ __device__ inline MmseSmem mmse_smem_layout(int nr, int nt, int n_sym)
     MmseSmem s;
     int o = 0;
     s.off_h = o;
-    o += nr * nt * 8;
+    o += nr * (nt + 1) * 8;  // rows padded by one element: column reads spread over banks
     s.off_y = o;
     o += n_sym * nr * 8;
     s.off_l = o;
-    o += nt * nt * 8;
+    o += nt * (nt + 1) * 8;
     s.off_w = o;
-    o += nt * nr * 8;
+    o += nt * (nr + 1) * 8;
     s.off_nu = o;
     o += nt * 4;
     s.off_imu = o;
@@ -72,12 +72,19 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
     float2 *sY = reinterpret_cast<float2 *>(base + S.off_y);
     float2 *sL = reinterpret_cast<float2 *>(base + S.off_l);  // A, then its Cholesky factor
     float2 *sW = reinterpret_cast<float2 *>(base + S.off_w);
+    // row strides, one element longer than the rows: lanes that walk a
+    // column (16 lanes reading W rows, H columns, L columns) hit different
+    // banks instead of one
+    const int ldh = nt + 1, ldl = nt + 1, ldw = nr + 1;
     float *sNu = reinterpret_cast<float *>(base + S.off_nu);
     float *sImu = reinterpret_cast<float *>(base + S.off_imu);
 
     const float2 *gH = H + (size_t)sc * nr * nt;
     const float2 *gY = Y + (size_t)sc * n_sym * nr;
-    for (int k = lane; k < nr * nt; k += 32) sH[k] = gH[k];
+    for (int k = lane; k < nr * nt; k += 32) {
+        const int r = k / nt;
+        sH[r * ldh + (k - r * nt)] = gH[k];
+    }
     for (int k = lane; k < n_sym * nr; k += 32) sY[k] = gY[k];
     __syncwarp();
 
@@ -87,12 +94,12 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
         if (j > i) continue;
         float2 a = make_float2(0.f, 0.f);
         for (int r = 0; r < nr; ++r) {
-            const float2 hi = sH[r * nt + i], hj = sH[r * nt + j];
+            const float2 hi = sH[r * ldh + i], hj = sH[r * ldh + j];
             a.x = fmaf(hi.x, hj.x, fmaf(hi.y, hj.y, a.x));
             a.y = fmaf(hi.x, hj.y, fmaf(-hi.y, hj.x, a.y));
         }
         if (i == j) a = make_float2(a.x + sigma2, 0.f);
-        sL[i * nt + j] = a;
+        sL[i * ldl + j] = a;
     }
     __syncwarp();
     // Cholesky, right-looking: at step j column j is finished (L_jj = the
@@ -102,13 +109,13 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
     // recurrence subtracts them, in the same arithmetic (the diagonal's real
     // part loses |L_mj|^2); the trailing updates spread over the lanes.
     for (int j = 0; j < nt; ++j) {
-        const float ljj = sqrtf(sL[j * nt + j].x);
+        const float ljj = sqrtf(sL[j * ldl + j].x);
         for (int i = j + 1 + lane; i < nt; i += 32) {
-            const float2 t = sL[i * nt + j];
-            sL[i * nt + j] = make_float2(t.x / ljj, t.y / ljj);
+            const float2 t = sL[i * ldl + j];
+            sL[i * ldl + j] = make_float2(t.x / ljj, t.y / ljj);
         }
         __syncwarp();
-        if (lane == 0) sL[j * nt + j] = make_float2(ljj, 0.f);
+        if (lane == 0) sL[j * ldl + j] = make_float2(ljj, 0.f);
         const int w = nt - 1 - j;  // trailing order
         for (int p = lane; p < w * (w + 1) / 2; p += 32) {
             // p-th trailing entry, row by row: row ii holds ii + 1 entries
@@ -116,11 +123,11 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
             if ((ii + 1) * (ii + 2) / 2 <= p) ++ii;
             if (ii * (ii + 1) / 2 > p) --ii;
             const int i = j + 1 + ii, m = j + 1 + (p - ii * (ii + 1) / 2);
-            const float2 q = cmulc(sL[i * nt + j], sL[m * nt + j]);
-            float2 v = sL[i * nt + m];
+            const float2 q = cmulc(sL[i * ldl + j], sL[m * ldl + j]);
+            float2 v = sL[i * ldl + m];
             v.x -= q.x;
             v.y -= q.y;
-            sL[i * nt + m] = v;
+            sL[i * ldl + m] = v;
         }
         __syncwarp();
     }
@@ -130,15 +137,15 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
 #pragma unroll
         for (int i = 0; i < NT; ++i) {
             if (i < nt) {
-                const float2 h = sH[r * nt + i];
+                const float2 h = sH[r * ldh + i];
                 float2 t = make_float2(h.x, -h.y);
 #pragma unroll
                 for (int k = 0; k < i; ++k) {
-                    const float2 p = cmul(sL[i * nt + k], u[k]);
+                    const float2 p = cmul(sL[i * ldl + k], u[k]);
                     t.x -= p.x;
                     t.y -= p.y;
                 }
-                const float il = 1.0f / sL[i * nt + i].x;
+                const float il = 1.0f / sL[i * ldl + i].x;
                 u[i] = make_float2(t.x * il, t.y * il);
             }
         }
@@ -149,14 +156,14 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
 #pragma unroll
                 for (int k = i + 1; k < NT; ++k) {
                     if (k < nt) {
-                        const float2 p = cmulc(u[k], sL[k * nt + i]);  // conj(L_ki) v_k
+                        const float2 p = cmulc(u[k], sL[k * ldl + i]);  // conj(L_ki) v_k
                         t.x -= p.x;
                         t.y -= p.y;
                     }
                 }
-                const float il = 1.0f / sL[i * nt + i].x;
+                const float il = 1.0f / sL[i * ldl + i].x;
                 u[i] = make_float2(t.x * il, t.y * il);
-                sW[i * nr + r] = u[i];
+                sW[i * ldw + r] = u[i];
             }
         }
     }
@@ -172,12 +179,12 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
 #pragma unroll
                 for (int m = 0; m < i; ++m) {
                     if (m >= k) {
-                        const float2 p = cmul(sL[i * nt + m], u[m]);
+                        const float2 p = cmul(sL[i * ldl + m], u[m]);
                         t.x -= p.x;
                         t.y -= p.y;
                     }
                 }
-                const float il = 1.0f / sL[i * nt + i].x;
+                const float il = 1.0f / sL[i * ldl + i].x;
                 u[i] = make_float2(t.x * il, t.y * il);
                 acc = fmaf(u[i].x, u[i].x, fmaf(u[i].y, u[i].y, acc));
             } else {
@@ -195,7 +202,7 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
         const int s = t / nt, k = t - s * nt;
         float2 x = make_float2(0.f, 0.f);
         for (int r = 0; r < nr; ++r) {
-            const float2 p = cmul(sW[k * nr + r], sY[s * nr + r]);
+            const float2 p = cmul(sW[k * ldw + r], sY[s * nr + r]);
             x.x += p.x;
             x.y += p.y;
         }
@@ -218,6 +225,7 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
                 dx[i] = a * a;
                 dy[i] = c * c;
             }
+            float lv[B];
 #pragma unroll
             for (int b = 0; b < B; ++b) {
                 const int tb = b >> 1;  // bit position within the axis label, MSB first
@@ -228,7 +236,18 @@ __device__ __forceinline__ void mmse_warp(int sc, int n_sym, int nr, int nt, flo
                     if ((Qam<QAM>::axis_label(i) >> (HB - 1 - tb)) & 1) m1 = fminf(m1, dv);
                     else m0 = fminf(m0, dv);
                 }
-                llr[(det * nt + k) * B + b] = (m1 - m0) * inu;
+                lv[b] = (m1 - m0) * inu;
+            }
+            // B is even, so every row is as aligned as the array: pairs when
+            // that is 8 bytes (the ABI promises only 4)
+            float *row = llr + (det * nt + k) * B;
+            if ((reinterpret_cast<uintptr_t>(llr) & 7u) == 0) {
+#pragma unroll
+                for (int b = 0; b < B; b += 2)
+                    reinterpret_cast<float2 *>(row)[b >> 1] = make_float2(lv[b], lv[b + 1]);
+            } else {
+#pragma unroll
+                for (int b = 0; b < B; ++b) row[b] = lv[b];
             }
         }
     }

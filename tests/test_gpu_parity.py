@@ -395,3 +395,24 @@ def test_host_entry_point_matches_device_path(dev):
     assert out_h["hard"].device.type == "cpu"
     for k in ("hard", "llr", "ped2", "mmse_hard", "mmse_llr"):
         assert torch.equal(out_h[k], out_d[k].cpu()), k
+
+
+def test_mmse_llr_array_on_a_4_byte_boundary(dev):
+    """The ABI promises 4-byte alignment for float arrays: an LLR array that
+    starts 4 bytes past an 8-byte boundary gets the same values (the kernel
+    writes pairs only when the array is 8-byte aligned)."""
+    import ctypes
+    mpnl = _mpnl()
+    sl = inputs.make_slot(8, 8, 16, 40, 14, 15.0, "iid", 0.3, 9)
+    H, Y = _t(sl.H, dev), _t(sl.Y, dev)
+    hard, llr = mpnl.linear_mmse(H, Y, sl.sigma2, sl.qam)
+    buf = torch.zeros(llr.numel() + 1, dtype=torch.float32, device=dev)
+    hard2 = torch.empty_like(hard)
+    d = mpnl.Dims(sl.n_sc, 14, sl.nr, sl.nt, sl.qam, 1)
+    st = mpnl.load_library().mpnl_linear_mmse(
+        mpnl.context(dev.index), ctypes.byref(d), H.data_ptr(), Y.data_ptr(),
+        ctypes.c_float(sl.sigma2), hard2.data_ptr(), buf.data_ptr() + 4, None, None)
+    torch.cuda.synchronize()
+    assert st == mpnl.OK
+    assert torch.equal(hard2, hard)
+    assert torch.equal(buf[1:].view_as(llr), llr)
