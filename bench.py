@@ -570,6 +570,11 @@ def run_mpnl(args):
             v, thr, n_used, dt = time_oracle(sl0, qam, n_pe, args.cpu_seconds, keep=kept)
             accuracy = accuracy_vs_oracle(sl0, kept[0], n_used, qam, n_pe, dev)
             accuracy["per_snr"] = accuracy_per_snr(args.workload, n_pe, dev)
+            # the 8x8 16-QAM Kronecker-correlated workload's SNR sweep (the
+            # MPNL walks at N_pe 64 against the linear MMSE baseline), whole slots
+            if args.workload != "8x8-16qam-936sc":
+                accuracy["per_snr_8x8_16qam_kronecker"] = accuracy_per_snr(
+                    "8x8-16qam-936sc", 64, dev, n_sc=936)
             v1, _, n1, dt1 = time_oracle(sl0, qam, n_pe, args.cpu_seconds / 3, n_threads=1)
             cpu = {"value": v, "unit": UNIT, "cores": thr, "kind": "oracle",
                    "sample": f"{n_used} of {n_sc} subcarriers x 14 symbols of one slot "
