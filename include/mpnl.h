@@ -317,7 +317,11 @@ int mpnl_detect_mixed(mpnl_ctx *ctx, const mpnl_dims *dims, const void *R, const
  * baseline (it needs only H and Y) runs beside the path on a side stream of
  * the context, forked from `stream` after the input copies and joined back
  * before its outputs are copied; the context makes that stream on first use
- * and serialises the fork and join of concurrent callers.  The
+ * and serialises the fork and join of concurrent callers.  A call made while
+ * `stream` is being captured into a CUDA graph draws the side stream into
+ * that capture until the capture ends, so no other call with MPNL_SLOT_MMSE
+ * may use the same context in between (a capturing thread takes a context
+ * of its own).  The
  * buffers may be host memory (pinned lets the copies run asynchronously;
  * pageable makes CUDA copy them synchronously) or device memory.
  *   H, Y                 in   as mpnl_preprocess (nt <= nr, or nr + nt <= MPNL_MAX_NR

@@ -317,6 +317,11 @@ class Server:
                         if self.keep_results:
                             q.hard = q.bufs.hard_host.clone()
                             q.llr = llr.clone() if llr is not None else None
+                            if llr is not None and llr.is_cuda:
+                                # the device copy runs on the current stream; it
+                                # must be done before the buffer goes back to the
+                                # pool, where a round on another stream reuses it
+                                torch.cuda.current_stream(llr.device).synchronize()
                         else:
                             q.hard, q.llr = q.bufs.hard_host, llr
                         ru.pool.append(q.bufs)
