@@ -43,7 +43,16 @@
 //
 // A vector is keyed by 16 bytes (two u64, level nt-1 in the most significant
 // byte): comparing keys as unsigned integers is the lexicographic order from
-// the top level down, and the key bytes are the ranks written out.
+// the top level down, and the key bytes are the ranks written out.  For
+// N_pe >= 128 a narrower form runs first (select_group_narrow): one u64 key
+// with a field per level only as wide as the bound allows, and two lists
+// merged into in place, so that a group needs under half the shared memory.
+//
+// The bound is tightened from the single-deviation bound where there is
+// one; where all single deviations together are fewer than N_pe (none), the
+// bisection starts from the largest cost of a two-deviation vector instead,
+// provided that N_pe of those exist (16 levels of 64-QAM at N_pe 1024:
+// 5.3 -> 1.8 ms for 3276 subcarriers).
 #include "mpnl_common.cuh"
 #include "mpnl_internal.h"
 
@@ -113,30 +122,36 @@ struct RankLut {
 // real-valued decomposition (ranks 1..L, Pe = 2 (1 - 1/L) Q(.) per level).
 enum SelMode { kSelGeo = 0, kSelLut = 1, kSelPam = 2 };
 
-template <int QAM, int G, int MODE = kSelGeo>
-__device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, float sigma2,
-                                               const float2 *__restrict__ Rp,
-                                               uint8_t *__restrict__ paths, int base_off,
-                                               int group, int tid, RankLut lut = RankLut{})
+// Cost of rank 1 + j at level m under the cost model (w: the levels'
+// weights, or for a table the levels' bins), and the same in fixed point
+// (rounded to nearest, clamped to kCostMax).
+template <int QAM, int MODE>
+__device__ __forceinline__ float sel_shift_cost(const float *w, const RankLut &lut, int m, int j)
+{
+    if constexpr (MODE == kSelLut) return __ldg(lut.cost + (size_t)__float_as_int(w[m]) * QAM + j);
+    else return (float)j * w[m];
+}
+
+template <int QAM, int MODE>
+__device__ __forceinline__ unsigned long long sel_shift_q(const float *w, const RankLut &lut, int m,
+                                                          int j)
+{
+    return __float2ull_rn(fminf(sel_shift_cost<QAM, MODE>(w, lut, m, j), kCostMax) * kCostScale);
+}
+
+// The weights w[] of one subcarrier's levels and an upper bound *s_bound on
+// its final N_pe-th cost (fixed point; kNoBound: none), in the group's
+// shared memory, by the group of G warps; ends with a group barrier.
+template <int QAM, int G, int MODE>
+__device__ __forceinline__ void sel_setup(int sc, int nt, int n_pe, float sigma2,
+                                          const float2 *__restrict__ Rp, float *w,
+                                          unsigned long long *s_bound, int group, int tid,
+                                          const RankLut &lut)
 {
     constexpr bool LUT = MODE == kSelLut;
     constexpr bool PAM = MODE == kSelPam;
     constexpr int RK = PAM ? Qam<QAM>::L : QAM;  // ranks per level
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned char *base = smem_raw + base_off;
     constexpr unsigned FULL = 0xffffffffu;
-    constexpr int T = 32 * G;  // threads per subcarrier
-    // three lists (struct of arrays) addressed as base + list * n_pe, so that
-    // the list index stays arithmetic (no pointer arrays in local memory)
-    unsigned long long *HI = reinterpret_cast<unsigned long long *>(base);
-    unsigned long long *LO = HI + 3 * n_pe;
-    unsigned long long *CO = LO + 3 * n_pe;
-    unsigned long long *s_bound = CO + 3 * n_pe;
-    float *w = reinterpret_cast<float *>(s_bound + 1);
-#define hi(b) (HI + (size_t)(b) * n_pe)
-#define lo(b) (LO + (size_t)(b) * n_pe)
-#define cost(b) (CO + (size_t)(b) * n_pe)
-
     const int P = nt * (nt + 1) / 2;
     if (LUT && tid < nt) {  // w[l] holds the level's table row (its bin)
         const int l = tid;
@@ -162,14 +177,8 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         w[l] = -logf(pe);
     }
     group_sync<G>(group);
-    // cost of rank 1 + j at level m
     auto shift_cost = [&](int m, int j) -> float {
-        if constexpr (LUT) return __ldg(lut.cost + (size_t)__float_as_int(w[m]) * QAM + j);
-        else return (float)j * w[m];
-    };
-    // the same in fixed point (rounded to nearest, clamped to kCostMax)
-    auto shift_q = [&](int m, int j) -> unsigned long long {
-        return __float2ull_rn(fminf(shift_cost(m, j), kCostMax) * kCostScale);
+        return sel_shift_cost<QAM, MODE>(w, lut, m, j);
     };
     // Number of deviations j >= 1 at level m whose shift cost j w_m is at
     // most r (linear costs; conservative: r w_m^-1 in float, and callers pass
@@ -194,31 +203,46 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     // v in float; the result is padded upward and returned in fixed point
     // (kNoBound: none).
     auto tighten_bound = [&](unsigned v1bits) -> unsigned long long {
-        if (v1bits == 0x7f800000u) return kNoBound;
-        float hi_v = __uint_as_float(v1bits);
-        if (!LUT && nt >= 2 && n_pe >= kBoundMinPe) {  // linear costs only
-            const int lane = tid & 31, a = lane & 15, h = lane >> 4;
+        const bool pairs = !LUT && nt >= 2 && n_pe >= kBoundMinPe;  // linear costs only
+        const int lane = tid & 31, a = lane & 15, h = lane >> 4;
+        // vectors with one or two deviations costing at most v (1 - 1e-5),
+        // all-ones included (all lanes of the first warp)
+        auto count_pairs = [&](float v) -> int {
+            const float vp = v * (1.0f - 1e-5f);
+            int cnt = 0;
+            if (a < nt) {
+                if (h == 0) cnt += count_upto(a, vp);
+                for (int k = 1 + h; 2 * k <= nt; k += 2) {
+                    if (2 * k == nt && a >= k) continue;
+                    const int b = a + k < nt ? a + k : a + k - nt;
+                    const bool ao = shift_cost(a, 1) >= shift_cost(b, 1);
+                    const int o = ao ? a : b, q = ao ? b : a;
+                    for (int j = 1; j < RK; ++j) {
+                        const float r = vp - shift_cost(o, j);
+                        if (!(r >= 0.f)) break;
+                        cnt += count_upto(q, r);
+                    }
+                }
+            }
+            return (int)__reduce_add_sync(FULL, (unsigned)cnt) + 1;
+        };
+        float hi_v;
+        if (v1bits != 0x7f800000u) {
+            hi_v = __uint_as_float(v1bits);
+        } else {
+            // fewer single-deviation vectors than N_pe: start from the most
+            // a two-deviation vector can cost, if enough of those exist
+            if (!pairs) return kNoBound;
+            float mx = 0.f;
+            for (int m = 0; m < nt; ++m) mx = fmaxf(mx, shift_cost(m, RK - 1));
+            hi_v = 2.0f * mx;
+            if (count_pairs(hi_v) < n_pe) return kNoBound;
+        }
+        if (pairs) {
             float lo_v = 0.f;
             for (int it = 0; it < kBoundIters; ++it) {
                 const float mid = 0.5f * (lo_v + hi_v);
-                const float vp = mid * (1.0f - 1e-5f);
-                int cnt = 0;
-                if (a < nt) {
-                    if (h == 0) cnt += count_upto(a, vp);
-                    for (int k = 1 + h; 2 * k <= nt; k += 2) {
-                        if (2 * k == nt && a >= k) continue;
-                        const int b = a + k < nt ? a + k : a + k - nt;
-                        const bool ao = shift_cost(a, 1) >= shift_cost(b, 1);
-                        const int o = ao ? a : b, q = ao ? b : a;
-                        for (int j = 1; j < RK; ++j) {
-                            const float r = vp - shift_cost(o, j);
-                            if (!(r >= 0.f)) break;
-                            cnt += count_upto(q, r);
-                        }
-                    }
-                }
-                cnt = (int)__reduce_add_sync(FULL, (unsigned)cnt) + 1;
-                if (cnt >= n_pe) hi_v = mid;
+                if (count_pairs(mid) >= n_pe) hi_v = mid;
                 else lo_v = mid;
             }
         }
@@ -304,6 +328,33 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
         if (tid == 0) *s_bound = bq;
     }
     group_sync<G>(group);
+}
+
+template <int QAM, int G, int MODE = kSelGeo>
+__device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, float sigma2,
+                                               const float2 *__restrict__ Rp,
+                                               uint8_t *__restrict__ paths, int base_off,
+                                               int group, int tid, RankLut lut = RankLut{})
+{
+    constexpr int RK = MODE == kSelPam ? Qam<QAM>::L : QAM;  // ranks per level
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + base_off;
+    constexpr int T = 32 * G;  // threads per subcarrier
+    // three lists (struct of arrays) addressed as base + list * n_pe, so that
+    // the list index stays arithmetic (no pointer arrays in local memory)
+    unsigned long long *HI = reinterpret_cast<unsigned long long *>(base);
+    unsigned long long *LO = HI + 3 * n_pe;
+    unsigned long long *CO = LO + 3 * n_pe;
+    unsigned long long *s_bound = CO + 3 * n_pe;
+    float *w = reinterpret_cast<float *>(s_bound + 1);
+#define hi(b) (HI + (size_t)(b) * n_pe)
+#define lo(b) (LO + (size_t)(b) * n_pe)
+#define cost(b) (CO + (size_t)(b) * n_pe)
+
+    sel_setup<QAM, G, MODE>(sc, nt, n_pe, sigma2, Rp, w, s_bound, group, tid, lut);
+    auto shift_q = [&](int m, int j) -> unsigned long long {
+        return sel_shift_q<QAM, MODE>(w, lut, m, j);
+    };
     const unsigned long long bound = *s_bound;  // fixed point; kNoBound: none
     // The first level processed (nt-1) in closed form: starting from the
     // all-ones vector, its list is the arithmetic sequence j * w (rank j + 1
@@ -415,6 +466,225 @@ __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, floa
     group_sync<G>(group);  // the region may be reused for the group's next subcarrier
 }
 
+// Narrow keys (the per-call geometric selection, N_pe >= kNarrowMinPe).  A
+// level m's rank offset p_m - 1 never exceeds j_m, the largest j whose shift
+// cost is within the bound (the merges stop there), so the key needs only
+// ceil(log2(j_m + 1)) bits for level m: fields packed with level nt-1 most
+// significant, so that comparing keys as integers is still the lexicographic
+// order from the top level down.  With the tightened bound that is under 40
+// bits on 16 levels of 64-QAM (N_pe 256 and 1024, 15-30 dB), so a key is one
+// u64 and an entry 16 bytes; and with two lists -- the previous level's list
+// L and the list B being built, merged into in place -- a group's state is
+// 32 N_pe + 108 bytes, under half of the general body's, so that the groups
+// of a 3276-subcarrier slot fit on the GPU at once.  The merges, their order
+// and their stopping rules are the general body's, so the tables are the
+// same.  A subcarrier whose fields need more than 64 bits marks its table (a
+// 0 in its first entry, which is otherwise rank 1) and is left to
+// select_paths_rest_kernel.
+__host__ __device__ inline size_t narrow_group_bytes(int n_pe)
+{
+    // 2 lists x (8 + 8) bytes, the bound, w[], field offsets and widths, a flag
+    return ((size_t)n_pe * 32 + 8 + kMaxNt * 4 + kMaxNt * 2 + 4 + 15) & ~(size_t)15;
+}
+
+constexpr int kNarrowPer = 4;  // outputs a thread holds per pass of an in-place merge
+// Shorter lists fit on the GPU at once with the general body already, which
+// is then faster: no in-place barriers, no second launch (measured on 16x16
+// 64-QAM, N_pe 64: 0.072 against 0.076 ms; N_pe 128: 0.108 against 0.103).
+constexpr int kNarrowMinPe = 128;
+
+__device__ __forceinline__ bool before_n(unsigned long long ca, unsigned long long ka,
+                                         unsigned long long cb, unsigned long long kb)
+{
+    return ca < cb || (ca == cb && ka < kb);
+}
+
+template <int QAM, int G>
+__device__ __forceinline__ void select_group_narrow(int sc, int nt, int n_pe, float sigma2,
+                                                    const float2 *__restrict__ Rp,
+                                                    uint8_t *__restrict__ paths, int base_off,
+                                                    int group, int tid)
+{
+    constexpr int RK = QAM;
+    constexpr int T = 32 * G;
+    constexpr unsigned FULL = 0xffffffffu;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *base = smem_raw + base_off;
+    unsigned long long *CO = reinterpret_cast<unsigned long long *>(base);  // [2][n_pe] costs
+    unsigned long long *KY = CO + 2 * n_pe;                                  // [2][n_pe] keys
+    unsigned long long *s_bound = KY + 2 * n_pe;
+    float *w = reinterpret_cast<float *>(s_bound + 1);
+    uint8_t *s_off = reinterpret_cast<uint8_t *>(w + kMaxNt);  // field offset per level
+    uint8_t *s_bits = s_off + kMaxNt;                            // field width per level
+    int *s_ok = reinterpret_cast<int *>(s_bits + kMaxNt);
+#define nco(b) (CO + (size_t)(b) * n_pe)
+#define nky(b) (KY + (size_t)(b) * n_pe)
+
+    const RankLut lut{};
+    sel_setup<QAM, G, kSelGeo>(sc, nt, n_pe, sigma2, Rp, w, s_bound, group, tid, lut);
+    auto shift_q = [&](int m, int j) -> unsigned long long {
+        return sel_shift_q<QAM, kSelGeo>(w, lut, m, j);
+    };
+    const unsigned long long bound = *s_bound;
+    // field widths: the largest rank offset each level can take under the
+    // bound, found with the merges' own fixed-point comparison
+    if (tid < 32) {
+        int bits = 0;
+        if (tid < nt) {
+            int jm = 0;
+            while (jm + 1 < RK && shift_q(tid, jm + 1) <= bound) ++jm;
+            bits = jm ? 32 - __clz(jm) : 0;
+        }
+        int incl = bits;  // inclusive sum over levels 0..tid
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, o);
+            if (tid >= o) incl += v;
+        }
+        if (tid < nt) {
+            s_off[tid] = (uint8_t)(incl - bits);
+            s_bits[tid] = (uint8_t)bits;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        if (tid == 0) *s_ok = total <= 64;
+    }
+    group_sync<G>(group);
+    uint8_t *out = paths + (size_t)sc * n_pe * nt;
+    if (!*s_ok) {
+        if (tid == 0) out[0] = 0;  // left to the general body
+        group_sync<G>(group);
+        return;
+    }
+    // the first level (nt-1) in closed form, as in the general body
+    int li = 0, nL = 1;
+    {
+        const int mt = nt - 1;
+        while (nL < RK && nL < n_pe && shift_q(mt, nL) <= bound) ++nL;
+        const int sh = s_off[mt];  // below 64 whenever nL > 1
+        for (int j = tid; j < nL; j += T) {
+            nco(0)[j] = shift_q(mt, j);
+            nky(0)[j] = j ? (unsigned long long)j << sh : 0ull;
+        }
+    }
+    group_sync<G>(group);
+    for (int m = nt - 2; m >= 0; --m) {
+        const int sh = s_off[m];
+        int bi = li, nB = nL;  // B starts as L itself (read only)
+        const int oi = 1 - li;
+        for (int j = 1; j < RK; ++j) {
+            const unsigned long long cj = shift_q(m, j);
+            if (cj > bound) break;
+            const unsigned long long add = (unsigned long long)j << sh;  // level m has a field
+            if (nB == n_pe &&
+                !before_n(nco(li)[0] + cj, nky(li)[0] + add, nco(bi)[nB - 1], nky(bi)[nB - 1]))
+                break;
+            const int nOut = min(n_pe, nB + nL);
+            // co-rank of output k0: how many of the first k0 outputs come from B
+            auto co_rank = [&](int k0) {
+                int lo_i = max(0, k0 - nL), hi_i = min(k0, nB);
+                while (lo_i < hi_i) {
+                    const int i = (lo_i + hi_i) >> 1, jj = k0 - i;  // jj >= 1, i < nB
+                    if (before_n(nco(bi)[i], nky(bi)[i], nco(li)[jj - 1] + cj, nky(li)[jj - 1] + add))
+                        lo_i = i + 1;
+                    else
+                        hi_i = i;
+                }
+                return lo_i;
+            };
+            if (bi == li) {
+                // the level's first merge: B is L, the result goes to the other list
+                const int per = (nOut + T - 1) / T;
+                const int k0 = min(nOut, tid * per), k1 = min(nOut, k0 + per);
+                if (k0 < k1) {
+                    int i = co_rank(k0), jj = k0 - i;
+                    for (int k = k0; k < k1; ++k) {
+                        unsigned long long ca = 0ull, ka = 0ull, cc = 0ull, kc = 0ull;
+                        if (i < nB) {
+                            ca = nco(bi)[i];
+                            ka = nky(bi)[i];
+                        }
+                        if (jj < nL) {
+                            cc = nco(li)[jj] + cj;
+                            kc = nky(li)[jj] + add;
+                        }
+                        const bool take_b = jj >= nL || (i < nB && before_n(ca, ka, cc, kc));
+                        nco(oi)[k] = take_b ? ca : cc;
+                        nky(oi)[k] = take_b ? ka : kc;
+                        if (take_b) ++i;
+                        else ++jj;
+                    }
+                }
+                group_sync<G>(group);
+                bi = oi;
+            } else {
+                // in place in B: passes over the outputs from the back.  A
+                // pass reads only entries of B below its end, which no pass
+                // has written yet, into registers; the group meets; then it
+                // writes.  Outputs that stay where they are are not written.
+                for (int end = nOut; end > 0; end -= T * kNarrowPer) {
+                    const int start = max(0, end - T * kNarrowPer);
+                    const int per = (end - start + T - 1) / T;
+                    const int k0 = min(end, start + tid * per), k1 = min(end, k0 + per);
+                    unsigned long long rc[kNarrowPer], rk[kNarrowPer];
+                    bool moved = false;
+                    if (k0 < k1) {
+                        int i = co_rank(k0), jj = k0 - i;
+                        moved = jj != 0;
+#pragma unroll
+                        for (int q = 0; q < kNarrowPer; ++q) {
+                            rc[q] = rk[q] = 0ull;
+                            if (k0 + q < k1) {
+                                unsigned long long ca = 0ull, ka = 0ull, cc = 0ull, kc = 0ull;
+                                if (i < nB) {
+                                    ca = nco(bi)[i];
+                                    ka = nky(bi)[i];
+                                }
+                                if (jj < nL) {
+                                    cc = nco(li)[jj] + cj;
+                                    kc = nky(li)[jj] + add;
+                                }
+                                const bool take_b = jj >= nL || (i < nB && before_n(ca, ka, cc, kc));
+                                rc[q] = take_b ? ca : cc;
+                                rk[q] = take_b ? ka : kc;
+                                if (take_b) {
+                                    ++i;
+                                } else {
+                                    ++jj;
+                                    moved = true;
+                                }
+                            }
+                        }
+                    }
+                    group_sync<G>(group);
+                    if (moved) {
+#pragma unroll
+                        for (int q = 0; q < kNarrowPer; ++q)
+                            if (k0 + q < k1) {
+                                nco(bi)[k0 + q] = rc[q];
+                                nky(bi)[k0 + q] = rk[q];
+                            }
+                    }
+                }
+                group_sync<G>(group);
+            }
+            nB = nOut;
+        }
+        li = bi;
+        nL = nB;
+    }
+
+    // the table: row r, level l -> 1 + the key's field for l
+    for (int k = tid; k < n_pe * nt; k += T) {
+        const int r = k / nt, l = k - r * nt;
+        const int b = s_bits[l];
+        const unsigned long long v = nky(li)[r];
+        out[k] = (uint8_t)(1 + (b ? (int)((v >> s_off[l]) & ((1ull << b) - 1ull)) : 0));
+    }
+#undef nco
+#undef nky
+    group_sync<G>(group);
+}
+
 template <int QAM, int G>
 __global__ void __launch_bounds__(kSelMaxWarps * 32)
 select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
@@ -426,6 +696,39 @@ select_paths_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__re
     if (sc >= n_sc) return;  // whole groups leave; each group syncs only itself
     select_group_body<QAM, G>(sc, nt, n_pe, sigma2, Rp, paths,
                               group * (int)sel_group_bytes(n_pe), group, tid);
+}
+
+// Two warps a subcarrier: at most 40 registers, so that twelve CTAs (24
+// subcarriers) fit on an SM; one warp: the shared memory allows 24 anyway.
+template <int QAM, int G>
+__global__ void __launch_bounds__(kSelMaxWarps * 32, G == 2 ? 12 : 1)
+select_paths_narrow_kernel(int n_sc, int nt, int n_pe, float sigma2,
+                           const float2 *__restrict__ Rp, uint8_t *__restrict__ paths)
+{
+    constexpr int T = 32 * G;
+    const int group = threadIdx.x / T, tid = threadIdx.x % T;
+    const int sc = blockIdx.x * (blockDim.x / T) + group;
+    if (sc >= n_sc) return;
+    select_group_narrow<QAM, G>(sc, nt, n_pe, sigma2, Rp, paths,
+                                group * (int)narrow_group_bytes(n_pe), group, tid);
+}
+
+// The subcarriers select_paths_narrow_kernel left (a 0 in the first entry of
+// their table), by the general body; groups stride over the subcarriers and
+// skip the others after one byte.
+template <int QAM, int G>
+__global__ void __launch_bounds__(kSelMaxWarps * 32)
+select_paths_rest_kernel(int n_sc, int nt, int n_pe, float sigma2, const float2 *__restrict__ Rp,
+                         uint8_t *__restrict__ paths)
+{
+    constexpr int T = 32 * G;
+    const int group = threadIdx.x / T, tid = threadIdx.x % T;
+    const int groups = blockDim.x / T;
+    for (int sc = blockIdx.x * groups + group; sc < n_sc; sc += gridDim.x * groups) {
+        if (paths[(size_t)sc * n_pe * nt] != 0) continue;  // the same for the whole group
+        select_group_body<QAM, G>(sc, nt, n_pe, sigma2, Rp, paths,
+                                  group * (int)sel_group_bytes(n_pe), group, tid);
+    }
 }
 
 template <int QAM, int G>
@@ -517,9 +820,40 @@ cudaError_t launch_group_pam(int n_sc, int ntr, int n_pe, float sigma2, const fl
 }
 
 template <int QAM, int G>
+cudaError_t launch_group_narrow(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
+                                uint8_t *paths, cudaStream_t stream)
+{
+    // narrow keys, a CTA of kSelMaxWarps warps (kSelMaxWarps / G subcarriers)
+    {
+        const int groups = kSelMaxWarps / G;
+        const size_t smem = narrow_group_bytes(n_pe) * groups;
+        cudaError_t e = allow_dynamic_smem(select_paths_narrow_kernel<QAM, G>, smem);
+        if (e != cudaSuccess) return e;
+        const int grid = (n_sc + groups - 1) / groups;
+        select_paths_narrow_kernel<QAM, G><<<grid, groups * G * 32, smem, stream>>>(
+            n_sc, nt, n_pe, sigma2, R, paths);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // the subcarriers it left, by the general body
+    const size_t per = sel_group_bytes(n_pe);
+    int groups = (int)((100 * 1024) / per);
+    groups = groups < 1 ? 1 : (groups > kSelMaxWarps / G ? kSelMaxWarps / G : groups);
+    const size_t smem = per * groups;
+    cudaError_t e = allow_dynamic_smem(select_paths_rest_kernel<QAM, G>, smem);
+    if (e != cudaSuccess) return e;
+    const int grid = min((n_sc + groups - 1) / groups, 128);
+    select_paths_rest_kernel<QAM, G><<<grid, groups * G * 32, smem, stream>>>(n_sc, nt, n_pe,
+                                                                             sigma2, R, paths);
+    return cudaGetLastError();
+}
+
+template <int QAM, int G>
 cudaError_t launch_group(int n_sc, int nt, int n_pe, float sigma2, const float2 *R,
                          uint8_t *paths, cudaStream_t stream)
 {
+    if (n_pe >= kNarrowMinPe)
+        return launch_group_narrow<QAM, G>(n_sc, nt, n_pe, sigma2, R, paths, stream);
     // as many groups (subcarriers) per CTA as fit in about 100 KB of shared
     // memory, at most kSelMaxWarps warps
     const size_t per = sel_group_bytes(n_pe);
