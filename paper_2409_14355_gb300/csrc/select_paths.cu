@@ -112,11 +112,6 @@ struct RankLut {
     int n_bins;
 };
 
-// One subcarrier by one group of G warps (thread tid of the group, which is
-// group number `group` of its CTA), in the group's shared-memory region at
-// byte offset base_off (at least sel_group_bytes(n_pe)).  Inlined into
-// the per-call and the batch kernels alike (no contraction).  LUT: costs
-// from the table `lut` (else the geometric model, w_l = -log Pe_l).
 // Cost models: the geometric rank model of square M-QAM levels, a caller's
 // rank-cost table, or the geometric model of the L-PAM levels of the
 // real-valued decomposition (ranks 1..L, Pe = 2 (1 - 1/L) Q(.) per level).
@@ -330,6 +325,11 @@ __device__ __forceinline__ void sel_setup(int sc, int nt, int n_pe, float sigma2
     group_sync<G>(group);
 }
 
+// One subcarrier by one group of G warps (thread tid of the group, which is
+// group number `group` of its CTA), in the group's shared-memory region at
+// byte offset base_off (at least sel_group_bytes(n_pe)).  Inlined into
+// the per-call and the batch kernels alike (no contraction).  LUT: costs
+// from the table `lut` (else the geometric model, w_l = -log Pe_l).
 template <int QAM, int G, int MODE = kSelGeo>
 __device__ __forceinline__ void select_group_body(int sc, int nt, int n_pe, float sigma2,
                                                const float2 *__restrict__ Rp,
